@@ -1,0 +1,355 @@
+"""Throughput of the WADG right-hand side + LSRK update on GB300.
+
+Workload (the configuration the headline metric is quoted on): the warped
+Kuhn cube with 32^3 hexahedra x 6 = 196,608 curved tetrahedra, degree N = 4
+(Np = 35), heterogeneous c^2 = 1 + 0.5 sin(pi x) sin(pi y) sin(pi z) at the
+volume quadrature points, standing-wave initial data.  One step = one LSRK(5,4)
+time step = 5 fused stage launches (strong-weak volume + surface terms,
+weight-adjusted update, Runge-Kutta update).  DOF = 4 K Np S scalar unknowns;
+value = DOF * stages / second.
+
+The headline line is the FP32 path; the FP64 path is measured on the same
+mesh, data and dt and reported under "variants".  Inputs (1.1 GB of FP32
+geometric factors alone) are larger than the 129 MB L2, so no flush is
+needed between iterations.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n=32, N=4, warp=0.1, c2="heterogeneous")
+METRIC = "WADG RHS DOF*stage/s (RHS + weight-adjusted update + LSRK stage)"
+UNIT = "DOF*stage/s"
+
+
+def algorithmic(N: int, S: int, s: int):
+    """Per element and stage: algorithmic bytes (fields read/written once,
+    geometric factors read once, neighbour reads counted as L2 hits) and flops
+    (dense reference-operator products)."""
+    Np = (N + 1) * (N + 2) * (N + 3) // 6
+    Nq, Nfq = (N + 1) ** 3, (N + 1) ** 2
+    B = s * (16 * Np * S + 11 * Nq + 12 * Nfq) + 32
+    F = (24 + 16) * Nq * Np * S + 16 * Np * 4 * Nfq * S
+    return B, F
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 6800.0, "fallback", 2070.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_case(W, precision, rank):
+    import torch
+    from synthetic import warped_cube, c2_heterogeneous, standing_wave
+    VXYZ, EToV, geom = warped_cube(WORKLOAD["n"], WORKLOAD["N"], WORKLOAD["warp"])
+    m = W.wadg_mesh_create(WORKLOAD["N"], VXYZ, EToV, geom)
+    xq = W.wadg_volume_points(m)
+    W.wadg_set_operators(m, precision, 1, 1.0, 1.0, c2_heterogeneous(xq))
+    fq = torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda()
+    Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
+    W.wadg_project(m, fq, Q)
+    del fq
+    return m, Q
+
+
+def dt_for(m):
+    # CFL-type step: 0.5 h_min / (c_max (N+1)^2) with h = hex side / 2
+    h = 2.0 / WORKLOAD["n"]
+    return 0.5 * (h / 2) / (math.sqrt(1.5) * (WORKLOAD["N"] + 1) ** 2)
+
+
+def time_steps(W, m, Q, steps, warmup):
+    """Device time of `steps` LSRK steps (one C-ABI call) and of one stage launch."""
+    import torch
+    R = torch.zeros_like(Q)
+    dt = dt_for(m)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        W.wadg_step(m, Q, R, 0.0, dt, 1)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    W.wadg_step(m, Q, R, 0.0, dt, steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    total_ms = start.elapsed_time(stop)
+    # one stage launch alone, averaged (same stream, same kernel)
+    out = torch.empty_like(Q)
+    reps = 5
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        W.wadg_rhs(m, Q, out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return total_ms, a.elapsed_time(b) / reps
+
+
+def e2e_steps(W, m, Q, steps):
+    """Same metric end to end: pinned host Q, res -> device, one step, -> host."""
+    import torch
+    Qh = Q.cpu().pin_memory()
+    Rh = torch.zeros_like(Qh).pin_memory()
+    Qd, Rd = torch.empty_like(Q), torch.empty_like(Q)
+    dt = dt_for(m)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        Qd.copy_(Qh, non_blocking=True)
+        Rd.copy_(Rh, non_blocking=True)
+        W.wadg_step(m, Qd, Rd, 0.0, dt, 1)
+        Qh.copy_(Qd, non_blocking=True)
+        Rh.copy_(Rd, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    nbytes = 2 * Q.numel() * Q.element_size()
+    return a.elapsed_time(b) / steps, nbytes
+
+
+class OracleSample:
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: the
+    same recipe (warped cube, N = 4, heterogeneous c^2) on a 16^3-hex cube
+    (24,576 tets, 1/8 of the workload); one stage = oracle RHS (strong-weak
+    terms + matrix-free weight-adjusted inverse) + LSRK update, single thread."""
+
+    def __init__(self):
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        try:
+            from threadpoolctl import threadpool_limits
+            self._limit = threadpool_limits(1)
+        except Exception:
+            self._limit = None
+        from oracle import wadg as OW
+        from oracle.discretization import Mesh, RefTet
+        from synthetic import warped_cube, c2_heterogeneous, random_fields
+        self.OW = OW
+        n, N = 16, WORKLOAD["N"]
+        VXYZ, EToV, geom = warped_cube(n, N, WORKLOAD["warp"])
+        self.ref = RefTet(N)
+        self.mesh = Mesh(self.ref, VXYZ, EToV, geom)
+        self.c2 = c2_heterogeneous(self.mesh.xq)
+        self.c = self.ref.to_modal(random_fields((4, self.mesh.K, self.ref.Np), 1))
+        self.res = np.zeros_like(self.c)
+        self.dof = 4 * self.mesh.K * self.ref.Np
+        self.s = 0
+
+    def stage(self) -> float:
+        t0 = time.perf_counter()
+        r = self.OW.rhs(self.mesh, self.c, c2q=self.c2)
+        self.res = self.OW.LSRK_A[self.s % 5] * self.res + 1e-4 * r
+        self.c = self.c + self.OW.LSRK_B[self.s % 5] * self.res
+        self.s += 1
+        return time.perf_counter() - t0
+
+    def describe(self, stages, seconds):
+        return (f"warped cube 16^3 x 6 = {self.mesh.K} tets, N={self.ref.N}, heterogeneous c^2, FP64, "
+                f"{stages} stages in {seconds:.1f} s (1 thread)")
+
+
+def cpu_baseline(budget_s: float = 20.0):
+    o = OracleSample()
+    o.stage()  # warm-up
+    stages, t = 0, 0.0
+    while t < budget_s and stages < 25:
+        t += o.stage()
+        stages += 1
+    return {"value": o.dof * stages / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": o.describe(stages, t)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """Reference arm: the oracle on the host cores, one stage per step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    o = OracleSample()
+    for _ in range(args.warmup):
+        o.stage()
+    t = sum(o.stage() for _ in range(args.steps))
+    v = o.dof * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "warped Kuhn cube, N=4, heterogeneous c^2; FP64 oracle on a 16^3x6 = 24576-tet "
+                                   "sample of the 196608-tet workload, one stage per step"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": o.describe(args.steps, t), "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_1608_03836_gb300 as W
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    m, Q = build_case(W, "fp32", rank)
+    Np, K = m.Np, m.K
+    dof = 4 * K * Np
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        total_ms, stage_ms = time_steps(W, m, Q, args.steps, args.warmup)
+    barrier()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * dof * 5 / (ms_per_step * 1e-3)
+    e2e_ms, nbytes = e2e_steps(W, m, Q, max(2, args.steps // 2))
+    e2e_value = ws * dof * 5 / (e2e_ms * 1e-3)
+
+    hbm, peak_kind, sm_max = peaks()
+    B, F = algorithmic(WORKLOAD["N"], 1, 4)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, CUDA-core FMA
+    achieved_tf = F * K / (stage_ms * 1e-3) / 1e12
+    achieved_gbs = B * K / (stage_ms * 1e-3) / 1e9
+
+    variants = {}
+    if not args.no_fp64:
+        del Q
+        m64, Q64 = build_case(W, "fp64", rank)
+        t64, s64 = time_steps(W, m64, Q64, max(1, args.steps // 5), 3)
+        ms64 = t64 / max(1, args.steps // 5)
+        B64, _ = algorithmic(WORKLOAD["N"], 1, 8)
+        variants["fp64"] = {"value": ws * dof * 5 / (ms64 * 1e-3), "ms_per_step": ms64, "stage_ms": s64,
+                            "achieved_tflops": F * K / (s64 * 1e-3) / 1e12,
+                            "achieved_gbs": B64 * K / (s64 * 1e-3) / 1e9, "dtype": "f64"}
+        del Q64, m64
+    variants["fp32"] = {"value": value, "ms_per_step": ms_per_step, "stage_ms": stage_ms,
+                        "achieved_tflops": achieved_tf, "achieved_gbs": achieved_gbs, "dtype": "f32"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "warped Kuhn cube 32^3x6 = 196608 curved tets, N=4 (Np=35), heterogeneous c^2, "
+                               "1 shot, LSRK(5,4) step = 5 fused stage launches",
+                   "elements": K, "N": WORKLOAD["N"], "shots": 1, "dof": dof,
+                   "l2": "inputs larger than L2 (1.1 GB FP32 geometric factors)",
+                   "parallelism": f"replicas{ws}"},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp32_peak, "traffic": None,
+                     "kernel": "stage_kernel<float,4,16> (one launch = one stage over all elements)",
+                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)",
+                     "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                             "peak_kind": peak_kind}},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk.summary(),
+        "variants": variants,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

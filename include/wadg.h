@@ -1,0 +1,158 @@
+/*
+ * wadg.h -- C ABI of the GB300 weight-adjusted DG (WADG) library.
+ *
+ * Method: Chan, Hewett & Warburton, "Weight-adjusted discontinuous Galerkin
+ * methods: curvilinear meshes" (arXiv:1608.03836).  The library evaluates the
+ * semi-discrete acoustic system dQ/dt = -M~^{-1} A_h Q (Sec. 4) on curved
+ * tetrahedral meshes with the strong-weak formulation (Sec. 4.1), the
+ * weight-adjusted mass inverse M^^{-1} M_{c^2/J} M^^{-1} applied matrix-free as
+ * P_q diag(c^2_q/J_q) V_q (Sec. 6.2, Eq. (matfree); Sec. 7 for c^2), and the
+ * five-stage fourth-order low-storage Runge-Kutta scheme (Sec. 5.2).
+ *
+ * Conventions shared by every entry point
+ *  - Returns a wadg_status code; nothing aborts, traps or exits.  Argument and
+ *    geometry errors are detected on the host before any launch.  After an
+ *    error, wadg_last_error(mesh) holds a one-line description.
+ *  - Reference element: {r,s,t >= -1, r+s+t <= -1}, vertices v0=(-1,-1,-1),
+ *    v1=(1,-1,-1), v2=(-1,1,-1), v3=(-1,-1,1); faces f0=(v0,v1,v2),
+ *    f1=(v0,v1,v3), f2=(v1,v2,v3), f3=(v0,v2,v3).
+ *  - Nodal layout ("lattice"): the solution is stored as values at the
+ *    equispaced degree-N lattice, node (i,j,k), i+j+k <= N, at
+ *    (-1+2i/N, -1+2j/N, -1+2k/N), ordered i fastest, then j, then k.
+ *    Np = (N+1)(N+2)(N+3)/6.
+ *  - Field buffers Q, res, dQdt are caller-owned DEVICE arrays laid out
+ *    [4][K][S][Np] (fields p, u1, u2, u3; element; shot; node), in the mesh
+ *    precision (double for WADG_FP64, float otherwise), 16-byte aligned.
+ *  - Volume quadrature: collapsed Gauss-Jacobi rule with N+1 points per
+ *    direction (exact to degree 2N+1, Sec. 6.2), Nq = (N+1)^3; point
+ *    (ia,ib,ic) has index ia + (N+1)(ib + (N+1) ic), with
+ *    r = (1+a)(1-b)(1-c)/4 - 1, s = (1+b)(1-c)/2 - 1, t = c and a, b, c the
+ *    ascending Gauss-Jacobi nodes for the weights 1, (1-b), (1-c)^2.
+ *  - Face quadrature: collapsed rule with N+1 points per direction on the
+ *    reference triangle, Nfq = (N+1)^2.  A face shared by two elements is
+ *    integrated by both at the points of its owner, the element with the lower
+ *    index (Sec. 6.4 uses values at the same "neighbouring" face points).
+ *  - Streams are passed as opaque pointers (cudaStream_t; NULL = legacy
+ *    default stream).  Work is enqueued; no entry point synchronises unless it
+ *    returns a host value (wadg_energy, wadg_l2_error).
+ */
+#ifndef WADG_H
+#define WADG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wadg_mesh wadg_mesh;  /* opaque, library-owned */
+typedef void* wadg_stream;           /* a cudaStream_t */
+
+enum wadg_status {
+    WADG_OK = 0,
+    WADG_EINVAL = -1,       /* bad argument (size, pointer, alignment)        */
+    WADG_ENOMEM = -2,       /* device or host allocation failed               */
+    WADG_ECUDA = -3,        /* a CUDA call failed (message in last_error)     */
+    WADG_EGEOM = -4,        /* J <= 0, inverted element or non-conforming face */
+    WADG_ESTATE = -5,       /* call order (e.g. operators not set)            */
+    WADG_ETIMEOUT = -6,     /* a bounded device wait expired                  */
+    WADG_EUNSTABLE = -7,    /* non-finite energy                              */
+    WADG_EUNSUPPORTED = -8  /* order or precision not built                   */
+};
+
+enum wadg_precision {
+    WADG_FP64 = 0,          /* FP64 fields, FP64 arithmetic (CUDA cores)      */
+    WADG_FP32 = 1           /* FP32 fields, FP32 arithmetic (CUDA cores)      */
+};
+
+/* Library version as major*10000 + minor*100 + patch. */
+int wadg_version(void);
+
+/* Create a mesh (Sec. 2: elements D^k = Phi^k(D^), isoparametric of degree N).
+ *   N        polynomial degree, 1 <= N <= 6.
+ *   VXYZ     host [Nv][3] vertex coordinates (FP64).
+ *   EToV     host [K][4] vertex indices; each element must be positively
+ *            oriented for the reference vertex order above (WADG_EGEOM if not).
+ *   geom_xyz host [K][Np][3] physical coordinates of each element's lattice
+ *            nodes (the isoparametric map is their degree-N interpolant), or
+ *            NULL for straight-sided (affine) elements.
+ *   out      receives the handle.
+ * Builds connectivity (faces matched by their vertex triples; a face shared by
+ * more than two elements is WADG_EGEOM), the reference operators, and the FP64
+ * geometric factors on the current CUDA device: J and G_ai = J dx^_a/dx_i at
+ * volume points and n J^f at face points (Sec. 4.1: these are polynomial for
+ * an isoparametric map).  WADG_EGEOM if J <= 0 at any volume point.  The
+ * library copies what it needs; the caller keeps ownership of its arrays. */
+int wadg_mesh_create(int N, int64_t Nv, const double* VXYZ, int64_t K, const int64_t* EToV,
+                     const double* geom_xyz, wadg_mesh** out);
+
+/* Select precision and material, and allocate the library's work buffers.
+ *   precision WADG_FP64 or WADG_FP32.
+ *   shots     S >= 1 right-hand sides sharing the mesh (columns [K][S]).
+ *   tau_p, tau_u  penalty parameters of the strong-weak flux (Sec. 4.1;
+ *             1 = upwind, 0 = central), both >= 0.
+ *   c2q       host [K][Nq] values of c^2 at the volume quadrature points
+ *             (Sec. 7), or NULL for c^2 = 1; every value must be > 0.
+ * May be called again to change any of these. */
+int wadg_set_operators(wadg_mesh* mesh, int precision, int shots, double tau_p, double tau_u,
+                       const double* c2q);
+
+/* Sizes: info[0..7] = N, K, Np, Nq, Nfp, Nfq, S, precision (S, precision are
+ * -1 before wadg_set_operators). */
+int wadg_mesh_info(const wadg_mesh* mesh, int64_t info[8]);
+
+/* Physical coordinates of the volume quadrature points, host [K][Nq][3] FP64. */
+int wadg_volume_points(const wadg_mesh* mesh, double* xyz);
+
+/* Reference rules for degree N (host only, no device work): rst_q [Nq][3],
+ * w_q [Nq], rs_f [Nfq][2], w_f [Nfq].  Any pointer may be NULL. */
+int wadg_reference_rules(int N, double* rst_q, double* w_q, double* rs_f, double* w_f);
+
+/* Weight-adjusted pseudo-projection P_N u = Pi_N(J^{-1} Pi_N(u J)) (Sec. 3,
+ * Theorem) of values at the volume quadrature points.
+ *   fq  device [4][K][S][Nq] FP64 values of (p, u1, u2, u3).
+ *   Q   device [4][K][S][Np] output in the mesh precision. */
+int wadg_project(wadg_mesh* mesh, const double* fq, void* Q, wadg_stream stream);
+
+/* Right-hand side dQdt = -M~^{-1} A_h Q (Sec. 4; strong-weak A_h of Sec. 4.1;
+ * M~^{-1} = P_q diag(W) V_q M^^{-1}, W = c^2/J for p and 1/J for u, Sec. 6.2
+ * and Sec. 7).  Q and dQdt are device [4][K][S][Np] and must not overlap. */
+int wadg_rhs(wadg_mesh* mesh, const void* Q, void* dQdt, wadg_stream stream);
+
+/* nsteps steps of LSRK(5,4) (Sec. 5.2) from time t0 with step dt.  Each stage:
+ * res = a_s res + dt (-M~^{-1} A_h Q + source); Q = Q + b_s res.
+ *   Q, res   device [4][K][S][Np], updated in place (res = 0 at a cold start).
+ *   traces   device [nsteps][S][R] in the mesh precision: pressure at the
+ *            receivers after every step, or NULL (ignored when R = 0).
+ * Sources and receivers are those set by wadg_set_sources/wadg_set_receivers. */
+int wadg_step(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nsteps, void* traces,
+              wadg_stream stream);
+
+/* Point sources, one per shot: a Ricker wavelet (1-2 pi^2 f0^2 tau^2)
+ * exp(-pi^2 f0^2 tau^2), tau = t - t0, times delta(x - x_s) added to the
+ * pressure equation at every stage time.
+ *   xyz  host [S][3] physical source positions (S = shots); NULL removes the
+ *        sources.  A point outside the mesh is WADG_EINVAL. */
+int wadg_set_sources(wadg_mesh* mesh, const double* xyz, double f0, double t0);
+
+/* Receivers: R points per shot, host [S][R][3]; R = 0 removes them. */
+int wadg_set_receivers(wadg_mesh* mesh, int R, const double* xyz);
+
+/* Energy 1/2 int (p^2/c^2 + |u|^2) by the volume rule, summed over shots,
+ * FP64 reduction; E is a host double.  WADG_EUNSTABLE if not finite. */
+int wadg_energy(wadg_mesh* mesh, const void* Q, double* E, wadg_stream stream);
+
+/* L2 error sqrt(sum_k int (q_h - q)^2) over the fields in field_mask (bit f for
+ * field f) against exact values at the volume points, device [4][K][S][Nq]
+ * FP64.  err is a host double. */
+int wadg_l2_error(wadg_mesh* mesh, const void* Q, const double* exact_q, int field_mask, double* err,
+                  wadg_stream stream);
+
+void wadg_mesh_destroy(wadg_mesh* mesh);
+const char* wadg_status_string(int status);
+const char* wadg_last_error(const wadg_mesh* mesh);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WADG_H */

@@ -1,0 +1,33 @@
+"""GB300-native weight-adjusted DG (WADG) right-hand side for curved tetrahedral meshes.
+
+Chan, Hewett & Warburton, "Weight-adjusted discontinuous Galerkin methods:
+curvilinear meshes" (arXiv:1608.03836).  The hot path (strong-weak volume and
+surface terms, weight-adjusted mass inverse, LSRK(5,4) update) runs in the
+hand-written CUDA kernels of libwadg.so behind the C ABI of include/wadg.h;
+this package only marshals arguments.  Importing it loads the library and
+raises ImportError when it has not been built: there is no CPU fallback.
+"""
+from ._lib import WadgError, load, LIB_PATH  # noqa: F401
+
+load()
+
+from .api import (  # noqa: E402,F401
+    WADG_FP32,
+    WADG_FP64,
+    MeshHandle,
+    wadg_energy,
+    wadg_l2_error,
+    wadg_last_error,
+    wadg_mesh_create,
+    wadg_mesh_destroy,
+    wadg_project,
+    wadg_reference_rules,
+    wadg_rhs,
+    wadg_set_operators,
+    wadg_set_receivers,
+    wadg_set_sources,
+    wadg_status_string,
+    wadg_step,
+    wadg_version,
+    wadg_volume_points,
+)

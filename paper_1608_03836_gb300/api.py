@@ -1,0 +1,201 @@
+"""Python binding of the WADG C ABI (argument marshalling only).
+
+Every function has the name of the C entry point it calls (include/wadg.h).
+Device buffers are torch CUDA tensors (PyTorch supplies device memory and
+streams); host arrays are numpy.  All arithmetic runs in the library's CUDA
+kernels: nothing here computes on the data.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import WadgError, load
+
+WADG_FP64, WADG_FP32 = 0, 1
+PRECISIONS = {"fp64": WADG_FP64, "fp32": WADG_FP32}
+
+
+def _check(status: int, where: str, mesh=None):
+    if status != 0:
+        detail = ""
+        if mesh is not None:
+            detail = (load().wadg_last_error(mesh.handle) or b"").decode()
+        raise WadgError(status, where, detail)
+
+
+def _dptr(arr: np.ndarray):
+    return arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class MeshHandle:
+    """Owns a wadg_mesh*; freed by wadg_mesh_destroy."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+        info = (ctypes.c_int64 * 8)()
+        _check(load().wadg_mesh_info(handle, info), "wadg_mesh_info")
+        self.N, self.K, self.Np, self.Nq, self.Nfp, self.Nfq = (int(v) for v in info[:6])
+        self.S = 1
+        self.precision = None
+        self.R = 0
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == WADG_FP64 else torch.float32
+
+    def field_shape(self):
+        return (4, self.K, self.S, self.Np)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().wadg_mesh_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def wadg_version() -> int:
+    return load().wadg_version()
+
+
+def wadg_mesh_create(N: int, VXYZ, EToV, geom_xyz=None) -> MeshHandle:
+    lib = load()
+    V = np.ascontiguousarray(VXYZ, dtype=np.float64)
+    E = np.ascontiguousarray(EToV, dtype=np.int64)
+    G = None if geom_xyz is None else np.ascontiguousarray(geom_xyz, dtype=np.float64)
+    out = ctypes.c_void_p()
+    st = lib.wadg_mesh_create(int(N), V.shape[0], _dptr(V), E.shape[0],
+                              E.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              None if G is None else _dptr(G), ctypes.byref(out))
+    _check(st, "wadg_mesh_create")
+    return MeshHandle(out)
+
+
+def wadg_set_operators(mesh: MeshHandle, precision="fp64", shots: int = 1, tau_p: float = 1.0,
+                       tau_u: float = 1.0, c2q=None):
+    prec = PRECISIONS.get(precision, precision)
+    c2 = None if c2q is None else np.ascontiguousarray(c2q, dtype=np.float64)
+    if c2 is not None and c2.size != mesh.K * mesh.Nq:
+        raise ValueError("c2q must have K*Nq values")
+    st = load().wadg_set_operators(mesh.handle, int(prec), int(shots), float(tau_p), float(tau_u),
+                                   None if c2 is None else _dptr(c2))
+    _check(st, "wadg_set_operators", mesh)
+    mesh.S = int(shots)
+    mesh.precision = int(prec)
+    mesh.R = 0
+
+
+def wadg_reference_rules(N: int):
+    Nq, Nfq = (N + 1) ** 3, (N + 1) ** 2
+    rst, w, rs, wf = np.zeros((Nq, 3)), np.zeros(Nq), np.zeros((Nfq, 2)), np.zeros(Nfq)
+    _check(load().wadg_reference_rules(int(N), _dptr(rst), _dptr(w), _dptr(rs), _dptr(wf)), "wadg_reference_rules")
+    return rst, w, rs, wf
+
+
+def wadg_volume_points(mesh: MeshHandle) -> np.ndarray:
+    out = np.zeros((mesh.K, mesh.Nq, 3))
+    _check(load().wadg_volume_points(mesh.handle, _dptr(out)), "wadg_volume_points", mesh)
+    return out
+
+
+def _check_field(mesh, t, name, dtype=None, last=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    want = dtype if dtype is not None else mesh.dtype
+    if t.dtype != want:
+        raise TypeError(f"{name} must be {want}, got {t.dtype}")
+    n = 4 * mesh.K * mesh.S * (last if last is not None else mesh.Np)
+    if t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements [4][K][S][..], got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def wadg_project(mesh: MeshHandle, fq, Q, stream=None):
+    import torch
+    a = _check_field(mesh, fq, "fq", torch.float64, mesh.Nq)
+    b = _check_field(mesh, Q, "Q")
+    _check(load().wadg_project(mesh.handle, a, b, _stream(stream)), "wadg_project", mesh)
+
+
+def wadg_rhs(mesh: MeshHandle, Q, dQdt, stream=None):
+    a = _check_field(mesh, Q, "Q")
+    b = _check_field(mesh, dQdt, "dQdt")
+    _check(load().wadg_rhs(mesh.handle, a, b, _stream(stream)), "wadg_rhs", mesh)
+
+
+def wadg_step(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, traces=None, stream=None):
+    a = _check_field(mesh, Q, "Q")
+    b = _check_field(mesh, res, "res")
+    tr = None
+    if traces is not None:
+        if traces.dtype != mesh.dtype or not traces.is_cuda or traces.numel() < nsteps * mesh.S * mesh.R:
+            raise ValueError("traces must be a CUDA tensor of nsteps*S*R values in the mesh precision")
+        tr = ctypes.c_void_p(traces.data_ptr())
+    _check(load().wadg_step(mesh.handle, a, b, float(t0), float(dt), int(nsteps), tr, _stream(stream)),
+           "wadg_step", mesh)
+
+
+def wadg_set_sources(mesh: MeshHandle, xyz, f0: float = 5.0, t0: float | None = None):
+    if xyz is None:
+        _check(load().wadg_set_sources(mesh.handle, None, float(f0), 0.0), "wadg_set_sources", mesh)
+        return
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(mesh.S, 3)
+    t0 = 1.2 / f0 if t0 is None else t0
+    _check(load().wadg_set_sources(mesh.handle, _dptr(x), float(f0), float(t0)), "wadg_set_sources", mesh)
+
+
+def wadg_set_receivers(mesh: MeshHandle, xyz):
+    if xyz is None:
+        _check(load().wadg_set_receivers(mesh.handle, 0, None), "wadg_set_receivers", mesh)
+        mesh.R = 0
+        return
+    x = np.ascontiguousarray(xyz, dtype=np.float64)
+    R = x.shape[-2]
+    x = x.reshape(mesh.S, R, 3)
+    _check(load().wadg_set_receivers(mesh.handle, int(R), _dptr(x)), "wadg_set_receivers", mesh)
+    mesh.R = int(R)
+
+
+def wadg_energy(mesh: MeshHandle, Q, stream=None) -> float:
+    a = _check_field(mesh, Q, "Q")
+    E = ctypes.c_double()
+    _check(load().wadg_energy(mesh.handle, a, ctypes.byref(E), _stream(stream)), "wadg_energy", mesh)
+    return E.value
+
+
+def wadg_l2_error(mesh: MeshHandle, Q, exact_q, field_mask: int = 1, stream=None) -> float:
+    import torch
+    a = _check_field(mesh, Q, "Q")
+    b = _check_field(mesh, exact_q, "exact_q", torch.float64, mesh.Nq)
+    e = ctypes.c_double()
+    _check(load().wadg_l2_error(mesh.handle, a, b, int(field_mask), ctypes.byref(e), _stream(stream)),
+           "wadg_l2_error", mesh)
+    return e.value
+
+
+def wadg_mesh_destroy(mesh: MeshHandle):
+    if mesh.handle:
+        load().wadg_mesh_destroy(mesh.handle)
+        mesh.handle = None
+
+
+def wadg_status_string(status: int) -> str:
+    return load().wadg_status_string(int(status)).decode()
+
+
+def wadg_last_error(mesh: MeshHandle) -> str:
+    return (load().wadg_last_error(mesh.handle) or b"").decode()

@@ -1,0 +1,311 @@
+// FP64 set-up and diagnostic kernels: geometric factors of the isoparametric
+// map, the weight-adjusted pseudo-projection, the energy and L2 error
+// reductions, and the receiver samples.
+#include <cstdint>
+
+#include "aux_kernels.h"
+
+namespace wadg {
+
+// ---------------------------------------------------------------------------
+// Volume geometric factors (Sec. 4.1): with A_a = dx/dx^_a,
+//   J = A_0 . (A_1 x A_2),  G_a = A_b x A_c for cyclic (a,b,c),
+// so that G_ai = J dx^_a/dx_i; G and J are polynomial for an isoparametric
+// map.  One block per element, threads over quadrature points.
+// ---------------------------------------------------------------------------
+__global__ void geo_volume_kernel(int64_t K, int Np, int Nq, const double* __restrict__ X,
+                                  const double* __restrict__ Vq, const double* __restrict__ Vqa,
+                                  double* __restrict__ J, double* __restrict__ G, double* __restrict__ xq,
+                                  int* __restrict__ nbad) {
+  extern __shared__ double sXk[];  // [Np][3]
+  const int64_t k = blockIdx.x;
+  for (int i = threadIdx.x; i < 3 * Np; i += blockDim.x) sXk[i] = X[k * 3 * Np + i];
+  __syncthreads();
+  for (int q = threadIdx.x; q < Nq; q += blockDim.x) {
+    double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // A[a][i]
+    double x[3] = {0, 0, 0};
+    for (int n = 0; n < Np; ++n) {
+      const double v = Vq[q * Np + n];
+      const double d0 = Vqa[(0 * Nq + q) * Np + n];
+      const double d1 = Vqa[(1 * Nq + q) * Np + n];
+      const double d2 = Vqa[(2 * Nq + q) * Np + n];
+      for (int i = 0; i < 3; ++i) {
+        const double xi = sXk[n * 3 + i];
+        x[i] += v * xi;
+        A[0][i] += d0 * xi;
+        A[1][i] += d1 * xi;
+        A[2][i] += d2 * xi;
+      }
+    }
+    double Gm[3][3];
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, c = (a + 2) % 3;
+      Gm[a][0] = A[b][1] * A[c][2] - A[b][2] * A[c][1];
+      Gm[a][1] = A[b][2] * A[c][0] - A[b][0] * A[c][2];
+      Gm[a][2] = A[b][0] * A[c][1] - A[b][1] * A[c][0];
+    }
+    const double Jq = A[0][0] * Gm[0][0] + A[0][1] * Gm[0][1] + A[0][2] * Gm[0][2];
+    J[k * Nq + q] = Jq;
+    if (!(Jq > 0.0)) atomicAdd(nbad, 1);
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < 3; ++i) G[(k * 9 + a * 3 + i) * Nq + q] = Gm[a][i];
+    for (int i = 0; i < 3; ++i) xq[(k * Nq + q) * 3 + i] = x[i];
+  }
+}
+
+// Face normals times surface Jacobian at the owner's face points, by
+// Nanson's formula n J^f = sum_a G_ai (n^ |f^|)_a.  Owner faces only.
+__global__ void geo_face_owner_kernel(int64_t K, int Np, int Nfq, const double* __restrict__ X,
+                                      const double* __restrict__ Vfa, const uint8_t* __restrict__ owner,
+                                      double* __restrict__ nJ) {
+  extern __shared__ double sXk[];
+  const int64_t k = blockIdx.x;
+  for (int i = threadIdx.x; i < 3 * Np; i += blockDim.x) sXk[i] = X[k * 3 * Np + i];
+  __syncthreads();
+  const double nref[4][3] = {{0, 0, -1}, {0, -1, 0}, {1, 1, 1}, {-1, 0, 0}};
+  for (int it = threadIdx.x; it < 4 * Nfq; it += blockDim.x) {
+    const int f = it / Nfq, q = it % Nfq;
+    if (!owner[k * 4 + f]) continue;
+    double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int n = 0; n < Np; ++n)
+      for (int a = 0; a < 3; ++a) {
+        const double d = Vfa[((f * 3 + a) * Nfq + q) * Np + n];
+        for (int i = 0; i < 3; ++i) A[a][i] += d * sXk[n * 3 + i];
+      }
+    double out[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, c = (a + 2) % 3;
+      const double g0 = A[b][1] * A[c][2] - A[b][2] * A[c][1];
+      const double g1 = A[b][2] * A[c][0] - A[b][0] * A[c][2];
+      const double g2 = A[b][0] * A[c][1] - A[b][1] * A[c][0];
+      out[0] += g0 * nref[f][a];
+      out[1] += g1 * nref[f][a];
+      out[2] += g2 * nref[f][a];
+    }
+    for (int i = 0; i < 3; ++i) nJ[(k * 3 + i) * 4 * Nfq + f * Nfq + q] = out[i];
+  }
+}
+
+// Non-owner faces take the owner's values with the sign flipped: both sides
+// use the same physical points in the same (owner) order.
+__global__ void geo_face_copy_kernel(int64_t K, int Nfq, const int32_t* __restrict__ EToE,
+                                     const int32_t* __restrict__ EToF, const uint8_t* __restrict__ owner,
+                                     double* __restrict__ nJ) {
+  const int64_t total = K * 4 * Nfq;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < total; it += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(it % Nfq);
+    const int f = (int)((it / Nfq) % 4);
+    const int64_t k = it / (4 * Nfq);
+    if (owner[k * 4 + f]) continue;
+    const int64_t ko = EToE[k * 4 + f];
+    const int fo = EToF[k * 4 + f];
+    for (int i = 0; i < 3; ++i) nJ[(k * 3 + i) * 4 * Nfq + f * Nfq + q] = -nJ[(ko * 3 + i) * 4 * Nfq + fo * Nfq + q];
+  }
+}
+
+template <typename T>
+__global__ void geo_pack_kernel(int64_t K, int Nq, int Nfq, const double* __restrict__ J, const double* __restrict__ G,
+                                const double* __restrict__ c2, const double* __restrict__ nJ, T* __restrict__ vgeo,
+                                T* __restrict__ fgeo) {
+  const int64_t nv = K * Nq, nf = K * 3 * 4 * Nfq;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nv + nf; it += (int64_t)gridDim.x * blockDim.x) {
+    if (it < nv) {
+      const int64_t k = it / Nq;
+      const int q = (int)(it % Nq);
+      const double Jq = J[it];
+      for (int c = 0; c < 9; ++c) vgeo[(k * 11 + c) * Nq + q] = (T)G[(k * 9 + c) * Nq + q];
+      vgeo[(k * 11 + 9) * Nq + q] = (T)((c2 ? c2[it] : 1.0) / Jq);
+      vgeo[(k * 11 + 10) * Nq + q] = (T)(1.0 / Jq);
+    } else {
+      const int64_t j = it - nv;
+      fgeo[j] = (T)nJ[j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pseudo-projection P_N u = Pi_N(J^{-1} Pi_N(u J)) (Sec. 3, Theorem), with
+// Pi_N g = P_q g_q.  One block per column, FP64 arithmetic.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void project_kernel(int64_t ncols, int S, int Np, int Nq, const double* __restrict__ fq,
+                               const double* __restrict__ J, const double* __restrict__ Vq, const double* __restrict__ Pq,
+                               T* __restrict__ Q) {
+  extern __shared__ double sm[];
+  double* g = sm;        // [Nq]
+  double* c1 = sm + Nq;  // [Np]
+  const int64_t c = blockIdx.x;
+  const int fld = blockIdx.y;
+  const int64_t k = c / S;
+  const double* Jk = J + k * Nq;
+  for (int q = threadIdx.x; q < Nq; q += blockDim.x) g[q] = fq[(fld * ncols + c) * Nq + q] * Jk[q];
+  __syncthreads();
+  for (int n = threadIdx.x; n < Np; n += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < Nq; ++q) acc += Pq[n * Nq + q] * g[q];
+    c1[n] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < Nq; q += blockDim.x) {
+    double acc = 0.0;
+    for (int n = 0; n < Np; ++n) acc += Vq[q * Np + n] * c1[n];
+    g[q] = acc / Jk[q];
+  }
+  __syncthreads();
+  for (int n = threadIdx.x; n < Np; n += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < Nq; ++q) acc += Pq[n * Nq + q] * g[q];
+    Q[(fld * ncols + c) * Np + n] = (T)acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions.  mode 0: energy 1/2 sum w (p^2 J/c^2 + |u|^2 J);
+// mode 1: squared L2 error of the fields in mask against exact values.
+// One block per column; block partial sums, then a second pass on the host.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void reduce_kernel(int mode, int64_t ncols, int S, int Np, int Nq, const T* __restrict__ Q,
+                              const double* __restrict__ Vq, const double* __restrict__ wq, const double* __restrict__ J,
+                              const double* __restrict__ c2, const double* __restrict__ exact, int mask,
+                              double* __restrict__ partial) {
+  extern __shared__ double sm[];
+  double* qv = sm;            // [4][Np]
+  double* red = sm + 4 * Np;  // [blockDim]
+  const int64_t c = blockIdx.x;
+  const int64_t k = c / S;
+  for (int i = threadIdx.x; i < 4 * Np; i += blockDim.x) {
+    const int f = i / Np, n = i % Np;
+    qv[i] = (double)Q[(f * ncols + c) * Np + n];
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < Nq; q += blockDim.x) {
+    double v[4];
+    for (int f = 0; f < 4; ++f) {
+      double s = 0.0;
+      for (int n = 0; n < Np; ++n) s += Vq[q * Np + n] * qv[f * Np + n];
+      v[f] = s;
+    }
+    const double wJ = wq[q] * J[k * Nq + q];
+    if (mode == 0) {
+      const double cc = c2 ? c2[k * Nq + q] : 1.0;
+      acc += 0.5 * wJ * (v[0] * v[0] / cc + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+    } else {
+      for (int f = 0; f < 4; ++f)
+        if (mask & (1 << f)) {
+          const double d = v[f] - exact[(f * ncols + c) * Nq + q];
+          acc += wJ * d * d;
+        }
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[c] = red[0];
+}
+
+__global__ void sum_kernel(int64_t n, const double* __restrict__ in, double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += in[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// Receivers: trace[s][r] = sum_n l_n(x^_r) p_n of the receiver's column.
+template <typename T>
+__global__ void receiver_kernel(int64_t ncols, int S, int R, int Np, const T* __restrict__ Q,
+                                const int32_t* __restrict__ rec_col, const T* __restrict__ rec_vec, T* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S * R) return;
+  const int64_t c = rec_col[i];
+  T acc = 0;
+  for (int n = 0; n < Np; ++n) acc += rec_vec[(int64_t)i * Np + n] * Q[c * Np + n];
+  out[i] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_geo_volume(int64_t K, int Np, int Nq, const double* X, const double* Vq, const double* Vqa, double* J,
+                              double* G, double* xq, int* nbad, cudaStream_t st) {
+  geo_volume_kernel<<<(unsigned)K, 128, 3 * Np * sizeof(double), st>>>(K, Np, Nq, X, Vq, Vqa, J, G, xq, nbad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_geo_face(int64_t K, int Np, int Nfq, const double* X, const double* Vfa, const uint8_t* owner,
+                            const int32_t* EToE, const int32_t* EToF, double* nJ, cudaStream_t st) {
+  geo_face_owner_kernel<<<(unsigned)K, 128, 3 * Np * sizeof(double), st>>>(K, Np, Nfq, X, Vfa, owner, nJ);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  geo_face_copy_kernel<<<1024, 256, 0, st>>>(K, Nfq, EToE, EToF, owner, nJ);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_geo_pack(int64_t K, int Nq, int Nfq, const double* J, const double* G, const double* c2,
+                            const double* nJ, T* vgeo, T* fgeo, cudaStream_t st) {
+  geo_pack_kernel<T><<<2048, 256, 0, st>>>(K, Nq, Nfq, J, G, c2, nJ, vgeo, fgeo);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_project(int64_t ncols, int S, int Np, int Nq, const double* fq, const double* J, const double* Vq,
+                           const double* Pq, T* Q, cudaStream_t st) {
+  if (ncols == 0) return cudaSuccess;
+  dim3 grid((unsigned)ncols, 4);
+  project_kernel<T><<<grid, 128, (Nq + Np) * sizeof(double), st>>>(ncols, S, Np, Nq, fq, J, Vq, Pq, Q);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reduce(int mode, int64_t ncols, int S, int Np, int Nq, const T* Q, const double* Vq, const double* wq,
+                          const double* J, const double* c2, const double* exact, int mask, double* partial, double* out,
+                          cudaStream_t st) {
+  if (ncols == 0) return cudaMemsetAsync(out, 0, sizeof(double), st);
+  reduce_kernel<T><<<(unsigned)ncols, 128, (4 * Np + 128) * sizeof(double), st>>>(mode, ncols, S, Np, Nq, Q, Vq, wq, J,
+                                                                                   c2, exact, mask, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sum_kernel<<<1, 256, 0, st>>>(ncols, partial, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_receivers(int64_t ncols, int S, int R, int Np, const T* Q, const int32_t* rec_col, const T* rec_vec,
+                             T* out, cudaStream_t st) {
+  const int n = S * R;
+  if (n == 0) return cudaSuccess;
+  receiver_kernel<T><<<(n + 127) / 128, 128, 0, st>>>(ncols, S, R, Np, Q, rec_col, rec_vec, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_geo_pack<double>(int64_t, int, int, const double*, const double*, const double*,
+                                             const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_geo_pack<float>(int64_t, int, int, const double*, const double*, const double*,
+                                            const double*, float*, float*, cudaStream_t);
+template cudaError_t launch_project<double>(int64_t, int, int, int, const double*, const double*, const double*,
+                                            const double*, double*, cudaStream_t);
+template cudaError_t launch_project<float>(int64_t, int, int, int, const double*, const double*, const double*,
+                                           const double*, float*, cudaStream_t);
+template cudaError_t launch_reduce<double>(int, int64_t, int, int, int, const double*, const double*, const double*,
+                                           const double*, const double*, const double*, int, double*, double*,
+                                           cudaStream_t);
+template cudaError_t launch_reduce<float>(int, int64_t, int, int, int, const float*, const double*, const double*,
+                                          const double*, const double*, const double*, int, double*, double*,
+                                          cudaStream_t);
+template cudaError_t launch_receivers<double>(int64_t, int, int, int, const double*, const int32_t*, const double*,
+                                              double*, cudaStream_t);
+template cudaError_t launch_receivers<float>(int64_t, int, int, int, const float*, const int32_t*, const float*, float*,
+                                             cudaStream_t);
+
+}  // namespace wadg

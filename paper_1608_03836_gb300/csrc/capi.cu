@@ -1,0 +1,792 @@
+// C ABI of the WADG library (see include/wadg.h).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "aux_kernels.h"
+#include "wadg_internal.h"
+
+namespace wadg {
+
+template <typename T, int N>
+cudaError_t launch_stage_n(const StageParams<T>& p, int mode, cudaStream_t stream);
+
+template <typename T>
+cudaError_t launch_stage(int N, const StageParams<T>& p, int mode, cudaStream_t stream) {
+  switch (N) {
+    case 1: return launch_stage_n<T, 1>(p, mode, stream);
+    case 2: return launch_stage_n<T, 2>(p, mode, stream);
+    case 3: return launch_stage_n<T, 3>(p, mode, stream);
+    case 4: return launch_stage_n<T, 4>(p, mode, stream);
+    case 5: return launch_stage_n<T, 5>(p, mode, stream);
+    case 6: return launch_stage_n<T, 6>(p, mode, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients
+// (the scheme named in Sec. 5.2 of the paper, which does not print them).
+static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+static const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                               2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+static const int kFaceV[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+
+}  // namespace wadg
+
+using namespace wadg;
+
+namespace {
+
+int fail(wadg_mesh* m, int status, const char* fmt, ...) {
+  if (m) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    m->last_error = buf;
+  }
+  return status;
+}
+
+int cuda_fail(wadg_mesh* m, cudaError_t e, const char* where) {
+  return fail(m, e == cudaErrorMemoryAllocation ? WADG_ENOMEM : WADG_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define WADG_CUDA(m, call)                                  \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return cuda_fail((m), _e, #call); \
+  } while (0)
+
+// Runs a body with the mesh's device current, restoring the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = (cudaSetDevice(dev) == cudaSuccess);
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+size_t tsize(int precision) { return precision == WADG_FP64 ? sizeof(double) : sizeof(float); }
+
+// Upload the k-major operator tables in precision T.
+template <typename T>
+int upload_ops(wadg_mesh* m, DevOps<T>& ops) {
+  const RefOps& o = m->ref;
+  const int Np = o.Np, Nq = o.Nq, Nfp = o.Nfp, Nfq = o.Nfq;
+  std::vector<T> h;
+  auto push = [&](size_t n) {
+    size_t off = h.size();
+    h.resize(off + ((n + 31) / 32) * 32, T(0));
+    return off;
+  };
+  size_t oVq = push((size_t)Np * Nq), oVa = push(3 * (size_t)Np * Nq), oDw = push(3 * (size_t)Nq * Np),
+         oVw = push((size_t)Nq * Np), oVt = push((size_t)Np * Nq), oPq = push((size_t)Nq * Np),
+         oVtri = push((size_t)Nfp * Nfq), oVtriTw = push((size_t)Nfq * Nfp);
+  for (int n = 0; n < Np; ++n)
+    for (int q = 0; q < Nq; ++q) {
+      h[oVq + n * Nq + q] = (T)o.Vq[q * Np + n];
+      for (int a = 0; a < 3; ++a) h[oVa + (a * Np + n) * Nq + q] = (T)o.Vqa[(a * Nq + q) * Np + n];
+      for (int a = 0; a < 3; ++a) h[oDw + (a * Nq + q) * Np + n] = (T)o.Dw[(a * Np + n) * Nq + q];
+      h[oVw + q * Np + n] = (T)o.Vw[n * Nq + q];
+      h[oVt + n * Nq + q] = (T)o.Vtilde[q * Np + n];
+      h[oPq + q * Np + n] = (T)o.Pq[n * Nq + q];
+    }
+  for (int j = 0; j < Nfp; ++j)
+    for (int q = 0; q < Nfq; ++q) {
+      h[oVtri + j * Nfq + q] = (T)o.Vtri[q * Nfp + j];
+      h[oVtriTw + q * Nfp + j] = (T)o.VtriTw[j * Nfq + q];
+    }
+  std::vector<int16_t> hi(4 * 6 * Nfp + 4 * 6 * Np);
+  for (int i = 0; i < 4 * 6 * Nfp; ++i) hi[i] = (int16_t)o.gidx[i];
+  for (int i = 0; i < 4 * 6 * Np; ++i) hi[4 * 6 * Nfp + i] = (int16_t)o.ginv[i];
+  size_t bytes_t = h.size() * sizeof(T);
+  size_t bytes = bytes_t + hi.size() * sizeof(int16_t);
+  void* base = nullptr;
+  WADG_CUDA(m, cudaMalloc(&base, bytes));
+  WADG_CUDA(m, cudaMemcpy(base, h.data(), bytes_t, cudaMemcpyHostToDevice));
+  WADG_CUDA(m, cudaMemcpy((char*)base + bytes_t, hi.data(), hi.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+  T* b = (T*)base;
+  ops.base = base;
+  ops.VqT = b + oVq;
+  ops.VaT = b + oVa;
+  ops.DwT = b + oDw;
+  ops.VwT = b + oVw;
+  ops.VtT = b + oVt;
+  ops.PqT = b + oPq;
+  ops.VtriT = b + oVtri;
+  ops.VtriTwT = b + oVtriTw;
+  ops.gidx = (const int16_t*)((char*)base + bytes_t);
+  ops.ginv = ops.gidx + 4 * 6 * Nfp;
+  return WADG_OK;
+}
+
+// Locate a physical point: element index and reference coordinates.  Among
+// the elements whose node bounding box holds the point, Newton's method on
+// x_h(x^) = x; the element where the point is most interior wins.
+bool locate(const wadg_mesh* m, const double* x, int64_t& kout, double* rst) {
+  const RefOps& o = m->ref;
+  const int Np = o.Np;
+  double best = -1e300;
+  std::vector<double> vals(Np), grads(3 * Np);
+  for (int64_t k = 0; k < m->K; ++k) {
+    const double* X = &m->geom[(size_t)k * Np * 3];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int n = 0; n < Np; ++n)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], X[n * 3 + d]);
+        hi[d] = std::max(hi[d], X[n * 3 + d]);
+      }
+    bool in = true;
+    for (int d = 0; d < 3; ++d) {
+      double pad = 0.05 * (hi[d] - lo[d]) + 1e-12;
+      if (x[d] < lo[d] - pad || x[d] > hi[d] + pad) in = false;
+    }
+    if (!in) continue;
+    double r[3] = {-0.5, -0.5, -0.5};
+    bool ok = false;
+    for (int it = 0; it < 50; ++it) {
+      lattice_basis(o, 1, &r[0], &r[1], &r[2], vals.data(), grads.data());
+      double F[3] = {-x[0], -x[1], -x[2]}, A[3][3] = {{0}};
+      for (int n = 0; n < Np; ++n)
+        for (int i = 0; i < 3; ++i) {
+          F[i] += vals[n] * X[n * 3 + i];
+          for (int a = 0; a < 3; ++a) A[i][a] += grads[a * Np + n] * X[n * 3 + i];
+        }
+      double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                   A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+      if (std::fabs(det) < 1e-300) break;
+      double inv[3][3];
+      inv[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / det;
+      inv[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / det;
+      inv[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / det;
+      inv[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / det;
+      inv[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / det;
+      inv[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / det;
+      inv[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / det;
+      inv[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / det;
+      inv[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / det;
+      double step = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double d = inv[a][0] * F[0] + inv[a][1] * F[1] + inv[a][2] * F[2];
+        r[a] -= d;
+        step = std::max(step, std::fabs(d));
+      }
+      if (std::fabs(r[0]) > 10 || std::fabs(r[1]) > 10 || std::fabs(r[2]) > 10) break;
+      if (step < 1e-14) {
+        ok = true;
+        break;
+      }
+    }
+    if (!ok) continue;
+    // interior measure: smallest barycentric coordinate
+    double lam = std::min(std::min((1 + r[0]) / 2, (1 + r[1]) / 2), std::min((1 + r[2]) / 2, -(1 + r[0] + r[1] + r[2]) / 2));
+    if (lam > best && lam > -1e-10) {
+      best = lam;
+      kout = k;
+      rst[0] = r[0];
+      rst[1] = r[1];
+      rst[2] = r[2];
+    }
+  }
+  return best > -1e-10;
+}
+
+template <typename T>
+int set_points(wadg_mesh* m, int count, const double* xyz, int64_t* elem_out, std::vector<T>& vec) {
+  const int Np = m->ref.Np;
+  vec.assign((size_t)count * Np, T(0));
+  std::vector<double> vals(Np);
+  for (int i = 0; i < count; ++i) {
+    int64_t k = -1;
+    double rst[3];
+    if (!locate(m, xyz + 3 * i, k, rst))
+      return fail(m, WADG_EINVAL, "point %d (%g, %g, %g) is not inside the mesh", i, xyz[3 * i], xyz[3 * i + 1],
+                  xyz[3 * i + 2]);
+    lattice_basis(m->ref, 1, &rst[0], &rst[1], &rst[2], vals.data(), nullptr);
+    for (int n = 0; n < Np; ++n) vec[(size_t)i * Np + n] = (T)vals[n];
+    elem_out[i] = k;
+  }
+  return WADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wadg_version(void) { return 100; }
+
+const char* wadg_status_string(int status) {
+  switch (status) {
+    case WADG_OK: return "ok";
+    case WADG_EINVAL: return "invalid argument";
+    case WADG_ENOMEM: return "out of memory";
+    case WADG_ECUDA: return "CUDA error";
+    case WADG_EGEOM: return "invalid geometry";
+    case WADG_ESTATE: return "invalid call order";
+    case WADG_ETIMEOUT: return "device wait timed out";
+    case WADG_EUNSTABLE: return "non-finite energy";
+    case WADG_EUNSUPPORTED: return "unsupported order or precision";
+    default: return "unknown status";
+  }
+}
+
+const char* wadg_last_error(const wadg_mesh* m) { return m ? m->last_error.c_str() : ""; }
+
+int wadg_reference_rules(int N, double* rst_q, double* w_q, double* rs_f, double* w_f) {
+  RefOps o;
+  char err[256];
+  if (!build_refops(N, o, err, sizeof(err))) return WADG_EUNSUPPORTED;
+  for (int q = 0; q < o.Nq; ++q) {
+    if (rst_q) {
+      rst_q[3 * q] = o.rq[q];
+      rst_q[3 * q + 1] = o.sq[q];
+      rst_q[3 * q + 2] = o.tq[q];
+    }
+    if (w_q) w_q[q] = o.wq[q];
+  }
+  for (int q = 0; q < o.Nfq; ++q) {
+    if (rs_f) {
+      rs_f[2 * q] = o.rf[q];
+      rs_f[2 * q + 1] = o.sf[q];
+    }
+    if (w_f) w_f[q] = o.wf[q];
+  }
+  return WADG_OK;
+}
+
+void wadg_mesh_destroy(wadg_mesh* m) {
+  if (!m) return;
+  DeviceGuard g(m->device);
+  dfree(m->d_X);
+  dfree(m->d_J);
+  dfree(m->d_G);
+  dfree(m->d_nJ);
+  dfree(m->d_xq);
+  dfree(m->d_c2);
+  dfree(m->d_EToE);
+  dfree(m->d_fcode);
+  dfree(m->d_owner);
+  dfree(m->d_ref64);
+  dfree(m->d_vgeo);
+  dfree(m->d_fgeo);
+  if (m->ops64.base) cudaFree(m->ops64.base);
+  if (m->ops32.base) cudaFree(m->ops32.base);
+  dfree(m->d_Qtmp);
+  dfree(m->d_red);
+  dfree(m->d_src_elem);
+  dfree(m->d_src_vec);
+  dfree(m->d_rec_col);
+  dfree(m->d_rec_vec);
+  delete m;
+}
+
+int wadg_mesh_create(int N, int64_t Nv, const double* VXYZ, int64_t K, const int64_t* EToV, const double* geom_xyz,
+                     wadg_mesh** out) {
+  if (!out) return WADG_EINVAL;
+  *out = nullptr;
+  if (N < 1 || N > 6) return WADG_EUNSUPPORTED;
+  if (Nv < 4 || K < 1 || K > (int64_t)1 << 30 || !VXYZ || !EToV) return WADG_EINVAL;
+  wadg_mesh* m = new (std::nothrow) wadg_mesh();
+  if (!m) return WADG_ENOMEM;
+  char err[256];
+  if (!build_refops(N, m->ref, err, sizeof(err))) {
+    delete m;
+    return WADG_EUNSUPPORTED;
+  }
+  cudaGetDevice(&m->device);
+  m->N = N;
+  m->K = K;
+  const RefOps& o = m->ref;
+  const int Np = o.Np, Nq = o.Nq, Nfq = o.Nfq;
+
+  auto bail = [&](int st) {
+    // keep the message for the caller: copy into a static buffer is not
+    // possible without a mesh, so the mesh is returned only on success.
+    wadg_mesh_destroy(m);
+    return st;
+  };
+
+  // vertex indices and orientation
+  for (int64_t k = 0; k < K; ++k) {
+    const int64_t* v = EToV + 4 * k;
+    for (int i = 0; i < 4; ++i)
+      if (v[i] < 0 || v[i] >= Nv) return bail(WADG_EINVAL);
+    double a[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int d = 0; d < 3; ++d) a[i][d] = VXYZ[3 * v[i + 1] + d] - VXYZ[3 * v[0] + d];
+    double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                 a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+    if (!(det > 0)) return bail(WADG_EGEOM);
+  }
+
+  // connectivity: sort faces by their vertex triple
+  struct FaceRec {
+    int64_t a, b, c;
+    int64_t k;
+    int f;
+  };
+  std::vector<FaceRec> faces((size_t)K * 4);
+  for (int64_t k = 0; k < K; ++k)
+    for (int f = 0; f < 4; ++f) {
+      int64_t v[3] = {EToV[4 * k + kFaceV[f][0]], EToV[4 * k + kFaceV[f][1]], EToV[4 * k + kFaceV[f][2]]};
+      std::sort(v, v + 3);
+      faces[k * 4 + f] = {v[0], v[1], v[2], k, f};
+    }
+  std::sort(faces.begin(), faces.end(), [](const FaceRec& x, const FaceRec& y) {
+    if (x.a != y.a) return x.a < y.a;
+    if (x.b != y.b) return x.b < y.b;
+    if (x.c != y.c) return x.c < y.c;
+    return x.k < y.k;
+  });
+  m->EToE.assign(K * 4, -1);
+  m->EToF.assign(K * 4, -1);
+  for (size_t i = 0; i < faces.size();) {
+    size_t j = i + 1;
+    while (j < faces.size() && faces[j].a == faces[i].a && faces[j].b == faces[i].b && faces[j].c == faces[i].c) ++j;
+    if (j - i > 2) return bail(WADG_EGEOM);
+    if (j - i == 2) {
+      const FaceRec &x = faces[i], &y = faces[i + 1];
+      if (x.k == y.k) return bail(WADG_EGEOM);
+      m->EToE[x.k * 4 + x.f] = (int32_t)y.k;
+      m->EToF[x.k * 4 + x.f] = y.f;
+      m->EToE[y.k * 4 + y.f] = (int32_t)x.k;
+      m->EToF[y.k * 4 + y.f] = x.f;
+    }
+    i = j;
+  }
+  // owners and permutation codes
+  m->fcode.assign(K * 4, 0);
+  m->owner.assign(K * 4, 0);
+  auto perm_of = [&](int64_t k, int f, int64_t ko, int fo) {
+    int64_t mine[3], theirs[3];
+    for (int s = 0; s < 3; ++s) {
+      mine[s] = EToV[4 * k + kFaceV[f][s]];
+      theirs[s] = EToV[4 * ko + kFaceV[fo][s]];
+    }
+    int sig[3];
+    for (int s = 0; s < 3; ++s)
+      for (int t = 0; t < 3; ++t)
+        if (theirs[t] == mine[s]) sig[s] = t;
+    for (int pi = 0; pi < 6; ++pi)
+      if (kPerm[pi][0] == sig[0] && kPerm[pi][1] == sig[1] && kPerm[pi][2] == sig[2]) return pi;
+    return -1;
+  };
+  for (int64_t k = 0; k < K; ++k)
+    for (int f = 0; f < 4; ++f) {
+      const int64_t kn = m->EToE[k * 4 + f];
+      const int fn = m->EToF[k * 4 + f];
+      if (kn < 0) {
+        m->owner[k * 4 + f] = 1;
+        m->fcode[k * 4 + f] = 0;
+        continue;
+      }
+      const bool own = k < kn;
+      m->owner[k * 4 + f] = own ? 1 : 0;
+      const int64_t ko = own ? k : kn;
+      const int fo = own ? f : fn;
+      int pio = perm_of(k, f, ko, fo), pin = perm_of(kn, fn, ko, fo);
+      if (pio < 0 || pin < 0) return bail(WADG_EGEOM);
+      m->fcode[k * 4 + f] = (uint8_t)(pio + 6 * (pin + 6 * fn));
+    }
+
+  // geometry nodes (affine lattice map when none are given)
+  m->geom.resize((size_t)K * Np * 3);
+  if (geom_xyz) {
+    std::memcpy(m->geom.data(), geom_xyz, m->geom.size() * sizeof(double));
+  } else {
+    for (int64_t k = 0; k < K; ++k)
+      for (int n = 0; n < Np; ++n) {
+        double l[4] = {-(1 + o.r[n] + o.s[n] + o.t[n]) / 2, (1 + o.r[n]) / 2, (1 + o.s[n]) / 2, (1 + o.t[n]) / 2};
+        for (int d = 0; d < 3; ++d) {
+          double x = 0;
+          for (int v = 0; v < 4; ++v) x += l[v] * VXYZ[3 * EToV[4 * k + v] + d];
+          m->geom[((size_t)k * Np + n) * 3 + d] = x;
+        }
+      }
+  }
+
+  // device uploads
+  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
+  cudaError_t e;
+  if ((e = alloc((void**)&m->d_X, m->geom.size() * 8)) != cudaSuccess ||
+      (e = alloc((void**)&m->d_J, (size_t)K * Nq * 8)) != cudaSuccess ||
+      (e = alloc((void**)&m->d_G, (size_t)K * 9 * Nq * 8)) != cudaSuccess ||
+      (e = alloc((void**)&m->d_nJ, (size_t)K * 12 * Nfq * 8)) != cudaSuccess ||
+      (e = alloc((void**)&m->d_xq, (size_t)K * Nq * 3 * 8)) != cudaSuccess ||
+      (e = alloc((void**)&m->d_EToE, (size_t)K * 4 * 4)) != cudaSuccess ||
+      (e = alloc((void**)&m->d_fcode, (size_t)K * 4)) != cudaSuccess ||
+      (e = alloc((void**)&m->d_owner, (size_t)K * 4)) != cudaSuccess) {
+    return bail(e == cudaErrorMemoryAllocation ? WADG_ENOMEM : WADG_ECUDA);
+  }
+  // FP64 tables: Vq, Vqa, Pq, Vfa, wq
+  const size_t nVq = (size_t)Nq * Np, nVqa = 3 * nVq, nPq = nVq, nVfa = (size_t)4 * 3 * Nfq * Np;
+  std::vector<double> ref64(nVq + nVqa + nPq + nVfa + Nq);
+  std::copy(o.Vq.begin(), o.Vq.end(), ref64.begin());
+  std::copy(o.Vqa.begin(), o.Vqa.end(), ref64.begin() + nVq);
+  std::copy(o.Pq.begin(), o.Pq.end(), ref64.begin() + nVq + nVqa);
+  std::copy(o.Vfa.begin(), o.Vfa.end(), ref64.begin() + nVq + nVqa + nPq);
+  std::copy(o.wq.begin(), o.wq.end(), ref64.begin() + nVq + nVqa + nPq + nVfa);
+  if ((e = alloc((void**)&m->d_ref64, ref64.size() * 8)) != cudaSuccess) return bail(WADG_ENOMEM);
+  std::vector<int32_t> EToF32(m->EToF.begin(), m->EToF.end());
+  int32_t* d_EToF = nullptr;
+  int* d_nbad = nullptr;
+  if ((e = alloc((void**)&d_EToF, (size_t)K * 4 * 4)) != cudaSuccess) return bail(WADG_ENOMEM);
+  if ((e = alloc((void**)&d_nbad, sizeof(int))) != cudaSuccess) {
+    cudaFree(d_EToF);
+    return bail(WADG_ENOMEM);
+  }
+  int nbad = 0;
+  bool okc = cudaMemcpy(m->d_X, m->geom.data(), m->geom.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(m->d_ref64, ref64.data(), ref64.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(m->d_EToE, m->EToE.data(), (size_t)K * 16, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(d_EToF, EToF32.data(), (size_t)K * 16, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(m->d_fcode, m->fcode.data(), (size_t)K * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(m->d_owner, m->owner.data(), (size_t)K * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemset(d_nbad, 0, sizeof(int)) == cudaSuccess;
+  const double* dVq = m->d_ref64;
+  const double* dVqa = dVq + nVq;
+  const double* dVfa = dVq + nVq + nVqa + nPq;
+  okc = okc && launch_geo_volume(K, Np, Nq, m->d_X, dVq, dVqa, m->d_J, m->d_G, m->d_xq, d_nbad, 0) == cudaSuccess &&
+        launch_geo_face(K, Np, Nfq, m->d_X, dVfa, m->d_owner, m->d_EToE, d_EToF, m->d_nJ, 0) == cudaSuccess &&
+        cudaMemcpy(&nbad, d_nbad, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaFree(d_EToF);
+  cudaFree(d_nbad);
+  if (!okc) return bail(WADG_ECUDA);
+  if (nbad > 0) return bail(WADG_EGEOM);
+  *out = m;
+  return WADG_OK;
+}
+
+int wadg_mesh_info(const wadg_mesh* m, int64_t info[8]) {
+  if (!m || !info) return WADG_EINVAL;
+  info[0] = m->N;
+  info[1] = m->K;
+  info[2] = m->ref.Np;
+  info[3] = m->ref.Nq;
+  info[4] = m->ref.Nfp;
+  info[5] = m->ref.Nfq;
+  info[6] = m->S;
+  info[7] = m->precision;
+  return WADG_OK;
+}
+
+int wadg_volume_points(const wadg_mesh* m, double* xyz) {
+  if (!m || !xyz) return WADG_EINVAL;
+  DeviceGuard g(m->device);
+  cudaError_t e = cudaMemcpy(xyz, m->d_xq, (size_t)m->K * m->ref.Nq * 3 * 8, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? WADG_OK : WADG_ECUDA;
+}
+
+int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, double tau_u, const double* c2q) {
+  if (!m) return WADG_EINVAL;
+  if (precision != WADG_FP64 && precision != WADG_FP32)
+    return fail(m, WADG_EUNSUPPORTED, "precision %d is not built", precision);
+  if (shots < 1 || shots > (1 << 20)) return fail(m, WADG_EINVAL, "shots=%d", shots);
+  if (!(tau_p >= 0) || !(tau_u >= 0)) return fail(m, WADG_EINVAL, "penalties must be >= 0");
+  DeviceGuard g(m->device);
+  const int64_t K = m->K;
+  const int Nq = m->ref.Nq, Nfq = m->ref.Nfq, Np = m->ref.Np;
+  if (c2q) {
+    for (int64_t i = 0; i < K * Nq; ++i)
+      if (!(c2q[i] > 0) || !std::isfinite(c2q[i])) return fail(m, WADG_EINVAL, "c2q[%lld] = %g", (long long)i, c2q[i]);
+    if (!m->d_c2) WADG_CUDA(m, cudaMalloc(&m->d_c2, (size_t)K * Nq * 8));
+    WADG_CUDA(m, cudaMemcpy(m->d_c2, c2q, (size_t)K * Nq * 8, cudaMemcpyHostToDevice));
+  } else {
+    dfree(m->d_c2);
+  }
+  if (precision != m->precision) {
+    dfree(m->d_vgeo);
+    dfree(m->d_fgeo);
+  }
+  const size_t ts = tsize(precision);
+  if (!m->d_vgeo) WADG_CUDA(m, cudaMalloc(&m->d_vgeo, (size_t)K * 11 * Nq * ts));
+  if (!m->d_fgeo) WADG_CUDA(m, cudaMalloc(&m->d_fgeo, (size_t)K * 12 * Nfq * ts));
+  if (precision == WADG_FP64) {
+    WADG_CUDA(m, launch_geo_pack<double>(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, m->d_nJ, (double*)m->d_vgeo,
+                                         (double*)m->d_fgeo, 0));
+    if (!m->ops64.base) {
+      int st = upload_ops<double>(m, m->ops64);
+      if (st != WADG_OK) return st;
+    }
+  } else {
+    WADG_CUDA(m, launch_geo_pack<float>(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, m->d_nJ, (float*)m->d_vgeo,
+                                        (float*)m->d_fgeo, 0));
+    if (!m->ops32.base) {
+      int st = upload_ops<float>(m, m->ops32);
+      if (st != WADG_OK) return st;
+    }
+  }
+  const size_t qbytes = (size_t)4 * K * shots * Np * ts;
+  if (qbytes != m->qtmp_bytes) {
+    dfree(m->d_Qtmp);
+    dfree(m->d_red);
+    WADG_CUDA(m, cudaMalloc(&m->d_Qtmp, qbytes));
+    WADG_CUDA(m, cudaMalloc((void**)&m->d_red, ((size_t)K * shots + 1) * 8));
+    m->qtmp_bytes = qbytes;
+  }
+  if (shots != m->S || precision != m->precision) {
+    // sources and receivers depend on the shot count and precision
+    m->nsrc = 0;
+    m->R = 0;
+    dfree(m->d_src_elem);
+    dfree(m->d_src_vec);
+    dfree(m->d_rec_col);
+    dfree(m->d_rec_vec);
+  }
+  m->precision = precision;
+  m->S = shots;
+  m->tau_p = tau_p;
+  m->tau_u = tau_u;
+  WADG_CUDA(m, cudaDeviceSynchronize());
+  return WADG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+inline const DevOps<double>& ops_of(const wadg_mesh* m, double) { return m->ops64; }
+inline const DevOps<float>& ops_of(const wadg_mesh* m, float) { return m->ops32; }
+
+template <typename T>
+StageParams<T> base_params(const wadg_mesh* m) {
+  StageParams<T> p;
+  p.vgeo = (const T*)m->d_vgeo;
+  p.fgeo = (const T*)m->d_fgeo;
+  p.EToE = m->d_EToE;
+  p.fcode = m->d_fcode;
+  p.ops = ops_of(m, T());
+  p.ncols = m->K * m->S;
+  p.S = m->S;
+  p.tau_p = (T)m->tau_p;
+  p.tau_u = (T)m->tau_u;
+  return p;
+}
+
+int check_ready(wadg_mesh* m) {
+  if (!m) return WADG_EINVAL;
+  if (m->precision < 0) return fail(m, WADG_ESTATE, "wadg_set_operators has not been called");
+  return WADG_OK;
+}
+
+template <typename T>
+int rhs_t(wadg_mesh* m, const void* Q, void* dQdt, cudaStream_t st) {
+  StageParams<T> p = base_params<T>(m);
+  p.Qin = (const T*)Q;
+  p.out = (T*)dQdt;
+  cudaError_t e = launch_stage<T>(m->N, p, 0, st);
+  return e == cudaSuccess ? WADG_OK : cuda_fail(m, e, "stage kernel (rhs)");
+}
+
+double ricker(double t, double f0, double t0) {
+  const double pi = 3.14159265358979323846;
+  double a = pi * f0 * (t - t0);
+  a *= a;
+  return (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+template <typename T>
+int step_t(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, void* traces, cudaStream_t st) {
+  StageParams<T> p = base_params<T>(m);
+  p.res = (T*)res;
+  p.dt = (T)dt;
+  if (m->nsrc > 0) {
+    p.src_elem = m->d_src_elem;
+    p.src_vec = (const T*)m->d_src_vec;
+  }
+  T* cur = (T*)Q;
+  T* other = (T*)m->d_Qtmp;
+  const size_t bytes = (size_t)4 * m->K * m->S * m->ref.Np * sizeof(T);
+  for (int n = 0; n < nsteps; ++n) {
+    const double t = t0 + n * dt;
+    for (int s = 0; s < 5; ++s) {
+      p.Qin = cur;
+      p.Qout = other;
+      p.rk_a = (T)kRkA[s];
+      p.rk_b = (T)kRkB[s];
+      p.src_amp = (T)(m->nsrc > 0 ? ricker(t + kRkC[s] * dt, m->f0, m->t0) : 0.0);
+      cudaError_t e = launch_stage<T>(m->N, p, 1, st);
+      if (e != cudaSuccess) return cuda_fail(m, e, "stage kernel (lsrk)");
+      std::swap(cur, other);
+    }
+    if (traces && m->R > 0) {
+      cudaError_t e = launch_receivers<T>(m->K * m->S, m->S, m->R, m->ref.Np, cur, m->d_rec_col,
+                                          (const T*)m->d_rec_vec, (T*)traces + (size_t)n * m->S * m->R, st);
+      if (e != cudaSuccess) return cuda_fail(m, e, "receiver kernel");
+    }
+  }
+  if (cur != (T*)Q) {
+    cudaError_t e = cudaMemcpyAsync(Q, cur, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "copy back");
+  }
+  return WADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wadg_rhs(wadg_mesh* m, const void* Q, void* dQdt, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!Q || !dQdt || Q == dQdt || !aligned16(Q) || !aligned16(dQdt))
+    return fail(m, WADG_EINVAL, "Q and dQdt must be distinct 16-byte aligned device pointers");
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->precision == WADG_FP64 ? rhs_t<double>(m, Q, dQdt, s) : rhs_t<float>(m, Q, dQdt, s);
+}
+
+int wadg_step(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, void* traces, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!Q || !res || Q == res || !aligned16(Q) || !aligned16(res))
+    return fail(m, WADG_EINVAL, "Q and res must be distinct 16-byte aligned device pointers");
+  if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "nsteps/dt/t0");
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->precision == WADG_FP64 ? step_t<double>(m, Q, res, t0, dt, nsteps, traces, s)
+                                   : step_t<float>(m, Q, res, t0, dt, nsteps, traces, s);
+}
+
+int wadg_project(wadg_mesh* m, const double* fq, void* Q, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!fq || !Q) return fail(m, WADG_EINVAL, "null pointer");
+  DeviceGuard g(m->device);
+  const RefOps& o = m->ref;
+  const double* dVq = m->d_ref64;
+  const double* dPq = dVq + 4 * (size_t)o.Nq * o.Np;
+  cudaError_t e = m->precision == WADG_FP64
+                      ? launch_project<double>(m->K * m->S, m->S, o.Np, o.Nq, fq, m->d_J, dVq, dPq, (double*)Q,
+                                               (cudaStream_t)stream)
+                      : launch_project<float>(m->K * m->S, m->S, o.Np, o.Nq, fq, m->d_J, dVq, dPq, (float*)Q,
+                                              (cudaStream_t)stream);
+  return e == cudaSuccess ? WADG_OK : cuda_fail(m, e, "projection kernel");
+}
+
+static int reduce_common(wadg_mesh* m, int mode, const void* Q, const double* exact, int mask, double* outv,
+                         cudaStream_t s) {
+  const RefOps& o = m->ref;
+  const double* dVq = m->d_ref64;
+  const double* dwq = dVq + 4 * (size_t)o.Nq * o.Np + (size_t)o.Nq * o.Np + (size_t)4 * 3 * o.Nfq * o.Np;
+  double* partial = m->d_red;
+  double* out = m->d_red + m->K * m->S;
+  cudaError_t e = m->precision == WADG_FP64
+                      ? launch_reduce<double>(mode, m->K * m->S, m->S, o.Np, o.Nq, (const double*)Q, dVq, dwq, m->d_J,
+                                              m->d_c2, exact, mask, partial, out, s)
+                      : launch_reduce<float>(mode, m->K * m->S, m->S, o.Np, o.Nq, (const float*)Q, dVq, dwq, m->d_J,
+                                             m->d_c2, exact, mask, partial, out, s);
+  if (e != cudaSuccess) return cuda_fail(m, e, "reduction kernel");
+  e = cudaMemcpyAsync(outv, out, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(m, e, "reduction copy");
+  return WADG_OK;
+}
+
+int wadg_energy(wadg_mesh* m, const void* Q, double* E, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!Q || !E) return fail(m, WADG_EINVAL, "null pointer");
+  DeviceGuard g(m->device);
+  st = reduce_common(m, 0, Q, nullptr, 0, E, (cudaStream_t)stream);
+  if (st != WADG_OK) return st;
+  if (!std::isfinite(*E)) return fail(m, WADG_EUNSTABLE, "energy is %g", *E);
+  return WADG_OK;
+}
+
+int wadg_l2_error(wadg_mesh* m, const void* Q, const double* exact_q, int field_mask, double* err, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!Q || !exact_q || !err || field_mask <= 0 || field_mask > 15) return fail(m, WADG_EINVAL, "bad argument");
+  DeviceGuard g(m->device);
+  double sq = 0.0;
+  st = reduce_common(m, 1, Q, exact_q, field_mask, &sq, (cudaStream_t)stream);
+  if (st != WADG_OK) return st;
+  *err = std::sqrt(std::max(sq, 0.0));
+  return WADG_OK;
+}
+
+int wadg_set_sources(wadg_mesh* m, const double* xyz, double f0, double t0) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  DeviceGuard g(m->device);
+  dfree(m->d_src_elem);
+  dfree(m->d_src_vec);
+  m->nsrc = 0;
+  if (!xyz) return WADG_OK;
+  if (!(f0 > 0) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "f0 must be > 0");
+  const int S = m->S;
+  std::vector<int64_t> elem(S);
+  std::vector<int32_t> elem32(S);
+  const size_t ts = tsize(m->precision);
+  std::vector<double> v64;
+  std::vector<float> v32;
+  st = m->precision == WADG_FP64 ? set_points<double>(m, S, xyz, elem.data(), v64)
+                                 : set_points<float>(m, S, xyz, elem.data(), v32);
+  if (st != WADG_OK) return st;
+  for (int i = 0; i < S; ++i) elem32[i] = (int32_t)elem[i];
+  WADG_CUDA(m, cudaMalloc((void**)&m->d_src_elem, S * sizeof(int32_t)));
+  WADG_CUDA(m, cudaMalloc(&m->d_src_vec, (size_t)S * m->ref.Np * ts));
+  WADG_CUDA(m, cudaMemcpy(m->d_src_elem, elem32.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice));
+  WADG_CUDA(m, cudaMemcpy(m->d_src_vec, m->precision == WADG_FP64 ? (void*)v64.data() : (void*)v32.data(),
+                          (size_t)S * m->ref.Np * ts, cudaMemcpyHostToDevice));
+  m->nsrc = S;
+  m->f0 = f0;
+  m->t0 = t0;
+  return WADG_OK;
+}
+
+int wadg_set_receivers(wadg_mesh* m, int R, const double* xyz) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (R < 0 || (R > 0 && !xyz)) return fail(m, WADG_EINVAL, "R=%d", R);
+  DeviceGuard g(m->device);
+  dfree(m->d_rec_col);
+  dfree(m->d_rec_vec);
+  m->R = 0;
+  if (R == 0) return WADG_OK;
+  const int S = m->S, n = S * R;
+  std::vector<int64_t> elem(n);
+  std::vector<int32_t> col(n);
+  const size_t ts = tsize(m->precision);
+  std::vector<double> v64;
+  std::vector<float> v32;
+  st = m->precision == WADG_FP64 ? set_points<double>(m, n, xyz, elem.data(), v64)
+                                 : set_points<float>(m, n, xyz, elem.data(), v32);
+  if (st != WADG_OK) return st;
+  for (int i = 0; i < n; ++i) col[i] = (int32_t)(elem[i] * S + i / R);
+  WADG_CUDA(m, cudaMalloc((void**)&m->d_rec_col, n * sizeof(int32_t)));
+  WADG_CUDA(m, cudaMalloc(&m->d_rec_vec, (size_t)n * m->ref.Np * ts));
+  WADG_CUDA(m, cudaMemcpy(m->d_rec_col, col.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  WADG_CUDA(m, cudaMemcpy(m->d_rec_vec, m->precision == WADG_FP64 ? (void*)v64.data() : (void*)v32.data(),
+                          (size_t)n * m->ref.Np * ts, cudaMemcpyHostToDevice));
+  m->R = R;
+  return WADG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal types of the WADG library: the mesh object, device operator
+// tables and kernel parameter blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "refops.h"
+#include "wadg.h"
+
+namespace wadg {
+
+// Device copies of the reference operators in precision T, stored "k-major"
+// (A[k][m], consecutive output rows m contiguous) so that a warp of threads
+// owning consecutive output rows reads one coalesced line per k.
+template <typename T>
+struct DevOps {
+  const T* VqT = nullptr;     // [Np][Nq]     V_q
+  const T* VaT = nullptr;     // [3][Np][Nq]  V_q^a  (d/dr, d/ds, d/dt)
+  const T* DwT = nullptr;     // [3 Nq][Np]   (V_q^a)^T diag(w), a-major blocks
+  const T* VwT = nullptr;     // [Nq][Np]     V_q^T diag(w)
+  const T* VtT = nullptr;     // [Np][Nq]     V_q M^^{-1}
+  const T* PqT = nullptr;     // [Nq][Np]     M^^{-1} V_q^T diag(w)
+  const T* VtriT = nullptr;   // [Nfp][Nfq]   face interpolation
+  const T* VtriTwT = nullptr; // [Nfq][Nfp]   V_tri^T diag(w_f)
+  const int16_t* gidx = nullptr;  // [4][6][Nfp]
+  const int16_t* ginv = nullptr;  // [4][6][Np]
+  void* base = nullptr;       // single allocation holding all of the above
+};
+
+// Parameters of one fused stage launch (RHS + weight-adjusted update, and in
+// LSRK mode the Runge-Kutta update).
+template <typename T>
+struct StageParams {
+  const T* Qin = nullptr;   // [4][ncols][Np]
+  T* Qout = nullptr;        // LSRK: Q + b res; may not alias Qin
+  T* res = nullptr;         // LSRK: residual, read and written in place
+  T* out = nullptr;         // RHS mode: dQ/dt
+  const T* vgeo = nullptr;  // [K][11][Nq]: G_ai (a-major, 9), c^2/J, 1/J
+  const T* fgeo = nullptr;  // [K][3][4 Nfq]: n J^f at the owner face points
+  const int32_t* EToE = nullptr;  // [K][4], -1 on the boundary
+  const uint8_t* fcode = nullptr; // [K][4]: pi_own + 6 (pi_nbr + 6 f_nbr)
+  DevOps<T> ops;
+  int64_t ncols = 0;        // K * S
+  int S = 1;
+  T tau_p = 1, tau_u = 1;
+  T rk_a = 0, rk_b = 0, dt = 0;
+  // point sources, one per shot (src_elem < 0: none)
+  const int32_t* src_elem = nullptr;  // [S]
+  const T* src_vec = nullptr;         // [S][Np] l_n(x^_s)
+  T src_amp = 0;
+};
+
+// Launchers, one per (precision, degree); mode 0 = RHS, 1 = LSRK stage.
+template <typename T>
+cudaError_t launch_stage(int N, const StageParams<T>& p, int mode, cudaStream_t stream);
+
+}  // namespace wadg
+
+struct wadg_mesh {
+  int device = 0;
+  int N = 0;
+  int64_t K = 0;
+  wadg::RefOps ref;
+  // host connectivity
+  std::vector<int32_t> EToE;   // [K][4]
+  std::vector<int32_t> EToF;   // [K][4]
+  std::vector<uint8_t> fcode;  // [K][4]
+  std::vector<uint8_t> owner;  // [K][4] 1 if this element owns the face
+  std::vector<double> geom;    // [K][Np][3]
+  // device geometry (FP64)
+  double* d_X = nullptr;       // [K][Np][3]
+  double* d_J = nullptr;       // [K][Nq]
+  double* d_G = nullptr;       // [K][9][Nq]
+  double* d_nJ = nullptr;      // [K][3][4 Nfq]
+  double* d_xq = nullptr;      // [K][Nq][3]
+  double* d_c2 = nullptr;      // [K][Nq]
+  int32_t* d_EToE = nullptr;
+  uint8_t* d_fcode = nullptr;
+  uint8_t* d_owner = nullptr;
+  // FP64 operators (setup kernels, projection, diagnostics)
+  double* d_ref64 = nullptr;   // Vq [Nq][Np], Vqa [3][Nq][Np], Pq [Np][Nq], Vfa [4][3][Nfq][Np], wq [Nq]
+  // precision-dependent state
+  int precision = -1;
+  int S = -1;
+  double tau_p = 1.0, tau_u = 1.0;
+  void* d_vgeo = nullptr;
+  void* d_fgeo = nullptr;
+  wadg::DevOps<double> ops64;
+  wadg::DevOps<float> ops32;
+  void* d_Qtmp = nullptr;      // ping-pong buffer for LSRK stages
+  size_t qtmp_bytes = 0;
+  double* d_red = nullptr;     // reduction scratch
+  // sources and receivers
+  int nsrc = 0;
+  double f0 = 5.0, t0 = 0.24;
+  int32_t* d_src_elem = nullptr;
+  void* d_src_vec = nullptr;
+  int R = 0;
+  int32_t* d_rec_col = nullptr;   // [S][R] column index k*S+s
+  void* d_rec_vec = nullptr;      // [S][R][Np]
+  std::string last_error;
+};

@@ -1,0 +1,64 @@
+"""Shared helpers of the GPU parity tests: build the same seeded case for the
+CUDA library (through its C ABI) and for the FP64 oracle, and compare.
+
+Inputs come from the synthetic generators only; expected values come from
+the oracle only.  Nothing computed by the CUDA path is fed to the oracle.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from synthetic import warped_cube, c2_heterogeneous, random_fields
+
+# Parity bars (relative L2 over all compared values, and max-abs relative to
+# the largest expected value).  FP64: the target 1e-11.  FP32: unit roundoff
+# 6e-8 amplified by dot products of up to 3 Nq terms and the operator norms of
+# V_q^a / P_q (about 10^2 at N <= 6): 1e-5.
+TOL = {"fp64": 1e-11, "fp32": 1e-5}
+
+
+def make_mesh_inputs(n, N, amp=0.1):
+    return warped_cube(n, N, amp)
+
+
+def oracle_case(VXYZ, EToV, geom, N):
+    from oracle.discretization import Mesh, RefTet
+    ref = RefTet(N)
+    return Mesh(ref, VXYZ, EToV, geom)
+
+
+def library_mesh(VXYZ, EToV, geom, N, precision="fp64", shots=1, c2="one", tau=(1.0, 1.0)):
+    import paper_1608_03836_gb300 as W
+    m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
+    c2q = None
+    if c2 == "heterogeneous":
+        c2q = c2_heterogeneous(W.wadg_volume_points(m))
+    elif isinstance(c2, np.ndarray):
+        c2q = c2
+    W.wadg_set_operators(m, precision, shots, tau[0], tau[1], c2q)
+    return m
+
+
+def oracle_c2(omesh, c2):
+    if c2 == "one":
+        return None
+    if c2 == "heterogeneous":
+        return c2_heterogeneous(omesh.xq)
+    return c2
+
+
+def rel_errors(got, want):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    l2 = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300)
+    mx = np.abs(got - want).max() / max(np.abs(want).max(), 1e-300)
+    return l2, mx
+
+
+def to_torch(a, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def random_Q(K, S, Np, seed):
+    return random_fields((4, K, S, Np), seed)
