@@ -46,8 +46,26 @@ def _compile(nvcc, src, verbose):
     return obj, r.stderr
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
+def _arch_stamp():
+    """Object files are only reused on the machine type that made them."""
+    import platform
     os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "machine.txt")
+    here = platform.machine()
+    try:
+        old = open(stamp).read().strip()
+    except OSError:
+        old = None
+    if old != here:
+        for f in os.listdir(BUILD):
+            if f.endswith(".o"):
+                os.remove(os.path.join(BUILD, f))
+        with open(stamp, "w") as fh:
+            fh.write(here)
+
+
+def build(verbose: bool = False, jobs: int | None = None) -> str:
+    _arch_stamp()
     nvcc = _nvcc()
     srcs = sources()
     jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))

@@ -19,10 +19,11 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1608_03836_gb300 import build
-    if not os.path.exists(build.LIB):
-        build.build()
-    return ctypes.CDLL(build.LIB)
+    import __graft_entry__ as g
+    b = g._build_module()
+    if not os.path.exists(b.LIB):
+        b.build()
+    return ctypes.CDLL(b.LIB)
 
 
 def test_every_declared_symbol_is_exported(lib):
