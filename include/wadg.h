@@ -142,6 +142,22 @@ int wadg_set_receivers(wadg_mesh* mesh, int R, const double* xyz);
  * FP64 reduction; E is a host double.  WADG_EUNSTABLE if not finite. */
 int wadg_energy(wadg_mesh* mesh, const void* Q, double* E, wadg_stream stream);
 
+/* The energy of wadg_energy, computed without allocating anything.  The paper
+ * has no counterpart: this entry point serves callers that must not call
+ * cudaMalloc when they need the value -- code running while a stream is being
+ * captured into a CUDA graph, code inside a framework whose caching allocator
+ * owns the device memory budget, and real-time loops that must not wait on the
+ * driver's allocator.  Its scratch is a fixed array of 2^20 + 1 doubles
+ * (8 MiB) in device memory that every GPU loading the library holds until the
+ * process exits; a mesh with K*S > 2^20 columns is rejected with WADG_EINVAL.
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, so calls that
+ * overlap on the GPU (other streams, other host threads) race and return wrong
+ * values; every slot a call reads it writes first, so nothing needs clearing.
+ * Q, E, stream and the return codes are as for wadg_energy. */
+int wadg_energy_noalloc(wadg_mesh* mesh, const void* Q, double* E, wadg_stream stream);
+
 /* L2 error sqrt(sum_k int (q_h - q)^2) over the fields in field_mask (bit f for
  * field f) against exact values at the volume points, device [4][K][S][Nq]
  * FP64.  err is a host double. */

@@ -16,6 +16,7 @@ from .api import (  # noqa: E402,F401
     WADG_FP64,
     MeshHandle,
     wadg_energy,
+    wadg_energy_noalloc,
     wadg_l2_error,
     wadg_last_error,
     wadg_mesh_create,

@@ -25,6 +25,7 @@ SIGNATURES = {
     "wadg_set_sources": (c_int, [c_void_p, P_double, c_double, c_double]),
     "wadg_set_receivers": (c_int, [c_void_p, c_int, P_double]),
     "wadg_energy": (c_int, [c_void_p, c_void_p, P_double, c_void_p]),
+    "wadg_energy_noalloc": (c_int, [c_void_p, c_void_p, P_double, c_void_p]),
     "wadg_l2_error": (c_int, [c_void_p, c_void_p, c_void_p, c_int, P_double, c_void_p]),
     "wadg_mesh_destroy": (None, [c_void_p]),
     "wadg_status_string": (ctypes.c_char_p, [c_int]),

@@ -177,6 +177,15 @@ def wadg_energy(mesh: MeshHandle, Q, stream=None) -> float:
     return E.value
 
 
+def wadg_energy_noalloc(mesh: MeshHandle, Q, stream=None) -> float:
+    """wadg_energy without any allocation (fixed library scratch; see include/wadg.h)."""
+    a = _check_field(mesh, Q, "Q")
+    E = ctypes.c_double()
+    _check(load().wadg_energy_noalloc(mesh.handle, a, ctypes.byref(E), _stream(stream)), "wadg_energy_noalloc",
+           mesh)
+    return E.value
+
+
 def wadg_l2_error(mesh: MeshHandle, Q, exact_q, field_mask: int = 1, stream=None) -> float:
     import torch
     a = _check_field(mesh, Q, "Q")
