@@ -104,22 +104,25 @@ int upload_ops(wadg_mesh* m, DevOps<T>& ops) {
     h.resize(off + ((n + 31) / 32) * 32, T(0));
     return off;
   };
-  size_t oVq = push((size_t)Np * Nq), oVa = push(3 * (size_t)Np * Nq), oDw = push(3 * (size_t)Nq * Np),
-         oVw = push((size_t)Nq * Np), oVt = push((size_t)Np * Nq), oPq = push((size_t)Nq * Np),
-         oVtri = push((size_t)Nfp * Nfq), oVtriTw = push((size_t)Nfq * Nfp);
+  // Row counts padded to a multiple of 4 so that 4 rows load as one vector.
+  auto pad4 = [](int n) { return (n + 3) / 4 * 4; };
+  const int NQP = pad4(Nq), NPP = pad4(Np), NFQP = pad4(Nfq), NFPP = pad4(Nfp);
+  size_t oVq = push((size_t)Np * NQP), oVa = push(3 * (size_t)Np * NQP), oDw = push(3 * (size_t)Nq * NPP),
+         oVw = push((size_t)Nq * NPP), oVt = push((size_t)Np * NQP), oPq = push((size_t)Nq * NPP),
+         oVtri = push((size_t)Nfp * NFQP), oVtriTw = push((size_t)Nfq * NFPP);
   for (int n = 0; n < Np; ++n)
     for (int q = 0; q < Nq; ++q) {
-      h[oVq + n * Nq + q] = (T)o.Vq[q * Np + n];
-      for (int a = 0; a < 3; ++a) h[oVa + (a * Np + n) * Nq + q] = (T)o.Vqa[(a * Nq + q) * Np + n];
-      for (int a = 0; a < 3; ++a) h[oDw + (a * Nq + q) * Np + n] = (T)o.Dw[(a * Np + n) * Nq + q];
-      h[oVw + q * Np + n] = (T)o.Vw[n * Nq + q];
-      h[oVt + n * Nq + q] = (T)o.Vtilde[q * Np + n];
-      h[oPq + q * Np + n] = (T)o.Pq[n * Nq + q];
+      h[oVq + n * NQP + q] = (T)o.Vq[q * Np + n];
+      for (int a = 0; a < 3; ++a) h[oVa + (a * Np + n) * NQP + q] = (T)o.Vqa[(a * Nq + q) * Np + n];
+      for (int a = 0; a < 3; ++a) h[oDw + (a * Nq + q) * NPP + n] = (T)o.Dw[(a * Np + n) * Nq + q];
+      h[oVw + q * NPP + n] = (T)o.Vw[n * Nq + q];
+      h[oVt + n * NQP + q] = (T)o.Vtilde[q * Np + n];
+      h[oPq + q * NPP + n] = (T)o.Pq[n * Nq + q];
     }
   for (int j = 0; j < Nfp; ++j)
     for (int q = 0; q < Nfq; ++q) {
-      h[oVtri + j * Nfq + q] = (T)o.Vtri[q * Nfp + j];
-      h[oVtriTw + q * Nfp + j] = (T)o.VtriTw[j * Nfq + q];
+      h[oVtri + j * NFQP + q] = (T)o.Vtri[q * Nfp + j];
+      h[oVtriTw + q * NFPP + j] = (T)o.VtriTw[j * Nfq + q];
     }
   std::vector<int16_t> hi(4 * 6 * Nfp + 4 * 6 * Np);
   for (int i = 0; i < 4 * 6 * Nfp; ++i) hi[i] = (int16_t)o.gidx[i];

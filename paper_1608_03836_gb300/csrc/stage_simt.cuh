@@ -17,9 +17,10 @@
 //   4. RHS mode: dQ/dt = r.  LSRK mode (Sec. 5.2): res = a res + dt r,
 //      Q_out = Q + b res.
 // Every phase is a set of small matrix products "A (rows x k) times a block of
-// E columns" in which a thread owns one output row for EG columns; the
-// reference operators are read through the read-only data path (they are
-// shared by all blocks and stay resident in L1/L2).
+// E columns" in which a thread owns a register tile of 4 (or 2) output rows by
+// 4 columns, loading 4 rows of A with one 128-bit read-only load and 4 columns
+// of the input with one 128-bit shared-memory load per k; the reference
+// operators are shared by all blocks and stay resident in L1/L2.
 #pragma once
 
 #include "wadg_internal.h"
@@ -35,29 +36,89 @@ struct Dims {
   static constexpr int XV = 6 * NQ;                    // volume quadrature arrays
   static constexpr int XF = 7 * 4 * NFP + 7 * 4 * NFQ; // face node + face point arrays
   static constexpr int XS = XV > XF ? XV : XF;
-  static constexpr int PER_COL = 8 * NP + XS;          // shared values per column
+  static constexpr int PER_COL = 10 * NP + XS;         // shared values per column
+  // operator row counts padded to a multiple of 4 (k-major tables)
+  static constexpr int NQP = (NQ + 3) / 4 * 4;
+  static constexpr int NPP = (NP + 3) / 4 * 4;
+  static constexpr int NFQP = (NFQ + 3) / 4 * 4;
+  static constexpr int NFPP = (NFP + 3) / 4 * 4;
 };
 
-// Columns per block: about 96 KB of shared memory, a multiple of 4.
+// Columns per block E.  E = 4 (mod 8) makes the row stride of the [row][E]
+// shared arrays 16 words modulo 32 banks, so that the 4x4 register tiles of a
+// warp (column group fastest) store without bank conflicts.  Budget: about
+// 76 KB of shared memory (3 blocks per SM), 112 KB for N >= 5.
+// FP64 is bound by the FP64 pipe, not by shared memory: it keeps ~96 KB
+// blocks with E a multiple of 4.
 template <typename T, int N>
 constexpr int cols_per_block() {
   constexpr int per = Dims<N>::PER_COL * (int)sizeof(T);
-  constexpr int e = (98304 / per) / 4 * 4;
-  return e < 4 ? 4 : (e > 32 ? 32 : e);
+  if (sizeof(T) == 8) {
+    constexpr int e8 = (98304 / per) / 4 * 4;
+    return e8 < 4 ? 4 : (e8 > 32 ? 32 : e8);
+  }
+  constexpr int budget = N >= 5 ? 114688 : 77824;
+  constexpr int fit = budget / per;
+  constexpr int e = fit >= 28 ? 28 : (fit >= 20 ? 20 : (fit >= 12 ? 12 : 4));
+  return e;
 }
 
 constexpr int kStageThreads = 256;
 
-// acc[e] = sum_k A[k*M + m] * in[k*E + e], e < EG
-template <typename T, int E, int EG, int M, int KK>
-__device__ __forceinline__ void rowdot(const T* __restrict__ A, const T* in, int m, T (&acc)[EG]) {
+// Vector loads: R consecutive operator rows through the read-only path, and
+// 4 consecutive columns from shared memory.
+__device__ __forceinline__ void ldg_rows(const float* p, float (&v)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ldg_rows(const float* p, float (&v)[2]) {
+  const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void ldg_rows(const double* p, double (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ldg_rows(const double* p, double (&v)[2]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  v[0] = a.x; v[1] = a.y;
+}
+__device__ __forceinline__ void lds_cols(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void lds_cols(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+__device__ __forceinline__ void sts_cols(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void sts_cols(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// Register tile: acc[r][e] = sum_k A[k*MP + m0 + r] * in[k*E + e] for R rows and
+// 4 columns.  A is a k-major operator table with MP (a multiple of 4) rows.
+template <typename T, int E, int R, int MP, int KK>
+__device__ __forceinline__ void tile_dot(const T* __restrict__ A, const T* in, int m0, T (&acc)[R][4]) {
 #pragma unroll
-  for (int e = 0; e < EG; ++e) acc[e] = T(0);
-#pragma unroll 4
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[r][e] = T(0);
+#pragma unroll 8
   for (int k = 0; k < KK; ++k) {
-    const T a = __ldg(A + k * M + m);
+    T a[R], b[4];
+    ldg_rows(A + k * MP + m0, a);
+    lds_cols(in + k * E, b);
 #pragma unroll
-    for (int e = 0; e < EG; ++e) acc[e] = fma(a, in[k * E + e], acc[e]);
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[r][e] = fma(a[r], b[e], acc[r][e]);
   }
 }
 
@@ -65,13 +126,15 @@ template <typename T, int N, int E, int MODE>
 __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<T> p) {
   using Dm = Dims<N>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NFP = Dm::NFP, NFQ = Dm::NFQ;
-  constexpr int EG = 4, NG = E / EG;
+  constexpr int NQP = Dm::NQP, NPP = Dm::NPP, NFQP = Dm::NFQP, NFPP = Dm::NFPP;
+  constexpr int NG = E / 4;
   constexpr int NT = kStageThreads;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sQ = reinterpret_cast<T*>(smem_raw);  // [4][NP][E]
   T* sR = sQ + 4 * NP * E;                 // [4][NP][E]  load vector b (un-inverted)
-  T* sX = sR + 4 * NP * E;                 // [XS][E]     scratch
+  T* sP = sR + 4 * NP * E;                 // [2][NP][E]  partial pressure volume terms
+  T* sX = sP + 2 * NP * E;                 // [XS][E]     scratch
   T* sFN = sX;                             // [7][4 NFP][E] face-node combos
   T* sFQ = sX + 7 * 4 * NFP * E;           // [7][4 NFQ][E] face-point values
 
@@ -93,17 +156,21 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
   }
   __syncthreads();
 
-  // ---- 1a. volume: values at quadrature points ----
-  for (int it = tid; it < 6 * NQ * NG; it += NT) {
-    const int m = it % NQ;
-    const int g = (it / NQ) % NG;
-    const int job = it / (NQ * NG);
-    const T* A = job < 3 ? ops.VqT : ops.VaT + (job - 3) * NP * NQ;
-    const T* in = (job < 3 ? sQ + (1 + job) * NP * E : sQ) + g * EG;
-    T acc[EG];
-    rowdot<T, E, EG, NQ, NP>(A, in, m, acc);
+  // ---- 1a. volume: values at quadrature points (6 products, 4 rows x 4 cols) ----
+  {
+    constexpr int RG = NQP / 4;
+    for (int it = tid; it < 6 * RG * NG; it += NT) {
+      const int g = it % NG;
+      const int m0 = ((it / NG) % RG) * 4;
+      const int job = it / (RG * NG);
+      const T* A = job < 3 ? ops.VqT : ops.VaT + (job - 3) * NP * NQP;
+      const T* in = (job < 3 ? sQ + (1 + job) * NP * E : sQ) + g * 4;
+      T acc[4][4];
+      tile_dot<T, E, 4, NQP, NP>(A, in, m0, acc);
 #pragma unroll
-    for (int e = 0; e < EG; ++e) sX[(job * NQ + m) * E + g * EG + e] = acc[e];
+      for (int r = 0; r < 4; ++r)
+        if (m0 + r < NQ) sts_cols(sX + (job * NQ + m0 + r) * E + g * 4, acc[r]);
+    }
   }
   __syncthreads();
 
@@ -133,21 +200,26 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
   }
   __syncthreads();
 
-  // ---- 1c. volume: test against the basis ----
-  for (int it = tid; it < 4 * NP * NG; it += NT) {
-    const int m = it % NP;
-    const int g = (it / NP) % NG;
-    const int job = it / (NP * NG);
-    T acc[EG];
-    if (job == 0) {
-      rowdot<T, E, EG, NP, 3 * NQ>(ops.DwT, sX + g * EG, m, acc);
-    } else {
-      rowdot<T, E, EG, NP, NQ>(ops.VwT, sX + (3 + job - 1) * NQ * E + g * EG, m, acc);
+  // ---- 1c. volume: test against the basis (6 equal products, 2 rows x 4 cols) ----
+  // jobs 0..2: (V_q^a)^T diag(w) U^a  -> pressure partials; jobs 3..5: -V_q^T diag(w) (J grad p)_i
+  {
+    constexpr int RG = NPP / 2;
+    for (int it = tid; it < 6 * RG * NG; it += NT) {
+      const int g = it % NG;
+      const int m0 = ((it / NG) % RG) * 2;
+      const int job = it / (RG * NG);
+      const T* A = job < 3 ? ops.DwT + job * NQ * NPP : ops.VwT;
+      T acc[2][4];
+      tile_dot<T, E, 2, NPP, NQ>(A, sX + job * NQ * E + g * 4, m0, acc);
+      T* out = job == 0 ? sR : (job < 3 ? sP + (job - 1) * NP * E : sR + (job - 2) * NP * E);
+      const T sgn = job < 3 ? T(1) : T(-1);
 #pragma unroll
-      for (int e = 0; e < EG; ++e) acc[e] = -acc[e];
+      for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[r][e] *= sgn;
+        if (m0 + r < NP) sts_cols(out + (m0 + r) * E + g * 4, acc[r]);
+      }
     }
-#pragma unroll
-    for (int e = 0; e < EG; ++e) sR[(job * NP + m) * E + g * EG + e] = acc[e];
   }
   __syncthreads();
 
@@ -194,14 +266,18 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
   __syncthreads();
 
   // ---- 2b. interpolate the 7 combinations to the face points ----
-  for (int it = tid; it < 28 * NFQ * NG; it += NT) {
-    const int m = it % NFQ;
-    const int g = (it / NFQ) % NG;
-    const int job = it / (NFQ * NG);  // combo * 4 + face
-    T acc[EG];
-    rowdot<T, E, EG, NFQ, NFP>(ops.VtriT, sFN + job * NFP * E + g * EG, m, acc);
+  {
+    constexpr int RG = NFQP / 4;
+    for (int it = tid; it < 28 * RG * NG; it += NT) {
+      const int g = it % NG;
+      const int m0 = ((it / NG) % RG) * 4;
+      const int job = it / (RG * NG);  // combo * 4 + face
+      T acc[4][4];
+      tile_dot<T, E, 4, NFQP, NFP>(ops.VtriT, sFN + job * NFP * E + g * 4, m0, acc);
 #pragma unroll
-    for (int e = 0; e < EG; ++e) sFQ[(job * NFQ + m) * E + g * EG + e] = acc[e];
+      for (int r = 0; r < 4; ++r)
+        if (m0 + r < NFQ) sts_cols(sFQ + (job * NFQ + m0 + r) * E + g * 4, acc[r]);
+    }
   }
   __syncthreads();
 
@@ -234,18 +310,22 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
   __syncthreads();
 
   // ---- 2d. V_tri^T diag(w_f): back to face nodes ----
-  for (int it = tid; it < 16 * NFP * NG; it += NT) {
-    const int m = it % NFP;
-    const int g = (it / NFP) % NG;
-    const int job = it / (NFP * NG);  // field * 4 + face
-    T acc[EG];
-    rowdot<T, E, EG, NFP, NFQ>(ops.VtriTwT, sFQ + job * NFQ * E + g * EG, m, acc);
+  {
+    constexpr int RG = NFPP / 2;
+    for (int it = tid; it < 16 * RG * NG; it += NT) {
+      const int g = it % NG;
+      const int m0 = ((it / NG) % RG) * 2;
+      const int job = it / (RG * NG);  // field * 4 + face
+      T acc[2][4];
+      tile_dot<T, E, 2, NFPP, NFQ>(ops.VtriTwT, sFQ + job * NFQ * E + g * 4, m0, acc);
 #pragma unroll
-    for (int e = 0; e < EG; ++e) sFN[(job * NFP + m) * E + g * EG + e] = acc[e];
+      for (int r = 0; r < 2; ++r)
+        if (m0 + r < NFP) sts_cols(sFN + (job * NFP + m0 + r) * E + g * 4, acc[r]);
+    }
   }
   __syncthreads();
 
-  // ---- 2e. scatter to volume nodes (+ point source) ----
+  // ---- 2e. scatter to volume nodes, pressure partials, point source ----
   for (int it = tid; it < 4 * NP * E; it += NT) {
     const int n = it % NP;
     const int e = (it / NP) % E;
@@ -254,6 +334,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
     c = c < ncols ? c : ncols - 1;
     const int64_t k = c / S;
     T acc = sR[(fld * NP + n) * E + e];
+    if (fld == 0) acc += sP[n * E + e] + sP[(NP + n) * E + e];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const int pio = p.fcode[k * 4 + f] % 6;
@@ -269,41 +350,54 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
   __syncthreads();
 
   // ---- 3a. update: W (V_q M^^{-1}) b at quadrature points ----
-  for (int it = tid; it < 4 * NQ * NG; it += NT) {
-    const int m = it % NQ;
-    const int g = (it / NQ) % NG;
-    const int fld = it / (NQ * NG);
-    T acc[EG];
-    rowdot<T, E, EG, NQ, NP>(ops.VtT, sR + fld * NP * E + g * EG, m, acc);
-    const int wc = fld == 0 ? 9 : 10;
+  {
+    constexpr int RG = NQP / 4;
+    for (int it = tid; it < 4 * RG * NG; it += NT) {
+      const int g = it % NG;
+      const int m0 = ((it / NG) % RG) * 4;
+      const int fld = it / (RG * NG);
+      T acc[4][4];
+      tile_dot<T, E, 4, NQP, NP>(ops.VtT, sR + fld * NP * E + g * 4, m0, acc);
+      const int wc = fld == 0 ? 9 : 10;
 #pragma unroll
-    for (int e = 0; e < EG; ++e) {
-      int64_t c = col0 + g * EG + e;
-      c = c < ncols ? c : ncols - 1;
-      const int64_t k = c / S;
-      sX[(fld * NQ + m) * E + g * EG + e] = acc[e] * __ldg(p.vgeo + (k * 11 + wc) * NQ + m);
+      for (int e = 0; e < 4; ++e) {
+        int64_t c = col0 + g * 4 + e;
+        c = c < ncols ? c : ncols - 1;
+        const T* w = p.vgeo + ((c / S) * 11 + wc) * NQ;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (m0 + r < NQ) sX[(fld * NQ + m0 + r) * E + g * 4 + e] = acc[r][e] * __ldg(w + m0 + r);
+      }
     }
   }
   __syncthreads();
 
   // ---- 3b. update: P_q back to nodes, then the epilogue ----
-  for (int it = tid; it < 4 * NP * NG; it += NT) {
-    const int m = it % NP;
-    const int g = (it / NP) % NG;
-    const int fld = it / (NP * NG);
-    T acc[EG];
-    rowdot<T, E, EG, NP, NQ>(ops.PqT, sX + fld * NQ * E + g * EG, m, acc);
+  {
+    constexpr int RG = NPP / 2;
+    for (int it = tid; it < 4 * RG * NG; it += NT) {
+      const int g = it % NG;
+      const int m0 = ((it / NG) % RG) * 2;
+      const int fld = it / (RG * NG);
+      T acc[2][4];
+      tile_dot<T, E, 2, NPP, NQ>(ops.PqT, sX + fld * NQ * E + g * 4, m0, acc);
 #pragma unroll
-    for (int e = 0; e < EG; ++e) {
-      const int64_t c = col0 + g * EG + e;
-      if (c >= ncols) continue;
-      const int64_t idx = fld * fs + c * NP + m;
-      if (MODE == 0) {
-        p.out[idx] = acc[e];
-      } else {
-        const T r = p.rk_a * p.res[idx] + p.dt * acc[e];
-        p.res[idx] = r;
-        p.Qout[idx] = sQ[(fld * NP + m) * E + g * EG + e] + p.rk_b * r;
+      for (int e = 0; e < 4; ++e) {
+        const int64_t c = col0 + g * 4 + e;
+        if (c >= ncols) continue;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int m = m0 + r;
+          if (m >= NP) continue;
+          const int64_t idx = fld * fs + c * NP + m;
+          if (MODE == 0) {
+            p.out[idx] = acc[r][e];
+          } else {
+            const T rr = p.rk_a * p.res[idx] + p.dt * acc[r][e];
+            p.res[idx] = rr;
+            p.Qout[idx] = sQ[(fld * NP + m) * E + g * 4 + e] + p.rk_b * rr;
+          }
+        }
       }
     }
   }

@@ -14,18 +14,19 @@
 namespace wadg {
 
 // Device copies of the reference operators in precision T, stored "k-major"
-// (A[k][m], consecutive output rows m contiguous) so that a warp of threads
-// owning consecutive output rows reads one coalesced line per k.
+// (A[k][m], consecutive output rows m contiguous, the row count m padded with
+// zero rows to a multiple of 4: Nq -> NQP etc.) so that a thread owning 4
+// consecutive output rows reads them with one vector load per k.
 template <typename T>
 struct DevOps {
-  const T* VqT = nullptr;     // [Np][Nq]     V_q
-  const T* VaT = nullptr;     // [3][Np][Nq]  V_q^a  (d/dr, d/ds, d/dt)
-  const T* DwT = nullptr;     // [3 Nq][Np]   (V_q^a)^T diag(w), a-major blocks
-  const T* VwT = nullptr;     // [Nq][Np]     V_q^T diag(w)
-  const T* VtT = nullptr;     // [Np][Nq]     V_q M^^{-1}
-  const T* PqT = nullptr;     // [Nq][Np]     M^^{-1} V_q^T diag(w)
-  const T* VtriT = nullptr;   // [Nfp][Nfq]   face interpolation
-  const T* VtriTwT = nullptr; // [Nfq][Nfp]   V_tri^T diag(w_f)
+  const T* VqT = nullptr;     // [Np][NQP]      V_q
+  const T* VaT = nullptr;     // [3][Np][NQP]   V_q^a  (d/dr, d/ds, d/dt)
+  const T* DwT = nullptr;     // [3][Nq][NPP]   (V_q^a)^T diag(w), one block per a
+  const T* VwT = nullptr;     // [Nq][NPP]      V_q^T diag(w)
+  const T* VtT = nullptr;     // [Np][NQP]      V_q M^^{-1}
+  const T* PqT = nullptr;     // [Nq][NPP]      M^^{-1} V_q^T diag(w)
+  const T* VtriT = nullptr;   // [Nfp][NFQP]    face interpolation
+  const T* VtriTwT = nullptr; // [Nfq][NFPP]    V_tri^T diag(w_f)
   const int16_t* gidx = nullptr;  // [4][6][Nfp]
   const int16_t* ginv = nullptr;  // [4][6][Np]
   void* base = nullptr;       // single allocation holding all of the above
