@@ -164,6 +164,38 @@ int wadg_energy_noalloc(wadg_mesh* mesh, const void* Q, double* E, wadg_stream s
 int wadg_l2_error(wadg_mesh* mesh, const void* Q, const double* exact_q, int field_mask, double* err,
                   wadg_stream stream);
 
+/* ---- Discrete adjoint (gradients of receiver misfits) -------------------
+ * The paper has no adjoint; these entry points apply the exact transposes of
+ * the discrete operators above: the strong-weak load operator A_h (Sec. 4.1),
+ * the weight-adjusted update P_q diag(W) V_q M^^{-1} (Sec. 6.2, Eq. (matfree);
+ * Sec. 7) and the LSRK(5,4) stage recurrence (Sec. 5.2).  With L the operator
+ * of wadg_rhs, the reverse of stage s is mu = lam_res + b_s lam_Q,
+ * lam_Q += dt L^T mu, lam_res = a_s mu. */
+
+/* out = L^T lambda (transpose of wadg_rhs).  lambda, out device [4][K][S][Np],
+ * distinct, mesh precision. */
+int wadg_rhs_adjoint(wadg_mesh* mesh, const void* lambda, void* out, wadg_stream stream);
+
+/* One LSRK step exactly as wadg_step with nsteps = 1 that also records, for
+ * each of its 5 stages, y_q = (V_q M^^{-1} b_p)_q / J_q at the volume points
+ * (the factor by which the pressure update depends on c^2_q).
+ *   ystore  device [5][K][S][Nq] in the mesh precision, or NULL (no record).
+ *   traces  device [S][R] receiver pressures after the step, or NULL. */
+int wadg_step_record(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, void* ystore, void* traces,
+                     wadg_stream stream);
+
+/* Reverse of one LSRK step.  lamQ, lamR (device [4][K][S][Np], distinct) hold
+ * the adjoints of Q and res after the step and are replaced by those before
+ * it.  ystore: the record of the same step from wadg_step_record, or NULL;
+ * dc2: device [K][Nq] FP64 accumulator of dJ/dc^2_q (summed over shots),
+ * NULL exactly when ystore is NULL. */
+int wadg_step_adjoint(wadg_mesh* mesh, void* lamQ, void* lamR, double dt, const void* ystore, double* dc2,
+                      wadg_stream stream);
+
+/* Transpose of the receiver samples: lamQ[p] += sum_r w_r l(x^_r) in each
+ * receiver's column.  weights device [S][R] in the mesh precision. */
+int wadg_receivers_adjoint(wadg_mesh* mesh, const void* weights, void* lamQ, wadg_stream stream);
+
 void wadg_mesh_destroy(wadg_mesh* mesh);
 const char* wadg_status_string(int status);
 const char* wadg_last_error(const wadg_mesh* mesh);

@@ -23,12 +23,16 @@ from .api import (  # noqa: E402,F401
     wadg_mesh_destroy,
     wadg_project,
     wadg_reference_rules,
+    wadg_receivers_adjoint,
     wadg_rhs,
+    wadg_rhs_adjoint,
     wadg_set_operators,
     wadg_set_receivers,
     wadg_set_sources,
     wadg_status_string,
     wadg_step,
+    wadg_step_adjoint,
+    wadg_step_record,
     wadg_version,
     wadg_volume_points,
 )

@@ -27,6 +27,10 @@ SIGNATURES = {
     "wadg_energy": (c_int, [c_void_p, c_void_p, P_double, c_void_p]),
     "wadg_energy_noalloc": (c_int, [c_void_p, c_void_p, P_double, c_void_p]),
     "wadg_l2_error": (c_int, [c_void_p, c_void_p, c_void_p, c_int, P_double, c_void_p]),
+    "wadg_rhs_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wadg_step_record": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, c_void_p, c_void_p, c_void_p]),
+    "wadg_step_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
+    "wadg_receivers_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "wadg_mesh_destroy": (None, [c_void_p]),
     "wadg_status_string": (ctypes.c_char_p, [c_int]),
     "wadg_last_error": (ctypes.c_char_p, [c_void_p]),

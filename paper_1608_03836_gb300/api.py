@@ -91,9 +91,11 @@ def wadg_set_operators(mesh: MeshHandle, precision="fp64", shots: int = 1, tau_p
     st = load().wadg_set_operators(mesh.handle, int(prec), int(shots), float(tau_p), float(tau_u),
                                    None if c2 is None else _dptr(c2))
     _check(st, "wadg_set_operators", mesh)
+    if int(shots) != mesh.S or int(prec) != mesh.precision:
+        mesh.R = 0                          # the library drops sources and receivers then
     mesh.S = int(shots)
     mesh.precision = int(prec)
-    mesh.R = 0
+    mesh.tau_p, mesh.tau_u = float(tau_p), float(tau_u)
 
 
 def wadg_reference_rules(N: int):
@@ -194,6 +196,45 @@ def wadg_l2_error(mesh: MeshHandle, Q, exact_q, field_mask: int = 1, stream=None
     _check(load().wadg_l2_error(mesh.handle, a, b, int(field_mask), ctypes.byref(e), _stream(stream)),
            "wadg_l2_error", mesh)
     return e.value
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def wadg_rhs_adjoint(mesh: MeshHandle, lam, out, stream=None):
+    a = _check_field(mesh, lam, "lambda")
+    b = _check_field(mesh, out, "out")
+    _check(load().wadg_rhs_adjoint(mesh.handle, a, b, _stream(stream)), "wadg_rhs_adjoint", mesh)
+
+
+def wadg_step_record(mesh: MeshHandle, Q, res, t0: float, dt: float, ystore=None, traces=None, stream=None):
+    a = _check_field(mesh, Q, "Q")
+    b = _check_field(mesh, res, "res")
+    if ystore is not None and (ystore.dtype != mesh.dtype or ystore.numel() != 5 * mesh.K * mesh.S * mesh.Nq):
+        raise ValueError("ystore must hold 5*K*S*Nq values in the mesh precision")
+    if traces is not None and (traces.dtype != mesh.dtype or traces.numel() < mesh.S * mesh.R):
+        raise ValueError("traces must hold S*R values in the mesh precision")
+    _check(load().wadg_step_record(mesh.handle, a, b, float(t0), float(dt), _ptr(ystore), _ptr(traces),
+                                   _stream(stream)), "wadg_step_record", mesh)
+
+
+def wadg_step_adjoint(mesh: MeshHandle, lamQ, lamR, dt: float, ystore=None, dc2=None, stream=None):
+    import torch
+    a = _check_field(mesh, lamQ, "lamQ")
+    b = _check_field(mesh, lamR, "lamR")
+    if dc2 is not None and (dc2.dtype != torch.float64 or dc2.numel() != mesh.K * mesh.Nq):
+        raise ValueError("dc2 must be a float64 tensor of K*Nq values")
+    _check(load().wadg_step_adjoint(mesh.handle, a, b, float(dt), _ptr(ystore), _ptr(dc2), _stream(stream)),
+           "wadg_step_adjoint", mesh)
+
+
+def wadg_receivers_adjoint(mesh: MeshHandle, weights, lamQ, stream=None):
+    a = _check_field(mesh, lamQ, "lamQ")
+    if weights.dtype != mesh.dtype or weights.numel() != mesh.S * mesh.R or not weights.is_contiguous():
+        raise ValueError("weights must be a contiguous S*R tensor in the mesh precision")
+    _check(load().wadg_receivers_adjoint(mesh.handle, _ptr(weights), a, _stream(stream)), "wadg_receivers_adjoint",
+           mesh)
 
 
 def wadg_mesh_destroy(mesh: MeshHandle):

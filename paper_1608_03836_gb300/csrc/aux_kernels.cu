@@ -233,6 +233,16 @@ __global__ void receiver_kernel(int64_t ncols, int S, int R, int Np, const T* __
   out[i] = acc;
 }
 
+// Transpose of the receiver samples: lambda_Q[p][col_r][n] += w_r l_n(x^_r).
+template <typename T>
+__global__ void receiver_adjoint_kernel(int S, int R, int Np, const T* __restrict__ w, const int32_t* __restrict__ rec_col,
+                                        const T* __restrict__ rec_vec, T* __restrict__ lamQ) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)S * R * Np) return;
+  const int r = (int)(i / Np), n = (int)(i % Np);
+  atomicAdd(lamQ + (int64_t)rec_col[r] * Np + n, w[r] * rec_vec[(int64_t)r * Np + n]);
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
@@ -289,6 +299,19 @@ cudaError_t launch_receivers(int64_t ncols, int S, int R, int Np, const T* Q, co
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_receivers_adjoint(int S, int R, int Np, const T* w, const int32_t* rec_col, const T* rec_vec, T* lamQ,
+                                     cudaStream_t st) {
+  const int64_t n = (int64_t)S * R * Np;
+  if (n == 0) return cudaSuccess;
+  receiver_adjoint_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(S, R, Np, w, rec_col, rec_vec, lamQ);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_receivers_adjoint<double>(int, int, int, const double*, const int32_t*, const double*,
+                                                      double*, cudaStream_t);
+template cudaError_t launch_receivers_adjoint<float>(int, int, int, const float*, const int32_t*, const float*, float*,
+                                                     cudaStream_t);
 template cudaError_t launch_geo_pack<double>(int64_t, int, int, const double*, const double*, const double*,
                                              const double*, double*, double*, cudaStream_t);
 template cudaError_t launch_geo_pack<float>(int64_t, int, int, const double*, const double*, const double*,

@@ -25,4 +25,8 @@ template <typename T>
 cudaError_t launch_receivers(int64_t ncols, int S, int R, int Np, const T* Q, const int32_t* rec_col, const T* rec_vec,
                              T* out, cudaStream_t st);
 
+template <typename T>
+cudaError_t launch_receivers_adjoint(int S, int R, int Np, const T* w, const int32_t* rec_col, const T* rec_vec, T* lamQ,
+                                     cudaStream_t st);
+
 }  // namespace wadg

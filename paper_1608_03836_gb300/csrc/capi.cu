@@ -29,6 +29,22 @@ cudaError_t launch_stage(int N, const StageParams<T>& p, int mode, cudaStream_t 
   }
 }
 
+template <typename T, int N>
+cudaError_t launch_adj_update_n(const AdjUpdateParams<T>& p, int lsrk, cudaStream_t stream);
+
+template <typename T>
+cudaError_t launch_adj_update(int N, const AdjUpdateParams<T>& p, int lsrk, cudaStream_t stream) {
+  switch (N) {
+    case 1: return launch_adj_update_n<T, 1>(p, lsrk, stream);
+    case 2: return launch_adj_update_n<T, 2>(p, lsrk, stream);
+    case 3: return launch_adj_update_n<T, 3>(p, lsrk, stream);
+    case 4: return launch_adj_update_n<T, 4>(p, lsrk, stream);
+    case 5: return launch_adj_update_n<T, 5>(p, lsrk, stream);
+    case 6: return launch_adj_update_n<T, 6>(p, lsrk, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients
 // (the scheme named in Sec. 5.2 of the paper, which does not print them).
 static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
@@ -109,7 +125,8 @@ int upload_ops(wadg_mesh* m, DevOps<T>& ops) {
   const int NQP = pad4(Nq), NPP = pad4(Np), NFQP = pad4(Nfq), NFPP = pad4(Nfp);
   size_t oVq = push((size_t)Np * NQP), oVa = push(3 * (size_t)Np * NQP), oDw = push(3 * (size_t)Nq * NPP),
          oVw = push((size_t)Nq * NPP), oVt = push((size_t)Np * NQP), oPq = push((size_t)Nq * NPP),
-         oVtri = push((size_t)Nfp * NFQP), oVtriTw = push((size_t)Nfq * NFPP);
+         oVtri = push((size_t)Nfp * NFQP), oVtriTw = push((size_t)Nfq * NFPP), oPqTT = push((size_t)Np * NQP),
+         oVtTT = push((size_t)Nq * NPP);
   for (int n = 0; n < Np; ++n)
     for (int q = 0; q < Nq; ++q) {
       h[oVq + n * NQP + q] = (T)o.Vq[q * Np + n];
@@ -118,6 +135,8 @@ int upload_ops(wadg_mesh* m, DevOps<T>& ops) {
       h[oVw + q * NPP + n] = (T)o.Vw[n * Nq + q];
       h[oVt + n * NQP + q] = (T)o.Vtilde[q * Np + n];
       h[oPq + q * NPP + n] = (T)o.Pq[n * Nq + q];
+      h[oPqTT + n * NQP + q] = (T)o.Pq[n * Nq + q];      // P_q^T: rows q, k = n
+      h[oVtTT + q * NPP + n] = (T)o.Vtilde[q * Np + n];  // (V_q M^-1)^T: rows n, k = q
     }
   for (int j = 0; j < Nfp; ++j)
     for (int q = 0; q < Nfq; ++q) {
@@ -143,6 +162,8 @@ int upload_ops(wadg_mesh* m, DevOps<T>& ops) {
   ops.PqT = b + oPq;
   ops.VtriT = b + oVtri;
   ops.VtriTwT = b + oVtriTw;
+  ops.PqTT = b + oPqTT;
+  ops.VtTT = b + oVtTT;
   ops.gidx = (const int16_t*)((char*)base + bytes_t);
   ops.ginv = ops.gidx + 4 * 6 * Nfp;
   return WADG_OK;
@@ -790,6 +811,149 @@ int wadg_set_receivers(wadg_mesh* m, int R, const double* xyz) {
                           (size_t)n * m->ref.Np * ts, cudaMemcpyHostToDevice));
   m->R = R;
   return WADG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+AdjUpdateParams<T> adj_params(const wadg_mesh* m) {
+  AdjUpdateParams<T> a;
+  a.vgeo = (const T*)m->d_vgeo;
+  a.ops = ops_of(m, T());
+  a.ncols = m->K * m->S;
+  a.S = m->S;
+  return a;
+}
+
+template <typename T>
+int rhs_adjoint_t(wadg_mesh* m, const void* lam, void* out, cudaStream_t st) {
+  AdjUpdateParams<T> a = adj_params<T>(m);
+  a.lam = (const T*)lam;
+  a.beta = (T*)m->d_Qtmp;
+  cudaError_t e = launch_adj_update<T>(m->N, a, 0, st);
+  if (e != cudaSuccess) return cuda_fail(m, e, "adjoint update kernel");
+  StageParams<T> p = base_params<T>(m);
+  p.Qin = (const T*)m->d_Qtmp;
+  p.out = (T*)out;
+  e = launch_stage<T>(m->N, p, 4, st);
+  return e == cudaSuccess ? WADG_OK : cuda_fail(m, e, "stage kernel (adjoint rhs)");
+}
+
+template <typename T>
+int step_record_t(wadg_mesh* m, void* Q, void* res, double t0, double dt, void* ystore, void* traces,
+                  cudaStream_t st) {
+  StageParams<T> p = base_params<T>(m);
+  p.res = (T*)res;
+  p.dt = (T)dt;
+  if (m->nsrc > 0) {
+    p.src_elem = m->d_src_elem;
+    p.src_vec = (const T*)m->d_src_vec;
+  }
+  T* cur = (T*)Q;
+  T* other = (T*)m->d_Qtmp;
+  const size_t ny = (size_t)m->K * m->S * m->ref.Nq;
+  for (int s = 0; s < 5; ++s) {
+    p.Qin = cur;
+    p.Qout = other;
+    p.rk_a = (T)kRkA[s];
+    p.rk_b = (T)kRkB[s];
+    p.src_amp = (T)(m->nsrc > 0 ? ricker(t0 + kRkC[s] * dt, m->f0, m->t0) : 0.0);
+    p.yrec = ystore ? (T*)ystore + s * ny : nullptr;
+    cudaError_t e = launch_stage<T>(m->N, p, ystore ? 2 : 1, st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "stage kernel (record)");
+    std::swap(cur, other);
+  }
+  if (traces && m->R > 0) {
+    cudaError_t e = launch_receivers<T>(m->K * m->S, m->S, m->R, m->ref.Np, cur, m->d_rec_col,
+                                        (const T*)m->d_rec_vec, (T*)traces, st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "receiver kernel");
+  }
+  const size_t bytes = (size_t)4 * m->K * m->S * m->ref.Np * sizeof(T);
+  cudaError_t e = cudaMemcpyAsync(Q, cur, bytes, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? WADG_OK : cuda_fail(m, e, "copy back");
+}
+
+template <typename T>
+int step_adjoint_t(wadg_mesh* m, void* lamQ, void* lamR, double dt, const void* ystore, double* dc2, cudaStream_t st) {
+  AdjUpdateParams<T> a = adj_params<T>(m);
+  a.lamQ = (T*)lamQ;
+  a.lamR = (T*)lamR;
+  a.beta = (T*)m->d_Qtmp;
+  a.dt = (T)dt;
+  a.dc2 = ystore ? dc2 : nullptr;
+  StageParams<T> p = base_params<T>(m);
+  p.Qin = (const T*)m->d_Qtmp;
+  p.Qout = (T*)lamQ;
+  p.dt = (T)dt;
+  const size_t ny = (size_t)m->K * m->S * m->ref.Nq;
+  for (int s = 4; s >= 0; --s) {
+    a.rk_a = (T)kRkA[s];
+    a.rk_b = (T)kRkB[s];
+    a.yrec = ystore ? (const T*)ystore + s * ny : nullptr;
+    cudaError_t e = launch_adj_update<T>(m->N, a, 1, st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "adjoint update kernel");
+    e = launch_stage<T>(m->N, p, 3, st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "stage kernel (adjoint)");
+  }
+  return WADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wadg_rhs_adjoint(wadg_mesh* m, const void* lam, void* out, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!lam || !out || lam == out || !aligned16(lam) || !aligned16(out))
+    return fail(m, WADG_EINVAL, "lambda and out must be distinct 16-byte aligned device pointers");
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->precision == WADG_FP64 ? rhs_adjoint_t<double>(m, lam, out, s) : rhs_adjoint_t<float>(m, lam, out, s);
+}
+
+int wadg_step_record(wadg_mesh* m, void* Q, void* res, double t0, double dt, void* ystore, void* traces,
+                     wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!Q || !res || Q == res || !aligned16(Q) || !aligned16(res))
+    return fail(m, WADG_EINVAL, "Q and res must be distinct 16-byte aligned device pointers");
+  if (!std::isfinite(dt) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "dt/t0");
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->precision == WADG_FP64 ? step_record_t<double>(m, Q, res, t0, dt, ystore, traces, s)
+                                   : step_record_t<float>(m, Q, res, t0, dt, ystore, traces, s);
+}
+
+int wadg_step_adjoint(wadg_mesh* m, void* lamQ, void* lamR, double dt, const void* ystore, double* dc2,
+                      wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!lamQ || !lamR || lamQ == lamR || !aligned16(lamQ) || !aligned16(lamR))
+    return fail(m, WADG_EINVAL, "lambda_Q and lambda_res must be distinct 16-byte aligned device pointers");
+  if ((dc2 != nullptr) != (ystore != nullptr)) return fail(m, WADG_EINVAL, "ystore and dc2 go together");
+  if (!std::isfinite(dt)) return fail(m, WADG_EINVAL, "dt");
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->precision == WADG_FP64 ? step_adjoint_t<double>(m, lamQ, lamR, dt, ystore, dc2, s)
+                                   : step_adjoint_t<float>(m, lamQ, lamR, dt, ystore, dc2, s);
+}
+
+int wadg_receivers_adjoint(wadg_mesh* m, const void* weights, void* lamQ, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!weights || !lamQ) return fail(m, WADG_EINVAL, "null pointer");
+  if (m->R == 0) return WADG_OK;
+  DeviceGuard g(m->device);
+  cudaError_t e = m->precision == WADG_FP64
+                      ? launch_receivers_adjoint<double>(m->S, m->R, m->ref.Np, (const double*)weights, m->d_rec_col,
+                                                         (const double*)m->d_rec_vec, (double*)lamQ,
+                                                         (cudaStream_t)stream)
+                      : launch_receivers_adjoint<float>(m->S, m->R, m->ref.Np, (const float*)weights, m->d_rec_col,
+                                                        (const float*)m->d_rec_vec, (float*)lamQ, (cudaStream_t)stream);
+  return e == cudaSuccess ? WADG_OK : cuda_fail(m, e, "receiver adjoint kernel");
 }
 
 }  // extern "C"

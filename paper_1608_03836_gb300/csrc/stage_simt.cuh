@@ -15,7 +15,13 @@
 //   3. the weight-adjusted update (Sec. 6.2, Eq. (matfree); Sec. 7):
 //        r = P_q diag(W) (V_q M^^{-1}) b,  W = c^2/J (p) or 1/J (u);
 //   4. RHS mode: dQ/dt = r.  LSRK mode (Sec. 5.2): res = a res + dt r,
-//      Q_out = Q + b res.
+//      Q_out = Q + b res.  Record mode: LSRK, and also stores
+//      y_q = (V_q M^^{-1} b_p)_q / J_q, the factor of dr_p/dc^2_q.
+// Adjoint modes apply A^T (the transpose of steps 1-2) to an input beta and
+// skip step 3: the strong-weak volume operator is skew, so its transpose is
+// its negative; the transpose of the surface operator is the same pipeline
+// with the central flux terms negated and the penalty terms unchanged.  Mode
+// ADJ_LSRK adds dt A^T beta to lambda_Q in place; mode ADJ_RHS writes it.
 // Every phase is a set of small matrix products "A (rows x k) times a block of
 // E columns" in which a thread owns a register tile of 4 (or 2) output rows by
 // 4 columns, loading 4 rows of A with one 128-bit read-only load and 4 columns
@@ -64,6 +70,8 @@ constexpr int cols_per_block() {
 }
 
 constexpr int kStageThreads = 256;
+
+enum StageMode { kRhs = 0, kLsrk = 1, kRecord = 2, kAdjLsrk = 3, kAdjRhs = 4 };
 
 // Vector loads: R consecutive operator rows through the read-only path, and
 // 4 consecutive columns from shared memory.
@@ -212,7 +220,8 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
       T acc[2][4];
       tile_dot<T, E, 2, NPP, NQ>(A, sX + job * NQ * E + g * 4, m0, acc);
       T* out = job == 0 ? sR : (job < 3 ? sP + (job - 1) * NP * E : sR + (job - 2) * NP * E);
-      const T sgn = job < 3 ? T(1) : T(-1);
+      T sgn = job < 3 ? T(1) : T(-1);
+      if (MODE >= kAdjLsrk) sgn = -sgn;  // the volume operator is skew
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
 #pragma unroll
@@ -300,8 +309,10 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
     const T j3 = sFQ[(6 * 4 * NFQ + qf) * E + e];
     const T aun = a1 * nx + a2 * ny + a3 * nz;
     const T jun = (j1 * nx + j2 * ny + j3 * nz) / Jf;
-    const T Fp = -aun + T(0.5) * p.tau_p * jp * Jf;
-    const T s = T(-0.5) * (jp - p.tau_u * jun);
+    // central terms change sign in the transpose; penalty terms do not
+    const T cs = MODE >= kAdjLsrk ? T(1) : T(-1);
+    const T Fp = cs * aun + T(0.5) * p.tau_p * jp * Jf;
+    const T s = T(0.5) * (cs * jp + p.tau_u * jun);
     sFQ[(0 * 4 * NFQ + qf) * E + e] = Fp;
     sFQ[(1 * 4 * NFQ + qf) * E + e] = s * nx;
     sFQ[(2 * 4 * NFQ + qf) * E + e] = s * ny;
@@ -347,6 +358,22 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
     }
     sR[(fld * NP + n) * E + e] = acc;
   }
+  if (MODE >= kAdjLsrk) {
+    // ---- adjoint epilogue: A^T beta is complete in sR ----
+    __syncthreads();
+    for (int it = tid; it < 4 * NP * E; it += NT) {
+      const int n = it % NP;
+      const int e = (it / NP) % E;
+      const int fld = it / (NP * E);
+      const int64_t c = col0 + e;
+      if (c >= ncols) continue;
+      const int64_t idx = fld * fs + c * NP + n;
+      const T a = sR[(fld * NP + n) * E + e];
+      if (MODE == kAdjLsrk) p.Qout[idx] += p.dt * a;
+      else p.out[idx] = a;
+    }
+    return;
+  }
   __syncthreads();
 
   // ---- 3a. update: W (V_q M^^{-1}) b at quadrature points ----
@@ -367,6 +394,12 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
 #pragma unroll
         for (int r = 0; r < 4; ++r)
           if (m0 + r < NQ) sX[(fld * NQ + m0 + r) * E + g * 4 + e] = acc[r][e] * __ldg(w + m0 + r);
+        if (MODE == kRecord && fld == 0 && col0 + g * 4 + e < ncols) {
+          const T* wj = p.vgeo + ((c / S) * 11 + 10) * NQ;  // 1/J
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (m0 + r < NQ) p.yrec[c * NQ + m0 + r] = acc[r][e] * __ldg(wj + m0 + r);
+        }
       }
     }
   }
@@ -390,7 +423,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
           const int m = m0 + r;
           if (m >= NP) continue;
           const int64_t idx = fld * fs + c * NP + m;
-          if (MODE == 0) {
+          if (MODE == kRhs) {
             p.out[idx] = acc[r][e];
           } else {
             const T rr = p.rk_a * p.res[idx] + p.dt * acc[r][e];
@@ -403,24 +436,29 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
   }
 }
 
-template <typename T, int N>
-cudaError_t launch_stage_n(const StageParams<T>& p, int mode, cudaStream_t stream) {
+template <typename T, int N, int MODE>
+cudaError_t launch_stage_mode(const StageParams<T>& p, cudaStream_t stream) {
   constexpr int E = cols_per_block<T, N>();
   const size_t smem = (size_t)Dims<N>::PER_COL * E * sizeof(T);
   const int64_t blocks = (p.ncols + E - 1) / E;
   if (blocks == 0) return cudaSuccess;
-  if (mode == 0) {
-    auto kern = stage_kernel<T, N, E, 0>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    kern<<<(unsigned)blocks, kStageThreads, smem, stream>>>(p);
-  } else {
-    auto kern = stage_kernel<T, N, E, 1>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    kern<<<(unsigned)blocks, kStageThreads, smem, stream>>>(p);
-  }
+  auto kern = stage_kernel<T, N, E, MODE>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  kern<<<(unsigned)blocks, kStageThreads, smem, stream>>>(p);
   return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t launch_stage_n(const StageParams<T>& p, int mode, cudaStream_t stream) {
+  switch (mode) {
+    case kRhs: return launch_stage_mode<T, N, kRhs>(p, stream);
+    case kLsrk: return launch_stage_mode<T, N, kLsrk>(p, stream);
+    case kRecord: return launch_stage_mode<T, N, kRecord>(p, stream);
+    case kAdjLsrk: return launch_stage_mode<T, N, kAdjLsrk>(p, stream);
+    case kAdjRhs: return launch_stage_mode<T, N, kAdjRhs>(p, stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace wadg

@@ -27,6 +27,8 @@ struct DevOps {
   const T* PqT = nullptr;     // [Nq][NPP]      M^^{-1} V_q^T diag(w)
   const T* VtriT = nullptr;   // [Nfp][NFQP]    face interpolation
   const T* VtriTwT = nullptr; // [Nfq][NFPP]    V_tri^T diag(w_f)
+  const T* PqTT = nullptr;    // [Np][NQP]      P_q^T            (adjoint update)
+  const T* VtTT = nullptr;    // [Nq][NPP]      (V_q M^^{-1})^T  (adjoint update)
   const int16_t* gidx = nullptr;  // [4][6][Nfp]
   const int16_t* ginv = nullptr;  // [4][6][Np]
   void* base = nullptr;       // single allocation holding all of the above
@@ -53,11 +55,30 @@ struct StageParams {
   const int32_t* src_elem = nullptr;  // [S]
   const T* src_vec = nullptr;         // [S][Np] l_n(x^_s)
   T src_amp = 0;
+  T* yrec = nullptr;                  // record mode: [ncols][Nq]
 };
 
-// Launchers, one per (precision, degree); mode 0 = RHS, 1 = LSRK stage.
+// Parameters of the adjoint weight-adjusted update beta = U^T mu (local).
+template <typename T>
+struct AdjUpdateParams {
+  const T* lam = nullptr;   // RHS mode: mu = lam
+  T* lamQ = nullptr;        // LSRK mode: mu = lamR + b lamQ
+  T* lamR = nullptr;        //            lamR <- a mu
+  T* beta = nullptr;        // output U^T mu, [4][ncols][Np]
+  const T* vgeo = nullptr;
+  DevOps<T> ops;
+  int64_t ncols = 0;
+  int S = 1;
+  T rk_a = 0, rk_b = 0, dt = 0;
+  const T* yrec = nullptr;  // [ncols][Nq] recorded forward factor (nullable)
+  double* dc2 = nullptr;    // [K][Nq] gradient accumulator (nullable)
+};
+
+// Launchers, one per (precision, degree); modes as in StageMode.
 template <typename T>
 cudaError_t launch_stage(int N, const StageParams<T>& p, int mode, cudaStream_t stream);
+template <typename T>
+cudaError_t launch_adj_update(int N, const AdjUpdateParams<T>& p, int lsrk, cudaStream_t stream);
 
 }  // namespace wadg
 

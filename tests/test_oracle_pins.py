@@ -473,3 +473,37 @@ def test_receivers_sample_a_linear_field_on_curved_elements():
     rec = OS.PointSet(mesh, pts)
     got = OS.sample(c, rec, np.arange(3))
     assert np.abs(got - pts @ np.array([1.0, 2.0, -1.0])).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# Discrete adjoint (O12): finite differences in FP64
+# ----------------------------------------------------------------------------
+
+def _misfit_problem():
+    from oracle import adjoint as OA
+    from synthetic import c2_perturbed_samples
+    ref, mesh = _mesh(1, 2)
+    c2q = c2_perturbed_samples(mesh.J.shape)
+    prob = OA.MisfitProblem(mesh, c2q, [0.1, -0.2, 0.15], np.array([[0.3, 0.1, -0.4], [-0.5, 0.2, 0.3]]),
+                            f0=5.0, t0=0.02, dt=4e-3, nsteps=6)
+    return ref, mesh, prob
+
+
+@pytest.mark.slow
+def test_adjoint_gradients_match_central_differences():
+    """8 seeded directions each for p0 and c^2: <grad, d> vs central differences.
+    J is quadratic in p0 (central differences exact up to rounding) and smooth
+    in c^2 (step 1e-5: truncation ~1e-10)."""
+    ref, mesh, prob = _misfit_problem()
+    rng = np.random.default_rng(2024)
+    p0 = rng.standard_normal((mesh.K, ref.Np))
+    J, gp, gc = prob.gradients(p0)
+    for _ in range(8):
+        d = rng.standard_normal(p0.shape)
+        eps = 1e-3
+        fd = (prob.misfit(p0 + eps * d) - prob.misfit(p0 - eps * d)) / (2 * eps)
+        assert abs(fd - np.sum(gp * d)) < 1e-8 * abs(fd)
+        dc = rng.standard_normal(gc.shape)
+        eps = 1e-5
+        fd = (prob.misfit(p0, prob.c2q + eps * dc) - prob.misfit(p0, prob.c2q - eps * dc)) / (2 * eps)
+        assert abs(fd - np.sum(gc * dc)) < 1e-6 * abs(fd)
