@@ -31,15 +31,17 @@ def library_mesh(VXYZ, EToV, geom, N, precision="fp64", shots=1, c2="one", tau=(
     import paper_1608_03836_gb300 as W
     m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
     c2q = None
-    if c2 == "heterogeneous":
-        c2q = c2_heterogeneous(W.wadg_volume_points(m))
-    elif isinstance(c2, np.ndarray):
+    if isinstance(c2, np.ndarray):
         c2q = c2
+    elif c2 == "heterogeneous":
+        c2q = c2_heterogeneous(W.wadg_volume_points(m))
     W.wadg_set_operators(m, precision, shots, tau[0], tau[1], c2q)
     return m
 
 
 def oracle_c2(omesh, c2):
+    if isinstance(c2, np.ndarray):
+        return c2
     if c2 == "one":
         return None
     if c2 == "heterogeneous":
