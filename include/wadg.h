@@ -128,6 +128,18 @@ int wadg_rhs(wadg_mesh* mesh, const void* Q, void* dQdt, wadg_stream stream);
 int wadg_step(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nsteps, void* traces,
               wadg_stream stream);
 
+/* Solve from t0 to t0 + T (Sec. 5.2 time stepping): nsteps = ceil(T/dt_max)
+ * LSRK(5,4) steps of dt = T/nsteps, exactly the launches of wadg_step.  All
+ * launches of the solve are captured once into a CUDA graph on a library
+ * stream and replayed; the graph is kept in the mesh and reused while Q, res,
+ * traces, t0, dt, nsteps and the operators, sources and receivers are
+ * unchanged.  The work is ordered after the caller's earlier work on `stream`
+ * and before its later work (events); the call does not synchronise.
+ *   traces      device [nsteps][S][R] or NULL.
+ *   nsteps_out  host int receiving nsteps, or NULL. */
+int wadg_solve(wadg_mesh* mesh, void* Q, void* res, double t0, double T, double dt_max, void* traces,
+               int* nsteps_out, wadg_stream stream);
+
 /* Point sources, one per shot: a Ricker wavelet (1-2 pi^2 f0^2 tau^2)
  * exp(-pi^2 f0^2 tau^2), tau = t - t0, times delta(x - x_s) added to the
  * pressure equation at every stage time.

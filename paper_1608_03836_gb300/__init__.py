@@ -29,6 +29,7 @@ from .api import (  # noqa: E402,F401
     wadg_set_operators,
     wadg_set_receivers,
     wadg_set_sources,
+    wadg_solve,
     wadg_status_string,
     wadg_step,
     wadg_step_adjoint,

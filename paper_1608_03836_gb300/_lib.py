@@ -22,6 +22,8 @@ SIGNATURES = {
     "wadg_project": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "wadg_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "wadg_step": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_void_p]),
+    "wadg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, c_double, c_void_p,
+                           ctypes.POINTER(c_int), c_void_p]),
     "wadg_set_sources": (c_int, [c_void_p, P_double, c_double, c_double]),
     "wadg_set_receivers": (c_int, [c_void_p, c_int, P_double]),
     "wadg_energy": (c_int, [c_void_p, c_void_p, P_double, c_void_p]),
@@ -52,7 +54,7 @@ def load() -> ctypes.CDLL:
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1608_03836_gb300.build` "
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_1608_03836_gb300/build.py` "
                           "(there is no CPU fallback)")
     lib = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in SIGNATURES.items():

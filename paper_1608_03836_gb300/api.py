@@ -151,6 +151,17 @@ def wadg_step(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, trace
            "wadg_step", mesh)
 
 
+def wadg_solve(mesh: MeshHandle, Q, res, t0: float, T: float, dt_max: float, traces=None, stream=None) -> int:
+    """Solve to t0 + T with a captured CUDA graph; returns the number of steps."""
+    a = _check_field(mesh, Q, "Q")
+    b = _check_field(mesh, res, "res")
+    n = ctypes.c_int()
+    _check(load().wadg_solve(mesh.handle, a, b, float(t0), float(T), float(dt_max),
+                             None if traces is None else ctypes.c_void_p(traces.data_ptr()), ctypes.byref(n),
+                             _stream(stream)), "wadg_solve", mesh)
+    return n.value
+
+
 def wadg_set_sources(mesh: MeshHandle, xyz, f0: float = 5.0, t0: float | None = None):
     if xyz is None:
         _check(load().wadg_set_sources(mesh.handle, None, float(f0), 0.0), "wadg_set_sources", mesh)

@@ -1,8 +1,10 @@
 """Compile the WADG CUDA library in-tree for sm_103a (GB300).
 
 Every translation unit under csrc/ is compiled in parallel with nvcc and
-linked into ``libwadg.so`` next to this file.  Run ``python -m
-paper_1608_03836_gb300.build`` or ``__graft_entry__.build()``.
+linked into ``libwadg.so`` next to this file.  Run it as a script
+(``python paper_1608_03836_gb300/build.py``) or through
+``__graft_entry__.build()``; importing the package first would try to load
+the library that is being built.
 """
 from __future__ import annotations
 

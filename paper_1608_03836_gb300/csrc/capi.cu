@@ -326,6 +326,10 @@ void wadg_mesh_destroy(wadg_mesh* m) {
   dfree(m->d_src_vec);
   dfree(m->d_rec_col);
   dfree(m->d_rec_vec);
+  if (m->solve_exec) cudaGraphExecDestroy(m->solve_exec);
+  if (m->ev_in) cudaEventDestroy(m->ev_in);
+  if (m->ev_out) cudaEventDestroy(m->ev_out);
+  if (m->solve_stream) cudaStreamDestroy(m->solve_stream);
   delete m;
 }
 
@@ -586,6 +590,7 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
   m->S = shots;
   m->tau_p = tau_p;
   m->tau_u = tau_u;
+  ++m->generation;
   WADG_CUDA(m, cudaDeviceSynchronize());
   return WADG_OK;
 }
@@ -782,6 +787,7 @@ int wadg_set_sources(wadg_mesh* m, const double* xyz, double f0, double t0) {
   m->nsrc = S;
   m->f0 = f0;
   m->t0 = t0;
+  ++m->generation;
   return WADG_OK;
 }
 
@@ -810,6 +816,7 @@ int wadg_set_receivers(wadg_mesh* m, int R, const double* xyz) {
   WADG_CUDA(m, cudaMemcpy(m->d_rec_vec, m->precision == WADG_FP64 ? (void*)v64.data() : (void*)v32.data(),
                           (size_t)n * m->ref.Np * ts, cudaMemcpyHostToDevice));
   m->R = R;
+  ++m->generation;
   return WADG_OK;
 }
 
@@ -957,3 +964,70 @@ int wadg_receivers_adjoint(wadg_mesh* m, const void* weights, void* lamQ, wadg_s
 }
 
 }  // extern "C"
+
+extern "C" int wadg_solve(wadg_mesh* m, void* Q, void* res, double t0, double T, double dt_max, void* traces,
+                          int* nsteps_out, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!Q || !res || Q == res || !aligned16(Q) || !aligned16(res))
+    return fail(m, WADG_EINVAL, "Q and res must be distinct 16-byte aligned device pointers");
+  if (!(T > 0) || !(dt_max > 0) || !std::isfinite(T) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "T, dt");
+  const double ratio = std::ceil(T / dt_max - 1e-12);
+  if (ratio > 1e8) return fail(m, WADG_EINVAL, "too many steps");
+  const int nsteps = std::max(1, (int)ratio);
+  const double dt = T / nsteps;
+  if (nsteps_out) *nsteps_out = nsteps;
+  DeviceGuard g(m->device);
+  if (!m->solve_stream) {
+    WADG_CUDA(m, cudaStreamCreateWithFlags(&m->solve_stream, cudaStreamNonBlocking));
+    WADG_CUDA(m, cudaEventCreateWithFlags(&m->ev_in, cudaEventDisableTiming));
+    WADG_CUDA(m, cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming));
+  }
+  wadg_mesh::SolveKey key;
+  key.Q = Q;
+  key.res = res;
+  key.traces = traces;
+  key.t0 = t0;
+  key.dt = dt;
+  key.nsteps = nsteps;
+  key.precision = m->precision;
+  key.S = m->S;
+  key.R = m->R;
+  key.nsrc = m->nsrc;
+  key.generation = m->generation;
+  const wadg_mesh::SolveKey& k0 = m->solve_key;
+  const bool same = m->solve_exec && k0.Q == key.Q && k0.res == key.res && k0.traces == key.traces &&
+                    k0.t0 == key.t0 && k0.dt == key.dt && k0.nsteps == key.nsteps && k0.precision == key.precision &&
+                    k0.S == key.S && k0.R == key.R && k0.nsrc == key.nsrc && k0.generation == key.generation;
+  if (!same) {
+    if (m->solve_exec) {
+      WADG_CUDA(m, cudaStreamSynchronize(m->solve_stream));
+      cudaGraphExecDestroy(m->solve_exec);
+      m->solve_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    WADG_CUDA(m, cudaStreamBeginCapture(m->solve_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = m->precision == WADG_FP64 ? step_t<double>(m, Q, res, t0, dt, nsteps, traces, m->solve_stream)
+                                       : step_t<float>(m, Q, res, t0, dt, nsteps, traces, m->solve_stream);
+    cudaError_t e = cudaStreamEndCapture(m->solve_stream, &graph);
+    if (rc != WADG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(m, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&m->solve_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      m->solve_exec = nullptr;
+      return cuda_fail(m, e, "cudaGraphInstantiate");
+    }
+    m->solve_key = key;
+  }
+  // order the graph after the caller's prior work and the caller's later work after it
+  WADG_CUDA(m, cudaEventRecord(m->ev_in, (cudaStream_t)stream));
+  WADG_CUDA(m, cudaStreamWaitEvent(m->solve_stream, m->ev_in, 0));
+  WADG_CUDA(m, cudaGraphLaunch(m->solve_exec, m->solve_stream));
+  WADG_CUDA(m, cudaEventRecord(m->ev_out, m->solve_stream));
+  WADG_CUDA(m, cudaStreamWaitEvent((cudaStream_t)stream, m->ev_out, 0));
+  return WADG_OK;
+}

@@ -124,5 +124,18 @@ struct wadg_mesh {
   int R = 0;
   int32_t* d_rec_col = nullptr;   // [S][R] column index k*S+s
   void* d_rec_vec = nullptr;      // [S][R][Np]
+  // wadg_solve: captured graph of the last solve and its key
+  cudaStream_t solve_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t solve_exec = nullptr;
+  struct SolveKey {
+    void* Q = nullptr;
+    void* res = nullptr;
+    void* traces = nullptr;
+    double t0 = 0, dt = 0;
+    int nsteps = -1, precision = -1, S = -1, R = -1, nsrc = -1;
+    uint64_t generation = 0;
+  } solve_key;
+  uint64_t generation = 0;  // bumped by every call that changes operators, sources or receivers
   std::string last_error;
 };

@@ -1,0 +1,70 @@
+"""wadg_solve (captured CUDA graph) and the full c0 solve against stored oracle values."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_util import library_mesh, make_mesh_inputs, random_Q, to_torch
+from synthetic import standing_wave
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c0_standing_wave.json")
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1608_03836_gb300 as lib
+    return lib
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_solve_graph_equals_steps(W, precision):
+    """The captured graph replays exactly the launches of wadg_step: bitwise
+    equal results, also on a second (replayed) call, with sources/receivers."""
+    import torch
+    from synthetic import source_positions, receiver_positions
+    VXYZ, EToV, geom = make_mesh_inputs(2, 3)
+    m = library_mesh(VXYZ, EToV, geom, 3, precision, shots=2, c2="heterogeneous")
+    W.wadg_set_sources(m, source_positions(2), 5.0, 0.05)
+    W.wadg_set_receivers(m, receiver_positions(4).reshape(2, 2, 3))
+    Q0 = to_torch(random_Q(m.K, 2, m.Np, 4), m.dtype)
+    T, dtmax = 0.05, 0.004
+    nst = int(np.ceil(T / dtmax))
+    outs = []
+    for rep in range(2):
+        Q, R = Q0.clone(), torch.zeros_like(Q0)
+        tr = torch.zeros((nst, 2, 2), dtype=m.dtype, device="cuda")
+        n = W.wadg_solve(m, Q, R, 0.0, T, dtmax, tr)
+        outs.append((Q.clone(), R.clone(), tr.clone(), n))
+    Qs, Rs = Q0.clone(), torch.zeros_like(Q0)
+    trs = torch.zeros((nst, 2, 2), dtype=m.dtype, device="cuda")
+    W.wadg_step(m, Qs, Rs, 0.0, T / nst, nst, trs)
+    torch.cuda.synchronize()
+    for Q, R, tr, n in outs:
+        assert n == nst
+        assert torch.equal(Q, Qs) and torch.equal(R, Rs) and torch.equal(tr, trs)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_c0_standing_wave_matches_oracle_solve(W, precision):
+    """c0: 48 tets, N = 3, T = 0.25.  The FP64 GPU error equals the oracle's
+    (same discrete solution) to 1e-9 relative; FP32 is within 1.05x of it
+    (equal L2 error)."""
+    import torch
+    g = json.load(open(GOLDEN))
+    VXYZ, EToV, geom = make_mesh_inputs(2, 3)
+    m = library_mesh(VXYZ, EToV, geom, 3, precision)
+    xq = W.wadg_volume_points(m)
+    Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
+    W.wadg_project(m, to_torch(standing_wave(xq, 0.0)[:, :, None, :], torch.float64), Q)
+    R = torch.zeros_like(Q)
+    n = W.wadg_solve(m, Q, R, 0.0, g["T"], g["dt_cfl"])
+    assert n == g["nsteps"]
+    err = W.wadg_l2_error(m, Q, to_torch(standing_wave(xq, g["T"])[:, :, None, :], torch.float64), 1)
+    want = g["wadg"]["l2_error_p_volume_rule"]
+    tol = 1e-9 if precision == "fp64" else 0.05
+    assert abs(err - want) < tol * want, (err, want)
