@@ -267,6 +267,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
     args = ap.parse_args()
@@ -326,6 +327,15 @@ def main():
         del Q64, m64
     variants["fp32"] = {"value": value, "ms_per_step": ms_per_step, "stage_ms": stage_ms,
                         "achieved_tflops": achieved_tf, "achieved_gbs": achieved_gbs, "dtype": "f32"}
+    if not args.no_tc:
+        mtc, Qtc = build_case(W, "fp32_3xbf16", rank)
+        ttc, stc = time_steps(W, mtc, Qtc, args.steps, 3)
+        W.wadg_device_status(mtc)
+        mstc = ttc / args.steps
+        variants["fp32_3xbf16"] = {"value": ws * dof * 5 / (mstc * 1e-3), "ms_per_step": mstc, "stage_ms": stc,
+                                   "achieved_tflops": F * K / (stc * 1e-3) / 1e12,
+                                   "achieved_gbs": B * K / (stc * 1e-3) / 1e9, "dtype": "f32 (bf16x3 products)"}
+        del Qtc, mtc
 
     if rank != 0:
         return

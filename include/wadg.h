@@ -62,7 +62,11 @@ enum wadg_status {
 
 enum wadg_precision {
     WADG_FP64 = 0,          /* FP64 fields, FP64 arithmetic (CUDA cores)      */
-    WADG_FP32 = 1           /* FP32 fields, FP32 arithmetic (CUDA cores)      */
+    WADG_FP32 = 1,          /* FP32 fields, FP32 arithmetic (CUDA cores)      */
+    WADG_FP32_3XBF16 = 3    /* FP32 fields; the dense products of the stage on
+                               the tensor cores with split bf16 operands
+                               (hi*hi + hi*lo + lo*hi, FP32 accumulation);
+                               N <= 4.  Adjoint and diagnostics as WADG_FP32. */
 };
 
 /* Library version as major*10000 + minor*100 + patch. */
@@ -96,6 +100,11 @@ int wadg_mesh_create(int N, int64_t Nv, const double* VXYZ, int64_t K, const int
  * May be called again to change any of these. */
 int wadg_set_operators(wadg_mesh* mesh, int precision, int shots, double tau_p, double tau_u,
                        const double* c2q);
+
+/* Status of the device-side checks: synchronises `stream` and returns
+ * WADG_ETIMEOUT if a bounded wait inside a tensor-core kernel expired since
+ * the last call (the flag is then cleared), WADG_OK otherwise. */
+int wadg_device_status(wadg_mesh* mesh, wadg_stream stream);
 
 /* Sizes: info[0..7] = N, K, Np, Nq, Nfp, Nfq, S, precision (S, precision are
  * -1 before wadg_set_operators). */

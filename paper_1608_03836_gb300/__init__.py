@@ -14,6 +14,8 @@ load()
 from .api import (  # noqa: E402,F401
     WADG_FP32,
     WADG_FP64,
+    WADG_FP32_3XBF16,
+    wadg_device_status,
     MeshHandle,
     wadg_energy,
     wadg_energy_noalloc,

@@ -29,8 +29,7 @@ def _full_Q(mesh, p0):
 class _ReceiverTraces(torch.autograd.Function):
     @staticmethod
     def forward(ctx, p0, c2q, mesh, dt, nsteps, checkpoint, t0):
-        W.wadg_set_operators(mesh, "fp64" if mesh.precision == W.WADG_FP64 else "fp32", mesh.S, mesh.tau_p,
-                             mesh.tau_u, c2q.detach().cpu().numpy())
+        W.wadg_set_operators(mesh, mesh.precision, mesh.S, mesh.tau_p, mesh.tau_u, c2q.detach().cpu().numpy())
         Q = _full_Q(mesh, p0.detach())
         R = torch.zeros_like(Q)
         traces = torch.zeros((nsteps, mesh.S, mesh.R), dtype=mesh.dtype, device="cuda")

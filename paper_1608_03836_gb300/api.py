@@ -13,8 +13,8 @@ import numpy as np
 
 from ._lib import WadgError, load
 
-WADG_FP64, WADG_FP32 = 0, 1
-PRECISIONS = {"fp64": WADG_FP64, "fp32": WADG_FP32}
+WADG_FP64, WADG_FP32, WADG_FP32_3XBF16 = 0, 1, 3
+PRECISIONS = {"fp64": WADG_FP64, "fp32": WADG_FP32, "fp32_3xbf16": WADG_FP32_3XBF16}
 
 
 def _check(status: int, where: str, mesh=None):
@@ -96,6 +96,11 @@ def wadg_set_operators(mesh: MeshHandle, precision="fp64", shots: int = 1, tau_p
     mesh.S = int(shots)
     mesh.precision = int(prec)
     mesh.tau_p, mesh.tau_u = float(tau_p), float(tau_u)
+
+
+def wadg_device_status(mesh: MeshHandle, stream=None):
+    """Raises WadgError (WADG_ETIMEOUT) if a bounded device wait expired."""
+    _check(load().wadg_device_status(mesh.handle, _stream(stream)), "wadg_device_status", mesh)
 
 
 def wadg_reference_rules(N: int):

@@ -322,6 +322,8 @@ void wadg_mesh_destroy(wadg_mesh* m) {
   if (m->ops32.base) cudaFree(m->ops32.base);
   dfree(m->d_Qtmp);
   dfree(m->d_red);
+  dfree(m->d_tcops);
+  dfree(m->d_err);
   dfree(m->d_src_elem);
   dfree(m->d_src_vec);
   dfree(m->d_rec_col);
@@ -347,6 +349,8 @@ int wadg_mesh_create(int N, int64_t Nv, const double* VXYZ, int64_t K, const int
     return WADG_EUNSUPPORTED;
   }
   cudaGetDevice(&m->device);
+  cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+  if (m->num_sms <= 0) m->num_sms = 1;
   m->N = N;
   m->K = K;
   const RefOps& o = m->ref;
@@ -532,8 +536,10 @@ int wadg_volume_points(const wadg_mesh* m, double* xyz) {
 
 int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, double tau_u, const double* c2q) {
   if (!m) return WADG_EINVAL;
-  if (precision != WADG_FP64 && precision != WADG_FP32)
+  if (precision != WADG_FP64 && precision != WADG_FP32 && precision != WADG_FP32_3XBF16)
     return fail(m, WADG_EUNSUPPORTED, "precision %d is not built", precision);
+  if (precision == WADG_FP32_3XBF16 && m->N > 4)
+    return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 4");
   if (shots < 1 || shots > (1 << 20)) return fail(m, WADG_EINVAL, "shots=%d", shots);
   if (!(tau_p >= 0) || !(tau_u >= 0)) return fail(m, WADG_EINVAL, "penalties must be >= 0");
   DeviceGuard g(m->device);
@@ -568,6 +574,16 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
       int st = upload_ops<float>(m, m->ops32);
       if (st != WADG_OK) return st;
     }
+    if (precision == WADG_FP32_3XBF16 && !m->d_tcops) {
+      std::vector<uint8_t> packed;
+      if (!pack_tc_ops(m->N, m->ref, packed)) return fail(m, WADG_EUNSUPPORTED, "tensor-core tables");
+      WADG_CUDA(m, cudaMalloc((void**)&m->d_tcops, packed.size()));
+      WADG_CUDA(m, cudaMemcpy(m->d_tcops, packed.data(), packed.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  if (!m->d_err) {
+    WADG_CUDA(m, cudaMalloc((void**)&m->d_err, sizeof(int)));
+    WADG_CUDA(m, cudaMemset(m->d_err, 0, sizeof(int)));
   }
   const size_t qbytes = (size_t)4 * K * shots * Np * ts;
   if (qbytes != m->qtmp_bytes) {
@@ -617,6 +633,24 @@ StageParams<T> base_params(const wadg_mesh* m) {
   return p;
 }
 
+// Stage launch for the mesh's precision: RHS and LSRK stages of
+// WADG_FP32_3XBF16 run on the tensor cores, everything else on CUDA cores.
+template <typename T>
+cudaError_t stage_launch(const wadg_mesh* m, const StageParams<T>& p, int mode, cudaStream_t st) {
+  return launch_stage<T>(m->N, p, mode, st);
+}
+template <>
+cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p, int mode, cudaStream_t st) {
+  if (m->precision == WADG_FP32_3XBF16 && (mode == 0 || mode == 1)) {
+    TcStageParams P;
+    P.s = p;
+    P.ops = m->d_tcops;
+    P.err = m->d_err;
+    return launch_stage_tc(m->N, P, mode, m->num_sms, st);
+  }
+  return launch_stage<float>(m->N, p, mode, st);
+}
+
 int check_ready(wadg_mesh* m) {
   if (!m) return WADG_EINVAL;
   if (m->precision < 0) return fail(m, WADG_ESTATE, "wadg_set_operators has not been called");
@@ -628,7 +662,7 @@ int rhs_t(wadg_mesh* m, const void* Q, void* dQdt, cudaStream_t st) {
   StageParams<T> p = base_params<T>(m);
   p.Qin = (const T*)Q;
   p.out = (T*)dQdt;
-  cudaError_t e = launch_stage<T>(m->N, p, 0, st);
+  cudaError_t e = stage_launch<T>(m, p, 0, st);
   return e == cudaSuccess ? WADG_OK : cuda_fail(m, e, "stage kernel (rhs)");
 }
 
@@ -659,7 +693,7 @@ int step_t(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, v
       p.rk_a = (T)kRkA[s];
       p.rk_b = (T)kRkB[s];
       p.src_amp = (T)(m->nsrc > 0 ? ricker(t + kRkC[s] * dt, m->f0, m->t0) : 0.0);
-      cudaError_t e = launch_stage<T>(m->N, p, 1, st);
+      cudaError_t e = stage_launch<T>(m, p, 1, st);
       if (e != cudaSuccess) return cuda_fail(m, e, "stage kernel (lsrk)");
       std::swap(cur, other);
     }
@@ -868,7 +902,7 @@ int step_record_t(wadg_mesh* m, void* Q, void* res, double t0, double dt, void* 
     p.rk_b = (T)kRkB[s];
     p.src_amp = (T)(m->nsrc > 0 ? ricker(t0 + kRkC[s] * dt, m->f0, m->t0) : 0.0);
     p.yrec = ystore ? (T*)ystore + s * ny : nullptr;
-    cudaError_t e = launch_stage<T>(m->N, p, ystore ? 2 : 1, st);
+    cudaError_t e = ystore ? launch_stage<T>(m->N, p, 2, st) : stage_launch<T>(m, p, 1, st);
     if (e != cudaSuccess) return cuda_fail(m, e, "stage kernel (record)");
     std::swap(cur, other);
   }
@@ -1029,5 +1063,20 @@ extern "C" int wadg_solve(wadg_mesh* m, void* Q, void* res, double t0, double T,
   WADG_CUDA(m, cudaGraphLaunch(m->solve_exec, m->solve_stream));
   WADG_CUDA(m, cudaEventRecord(m->ev_out, m->solve_stream));
   WADG_CUDA(m, cudaStreamWaitEvent((cudaStream_t)stream, m->ev_out, 0));
+  return WADG_OK;
+}
+
+extern "C" int wadg_device_status(wadg_mesh* m, wadg_stream stream) {
+  if (!m) return WADG_EINVAL;
+  if (!m->d_err) return WADG_OK;
+  DeviceGuard g(m->device);
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(m, e, "device status");
+  if (flag) {
+    cudaMemset(m->d_err, 0, sizeof(int));
+    return fail(m, WADG_ETIMEOUT, "a bounded wait in a tensor-core kernel expired");
+  }
   return WADG_OK;
 }

@@ -74,6 +74,15 @@ struct AdjUpdateParams {
   double* dc2 = nullptr;    // [K][Nq] gradient accumulator (nullable)
 };
 
+// Tensor-core stage (FP32 fields, split-bf16 products).
+struct TcStageParams {
+  StageParams<float> s;
+  const uint8_t* ops = nullptr;  // packed split operators: NCH volume chunks, then NCH update chunks
+  int* err = nullptr;            // set to 1 when a bounded wait expires
+};
+cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int grid, cudaStream_t stream);
+bool pack_tc_ops(int N, const RefOps& o, std::vector<uint8_t>& out);
+
 // Launchers, one per (precision, degree); modes as in StageMode.
 template <typename T>
 cudaError_t launch_stage(int N, const StageParams<T>& p, int mode, cudaStream_t stream);
@@ -113,6 +122,9 @@ struct wadg_mesh {
   void* d_fgeo = nullptr;
   wadg::DevOps<double> ops64;
   wadg::DevOps<float> ops32;
+  uint8_t* d_tcops = nullptr;  // split operators of the tensor-core stage
+  int* d_err = nullptr;        // device error flag (bounded waits)
+  int num_sms = 0;
   void* d_Qtmp = nullptr;      // ping-pong buffer for LSRK stages
   size_t qtmp_bytes = 0;
   double* d_red = nullptr;     // reduction scratch

@@ -40,15 +40,18 @@ def _gpu_rhs(W, m, Q):
     return out.double().cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
 @pytest.mark.parametrize("N,n", [(1, 3), (2, 2), (3, 2), (4, 2), (5, 2), (6, 1)])
 def test_rhs_matches_oracle(W, precision, N, n):
+    if precision == "fp32_3xbf16" and N > 4:
+        pytest.skip("the tensor-core stage is built for N <= 4")
     VXYZ, EToV, geom = make_mesh_inputs(n, N)
     om = oracle_case(VXYZ, EToV, geom, N)
     m = library_mesh(VXYZ, EToV, geom, N, precision, c2="heterogeneous")
     Q = random_Q(m.K, 1, m.Np, seed=100 + N)
     want = _oracle_rhs(om, Q[:, :, 0], c2q=oracle_c2(om, "heterogeneous"))
     got = _gpu_rhs(W, m, Q)[:, :, 0]
+    W.wadg_device_status(m)
     l2, mx = rel_errors(got, want)
     print(f"N={N} {precision}: rel L2 {l2:.3e}, rel max {mx:.3e}")
     assert l2 < TOL[precision] and mx < 10 * TOL[precision]
@@ -62,7 +65,7 @@ def test_volume_points_match_oracle_geometry(W):
     assert np.abs(xq - om.xq).max() < 1e-14
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
 def test_shots_and_ragged_tail(W, precision):
     """S = 3 shots of different data on one mesh; K*S = 162 is not a multiple of
     the block width, so the last block is ragged."""
@@ -101,7 +104,7 @@ def test_penalty_parameters(W, tau):
     assert l2 < TOL["fp64"]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
 def test_lsrk_steps_match_oracle(W, precision):
     import torch
     from oracle import wadg as OW
@@ -166,7 +169,7 @@ def test_bad_arguments_are_rejected(W):
     assert e.value.status == -8
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
 def test_sources_and_receivers_match_oracle(W, precision):
     """Two shots, each driven by a Ricker point source at its own seeded
     position, three receivers per shot, four LSRK steps from rest."""
@@ -188,7 +191,7 @@ def test_sources_and_receivers_match_oracle(W, precision):
     Rt = torch.zeros_like(Q)
     traces = torch.zeros((nsteps, S, R), dtype=m.dtype, device="cuda")
     W.wadg_step(m, Q, Rt, 0.0, dt, nsteps, traces)
-    torch.cuda.synchronize()
+    W.wadg_device_status(m)
     got_Q = Q.double().cpu().numpy()
     got_tr = traces.double().cpu().numpy()
     src = OS.PointSet(om, xs)
