@@ -157,6 +157,97 @@ def time_steps(W, m, Q, steps, warmup):
     return total_ms, a.elapsed_time(b) / reps
 
 
+def batched_shots(W, steps):
+    """Shots as columns: the 16^3 x 6 = 24,576-tet N=4 cube with 64 shots of
+    independent (seeded) data sharing the geometry, FP32 and FP32 + split-bf16
+    tensor cores; DOF = 4 K Np S."""
+    import torch
+    from synthetic import warped_cube, random_fields
+    n, N, S = 16, 4, 64
+    VXYZ, EToV, geom = warped_cube(n, N, 0.1)
+    out = {"workload": f"warped cube 16^3x6 = {len(EToV)} tets, N=4, 64 shots (columns K*S = {len(EToV) * S})"}
+    for prec in ("fp32", "fp32_3xbf16"):
+        m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
+        W.wadg_set_operators(m, prec, S, 1.0, 1.0, None)
+        Q = torch.from_numpy(random_fields((4, m.K, S, m.Np), 3).astype(np.float32)).cuda()
+        tot, st = time_steps(W, m, Q, steps, 3)
+        dof = 4 * m.K * S * m.Np
+        out[prec] = {"value": dof * 5 / (tot / steps * 1e-3), "ms_per_step": tot / steps, "stage_ms": st}
+        del Q, m
+        torch.cuda.empty_cache()
+    return out
+
+
+def uneven_batch(W, steps):
+    """12 meshes of uneven size and degree (n_i = 4 + round(12 i/11) hexes per
+    side, N_i = 2 + (i mod 5)) stepped by one persistent launch per stage
+    (autotuned grid), against the same meshes stepped one after another."""
+    import torch
+    from synthetic import warped_cube, random_fields
+    ms, Qs, Rs = [], [], []
+    dof = 0
+    for i in range(12):
+        n, N = 4 + int(round(12 * i / 11)), 2 + (i % 5)
+        VXYZ, EToV, geom = warped_cube(n, N, 0.1)
+        m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
+        W.wadg_set_operators(m, "fp32", 1, 1.0, 1.0, None)
+        ms.append(m)
+        Qs.append(torch.from_numpy(random_fields((4, m.K, 1, m.Np), 10 + i).astype(np.float32)).cuda() * 1e-3)
+        Rs.append(torch.zeros_like(Qs[-1]))
+        dof += 4 * m.K * m.Np
+    b = W.wadg_batch_create(ms)
+    grid = W.wadg_batch_autotune(b, Qs, Rs)
+    dt = 1e-4
+    stream = torch.cuda.current_stream()
+    W.wadg_batch_step(b, Qs, Rs, 0.0, dt, 3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    W.wadg_batch_step(b, Qs, Rs, 0.0, dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / steps
+    e0.record(stream)
+    for _ in range(steps):
+        for m, Q, R in zip(ms, Qs, Rs):
+            W.wadg_step(m, Q, R, 0.0, dt, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / steps
+    info = W.wadg_batch_info(b)
+    return {"workload": "12 warped cubes, n = 4..16, N = 2..6, FP32", "dof": dof, "items": info["items"],
+            "grid": grid, "value": dof * 5 / (t_batch * 1e-3), "ms_per_step": t_batch,
+            "sequential_ms_per_step": t_seq, "launches_per_step": 5, "sequential_launches_per_step": 60}
+
+
+def accuracy(W):
+    """Equal L2 error: the same mesh (16^3 x 6 tets, N = 4, c^2 = 1), standing
+    wave, same dt and steps in every precision; L2 error of p against the
+    analytic solution at T by the volume rule."""
+    import torch
+    from synthetic import warped_cube, standing_wave
+    n, N, T = 16, 4, 0.1
+    VXYZ, EToV, geom = warped_cube(n, N, 0.1)
+    h = 2.0 / n
+    dt_max = 0.5 * (h / 2) / (N + 1) ** 2
+    out = {"workload": f"warped cube 16^3x6, N=4, c^2=1, standing wave to T={T}, dt_max={dt_max:.3e}"}
+    for prec in ("fp64", "fp32", "fp32_3xbf16"):
+        m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
+        W.wadg_set_operators(m, prec, 1, 1.0, 1.0, None)
+        xq = W.wadg_volume_points(m)
+        Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
+        W.wadg_project(m, torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda(), Q)
+        R = torch.zeros_like(Q)
+        nsteps = W.wadg_solve(m, Q, R, 0.0, T, dt_max)
+        err = W.wadg_l2_error(m, Q, torch.from_numpy(standing_wave(xq, T)[:, :, None, :]).cuda(), 1)
+        out[prec] = {"l2_error_p": err, "nsteps": nsteps}
+    e64 = out["fp64"]["l2_error_p"]
+    for prec in ("fp32", "fp32_3xbf16"):
+        out[prec]["ratio_to_fp64"] = out[prec]["l2_error_p"] / e64
+        out[prec]["equal_l2_error"] = bool(out[prec]["l2_error_p"] <= 1.05 * e64)
+    return out
+
+
 def e2e_steps(W, m, Q, steps):
     """Same metric end to end: pinned host Q, res -> device, one step, -> host."""
     import torch
@@ -268,6 +359,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
     args = ap.parse_args()
@@ -337,6 +429,12 @@ def main():
                                    "achieved_gbs": B * K / (stc * 1e-3) / 1e9, "dtype": "f32 (bf16x3 products)"}
         del Qtc, mtc
 
+    extras = {}
+    if not args.no_extras:
+        extras["batched_shots"] = batched_shots(W, max(2, args.steps // 3))
+        extras["uneven_batch"] = uneven_batch(W, max(2, args.steps))
+        extras["accuracy"] = accuracy(W)
+
     if rank != 0:
         return
     line = {
@@ -358,6 +456,7 @@ def main():
         "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
         "variants": variants,
+        **extras,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -217,6 +217,47 @@ int wadg_step_adjoint(wadg_mesh* mesh, void* lamQ, void* lamR, double dt, const 
  * receiver's column.  weights device [S][R] in the mesh precision. */
 int wadg_receivers_adjoint(wadg_mesh* mesh, const void* weights, void* lamQ, wadg_stream stream);
 
+/* ---- Batches of meshes of uneven size and degree -------------------------
+ * Not in the paper, which tunes the number of elements per work-group for
+ * each kernel (Sec. 6.1) but steps one mesh at a time.  A batch steps several
+ * WADG_FP32 meshes together: each LSRK stage is ONE persistent launch over a
+ * work list of (mesh, tile) items, heaviest degree first, with exactly the
+ * arithmetic of wadg_step per mesh (results are bitwise equal).  Point
+ * sources and receivers of the meshes are not applied in batch stepping.
+ * Q[i], res[i]: device [4][K_i][S_i][Np_i] float buffers of mesh i. */
+typedef struct wadg_batch wadg_batch;
+
+/* meshes: host array of `count` handles, each already set to WADG_FP32 on the
+ * same device (WADG_ESTATE otherwise).  The batch keeps the handles (not
+ * owned); destroy it before the meshes. */
+int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out);
+
+/* info[0..3] = meshes, work items, persistent blocks in use, largest
+ * resident grid (occupancy x SMs). */
+int wadg_batch_info(const wadg_batch* batch, int64_t info[4]);
+
+/* Number of persistent blocks (clamped to the number of work items). */
+int wadg_batch_set_grid(wadg_batch* batch, int grid);
+
+/* Autotuner: times right-hand-side launches of the whole batch for
+ * 1, 2, 3, 4, 6, 8 blocks per SM (as occupancy allows) and one block per item,
+ * keeps the fastest and returns it in grid_out (nullable).  Q and res are not
+ * modified; each mesh's work buffer is overwritten.  Synchronises `stream`. */
+int wadg_batch_autotune(wadg_batch* batch, void* const* Q, void* const* res, int* grid_out, wadg_stream stream);
+
+/* nsteps LSRK(5,4) steps of every mesh (5 launches per step in total). */
+int wadg_batch_step(wadg_batch* batch, void* const* Q, void* const* res, double t0, double dt, int nsteps,
+                    wadg_stream stream);
+
+/* As wadg_solve for the whole batch: the launches of the solve are captured
+ * once into a CUDA graph, kept and replayed while the buffers, t0, dt and
+ * nsteps are unchanged. */
+int wadg_batch_solve(wadg_batch* batch, void* const* Q, void* const* res, double t0, double T, double dt_max,
+                     int* nsteps_out, wadg_stream stream);
+
+void wadg_batch_destroy(wadg_batch* batch);
+const char* wadg_batch_last_error(const wadg_batch* batch);
+
 void wadg_mesh_destroy(wadg_mesh* mesh);
 const char* wadg_status_string(int status);
 const char* wadg_last_error(const wadg_mesh* mesh);

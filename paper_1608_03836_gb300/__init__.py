@@ -16,7 +16,16 @@ from .api import (  # noqa: E402,F401
     WADG_FP64,
     WADG_FP32_3XBF16,
     wadg_device_status,
+    BatchHandle,
     MeshHandle,
+    wadg_batch_autotune,
+    wadg_batch_create,
+    wadg_batch_destroy,
+    wadg_batch_info,
+    wadg_batch_last_error,
+    wadg_batch_set_grid,
+    wadg_batch_solve,
+    wadg_batch_step,
     wadg_energy,
     wadg_energy_noalloc,
     wadg_l2_error,

@@ -34,6 +34,17 @@ SIGNATURES = {
     "wadg_step_record": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, c_void_p, c_void_p, c_void_p]),
     "wadg_step_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     "wadg_receivers_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wadg_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p)]),
+    "wadg_batch_info": (c_int, [c_void_p, P_int64]),
+    "wadg_batch_set_grid": (c_int, [c_void_p, c_int]),
+    "wadg_batch_autotune": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                    ctypes.POINTER(c_int), c_void_p]),
+    "wadg_batch_step": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_double, c_double,
+                                c_int, c_void_p]),
+    "wadg_batch_solve": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_double, c_double,
+                                 c_double, ctypes.POINTER(c_int), c_void_p]),
+    "wadg_batch_destroy": (None, [c_void_p]),
+    "wadg_batch_last_error": (ctypes.c_char_p, [c_void_p]),
     "wadg_mesh_destroy": (None, [c_void_p]),
     "wadg_status_string": (ctypes.c_char_p, [c_int]),
     "wadg_last_error": (ctypes.c_char_p, [c_void_p]),

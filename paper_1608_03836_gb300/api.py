@@ -253,6 +253,86 @@ def wadg_receivers_adjoint(mesh: MeshHandle, weights, lamQ, stream=None):
            mesh)
 
 
+class BatchHandle:
+    """Owns a wadg_batch*; keeps its meshes alive."""
+
+    def __init__(self, handle, meshes):
+        self.handle = handle
+        self.meshes = list(meshes)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().wadg_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def _bcheck(status, where, batch=None):
+    if status != 0:
+        detail = ""
+        if batch is not None and batch.handle:
+            detail = (load().wadg_batch_last_error(batch.handle) or b"").decode()
+        raise WadgError(status, where, detail)
+
+
+def _ptr_array(batch, tensors, name):
+    if len(tensors) != len(batch.meshes):
+        raise ValueError(f"{name}: one buffer per mesh")
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, (m, t) in enumerate(zip(batch.meshes, tensors)):
+        arr[i] = _check_field(m, t, f"{name}[{i}]")
+    return arr
+
+
+def wadg_batch_create(meshes) -> BatchHandle:
+    arr = (ctypes.c_void_p * len(meshes))(*[m.handle for m in meshes])
+    out = ctypes.c_void_p()
+    _bcheck(load().wadg_batch_create(arr, len(meshes), ctypes.byref(out)), "wadg_batch_create")
+    return BatchHandle(out, meshes)
+
+
+def wadg_batch_info(batch: BatchHandle) -> dict:
+    info = (ctypes.c_int64 * 4)()
+    _bcheck(load().wadg_batch_info(batch.handle, info), "wadg_batch_info", batch)
+    return {"meshes": info[0], "items": info[1], "grid": info[2], "max_grid": info[3]}
+
+
+def wadg_batch_set_grid(batch: BatchHandle, grid: int):
+    _bcheck(load().wadg_batch_set_grid(batch.handle, int(grid)), "wadg_batch_set_grid", batch)
+
+
+def wadg_batch_autotune(batch: BatchHandle, Q, res, stream=None) -> int:
+    g = ctypes.c_int()
+    _bcheck(load().wadg_batch_autotune(batch.handle, _ptr_array(batch, Q, "Q"), _ptr_array(batch, res, "res"),
+                                       ctypes.byref(g), _stream(stream)), "wadg_batch_autotune", batch)
+    return g.value
+
+
+def wadg_batch_step(batch: BatchHandle, Q, res, t0: float, dt: float, nsteps: int, stream=None):
+    _bcheck(load().wadg_batch_step(batch.handle, _ptr_array(batch, Q, "Q"), _ptr_array(batch, res, "res"),
+                                   float(t0), float(dt), int(nsteps), _stream(stream)), "wadg_batch_step", batch)
+
+
+def wadg_batch_solve(batch: BatchHandle, Q, res, t0: float, T: float, dt_max: float, stream=None) -> int:
+    n = ctypes.c_int()
+    _bcheck(load().wadg_batch_solve(batch.handle, _ptr_array(batch, Q, "Q"), _ptr_array(batch, res, "res"),
+                                    float(t0), float(T), float(dt_max), ctypes.byref(n), _stream(stream)),
+            "wadg_batch_solve", batch)
+    return n.value
+
+
+def wadg_batch_destroy(batch: BatchHandle):
+    if batch.handle:
+        load().wadg_batch_destroy(batch.handle)
+        batch.handle = None
+
+
+def wadg_batch_last_error(batch: BatchHandle) -> str:
+    return (load().wadg_batch_last_error(batch.handle) or b"").decode()
+
+
 def wadg_mesh_destroy(mesh: MeshHandle):
     if mesh.handle:
         load().wadg_mesh_destroy(mesh.handle)

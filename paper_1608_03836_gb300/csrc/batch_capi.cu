@@ -1,0 +1,329 @@
+// C ABI of mesh batches (see include/wadg.h, "Batches").
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "wadg_internal.h"
+
+using namespace wadg;
+
+struct wadg_batch {
+  std::vector<wadg_mesh*> meshes;
+  int device = 0;
+  int nitems = 0;
+  int* d_item_mesh = nullptr;
+  int* d_item_blk = nullptr;
+  int* d_mesh_N = nullptr;
+  size_t smem = 0;
+  int grid = 0;
+  int max_grid = 0;
+  // parameter tables: slot 2*s + parity for LSRK stage s, slot 10 for the RHS
+  StageParams<float>* d_params = nullptr;
+  std::vector<StageParams<float>> h_params;
+  std::vector<const void*> keyQ, keyR;
+  double key_dt = NAN;
+  // captured solve
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> gkeyQ, gkeyR;
+  double gkey_t0 = NAN, gkey_dt = NAN;
+  int gkey_n = -1;
+  std::string last_error;
+};
+
+namespace {
+
+int bfail(wadg_batch* b, int status, const std::string& msg) {
+  if (b) b->last_error = msg;
+  return status;
+}
+
+#define BCUDA(b, call)                                                                       \
+  do {                                                                                       \
+    cudaError_t _e = (call);                                                                 \
+    if (_e != cudaSuccess) return bfail((b), WADG_ECUDA, std::string(#call ": ") + cudaGetErrorString(_e)); \
+  } while (0)
+
+StageParams<float> mesh_params(const wadg_mesh* m) {
+  StageParams<float> p;
+  p.vgeo = (const float*)m->d_vgeo;
+  p.fgeo = (const float*)m->d_fgeo;
+  p.EToE = m->d_EToE;
+  p.fcode = m->d_fcode;
+  p.ops = m->ops32;
+  p.ncols = m->K * m->S;
+  p.S = m->S;
+  p.tau_p = (float)m->tau_p;
+  p.tau_u = (float)m->tau_u;
+  return p;
+}
+
+// (Re)build the parameter tables for these field buffers and step.
+int ensure_tables(wadg_batch* b, void* const* Q, void* const* res, double dt) {
+  const size_t nm = b->meshes.size();
+  bool same = b->d_params && b->key_dt == dt;
+  for (size_t i = 0; same && i < nm; ++i) same = b->keyQ[i] == Q[i] && b->keyR[i] == res[i];
+  if (same) return WADG_OK;
+  b->h_params.assign(11 * nm, StageParams<float>());
+  for (size_t i = 0; i < nm; ++i) {
+    const wadg_mesh* m = b->meshes[i];
+    for (int s = 0; s < 5; ++s)
+      for (int par = 0; par < 2; ++par) {
+        StageParams<float> p = mesh_params(m);
+        p.Qin = (const float*)(par == 0 ? Q[i] : m->d_Qtmp);
+        p.Qout = (float*)(par == 0 ? m->d_Qtmp : Q[i]);
+        p.res = (float*)res[i];
+        p.rk_a = (float)kRkA[s];
+        p.rk_b = (float)kRkB[s];
+        p.dt = (float)dt;
+        b->h_params[(2 * s + par) * nm + i] = p;
+      }
+    StageParams<float> r = mesh_params(m);
+    r.Qin = (const float*)Q[i];
+    r.out = (float*)m->d_Qtmp;
+    b->h_params[10 * nm + i] = r;
+  }
+  BCUDA(b, cudaMemcpy(b->d_params, b->h_params.data(), b->h_params.size() * sizeof(StageParams<float>),
+                      cudaMemcpyHostToDevice));
+  b->keyQ.assign(Q, Q + nm);
+  b->keyR.assign(res, res + nm);
+  b->key_dt = dt;
+  return WADG_OK;
+}
+
+int check_buffers(wadg_batch* b, void* const* Q, void* const* res) {
+  if (!Q || !res) return bfail(b, WADG_EINVAL, "null buffer arrays");
+  for (size_t i = 0; i < b->meshes.size(); ++i) {
+    if (!Q[i] || !res[i] || Q[i] == res[i] || ((uintptr_t)Q[i] & 15u) || ((uintptr_t)res[i] & 15u))
+      return bfail(b, WADG_EINVAL, "each Q[i], res[i] must be distinct 16-byte aligned device pointers");
+    if (b->meshes[i]->precision != WADG_FP32)
+      return bfail(b, WADG_ESTATE, "every mesh of a batch must be set to WADG_FP32");
+  }
+  return WADG_OK;
+}
+
+int enqueue_steps(wadg_batch* b, void* const* Q, int nsteps, cudaStream_t st) {
+  const size_t nm = b->meshes.size();
+  for (int n = 0; n < nsteps; ++n)
+    for (int s = 0; s < 5; ++s) {
+      const int par = (5 * n + s) & 1;
+      cudaError_t e = launch_batch_stage(1, b->d_params + (2 * s + par) * nm, b->d_item_mesh, b->d_item_blk,
+                                         b->d_mesh_N, b->nitems, b->grid, b->smem, st);
+      if (e != cudaSuccess) return bfail(b, WADG_ECUDA, std::string("batch stage: ") + cudaGetErrorString(e));
+    }
+  if ((5 * nsteps) & 1)
+    for (size_t i = 0; i < nm; ++i) {
+      const wadg_mesh* m = b->meshes[i];
+      const size_t bytes = (size_t)4 * m->K * m->S * m->ref.Np * sizeof(float);
+      cudaError_t e = cudaMemcpyAsync(Q[i], m->d_Qtmp, bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return bfail(b, WADG_ECUDA, std::string("copy back: ") + cudaGetErrorString(e));
+    }
+  return WADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void wadg_batch_destroy(wadg_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  cudaFree(b->d_item_mesh);
+  cudaFree(b->d_item_blk);
+  cudaFree(b->d_mesh_N);
+  cudaFree(b->d_params);
+  delete b;
+}
+
+int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
+  if (!out || !meshes || count < 1) return WADG_EINVAL;
+  *out = nullptr;
+  wadg_batch* b = new (std::nothrow) wadg_batch();
+  if (!b) return WADG_ENOMEM;
+  b->meshes.assign(meshes, meshes + count);
+  for (int i = 0; i < count; ++i) {
+    if (!meshes[i] || meshes[i]->precision != WADG_FP32 || meshes[i]->device != meshes[0]->device) {
+      delete b;
+      return WADG_ESTATE;
+    }
+  }
+  b->device = meshes[0]->device;
+  // work items, heaviest degree first
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return meshes[x]->N > meshes[y]->N; });
+  std::vector<int> im, ib, mn(count);
+  for (int i = 0; i < count; ++i) {
+    mn[i] = meshes[i]->N;
+    b->smem = std::max(b->smem, batch_smem_bytes(meshes[i]->N));
+  }
+  for (int oi : order) {
+    const wadg_mesh* m = meshes[oi];
+    const int E = batch_cols_per_block(m->N);
+    const int64_t blocks = (m->K * m->S + E - 1) / E;
+    for (int64_t k = 0; k < blocks; ++k) {
+      im.push_back(oi);
+      ib.push_back((int)k);
+    }
+  }
+  b->nitems = (int)im.size();
+  int nsm = meshes[0]->num_sms;
+  b->max_grid = batch_max_blocks_per_sm(b->smem) * nsm;
+  b->grid = std::min(b->max_grid, std::max(1, b->nitems));
+  bool ok = cudaMalloc((void**)&b->d_item_mesh, im.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc((void**)&b->d_item_blk, ib.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc((void**)&b->d_mesh_N, mn.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc((void**)&b->d_params, 11 * count * sizeof(StageParams<float>)) == cudaSuccess &&
+            cudaMemcpy(b->d_item_mesh, im.data(), im.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b->d_item_blk, ib.data(), ib.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b->d_mesh_N, mn.data(), mn.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    wadg_batch_destroy(b);
+    return WADG_ENOMEM;
+  }
+  *out = b;
+  return WADG_OK;
+}
+
+int wadg_batch_info(const wadg_batch* b, int64_t info[4]) {
+  if (!b || !info) return WADG_EINVAL;
+  info[0] = (int64_t)b->meshes.size();
+  info[1] = b->nitems;
+  info[2] = b->grid;
+  info[3] = b->max_grid;
+  return WADG_OK;
+}
+
+int wadg_batch_set_grid(wadg_batch* b, int grid) {
+  if (!b || grid < 1) return WADG_EINVAL;
+  b->grid = std::min(grid, std::max(1, b->nitems));
+  return WADG_OK;
+}
+
+int wadg_batch_step(wadg_batch* b, void* const* Q, void* const* res, double t0, double dt, int nsteps,
+                    wadg_stream stream) {
+  if (!b) return WADG_EINVAL;
+  int st = check_buffers(b, Q, res);
+  if (st != WADG_OK) return st;
+  if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) return bfail(b, WADG_EINVAL, "nsteps/dt/t0");
+  st = ensure_tables(b, Q, res, dt);
+  if (st != WADG_OK) return st;
+  return enqueue_steps(b, Q, nsteps, (cudaStream_t)stream);
+}
+
+// Times each candidate number of persistent blocks on right-hand-side
+// launches (the fields are not modified) and keeps the fastest.
+int wadg_batch_autotune(wadg_batch* b, void* const* Q, void* const* res, int* grid_out, wadg_stream stream) {
+  if (!b) return WADG_EINVAL;
+  int st = check_buffers(b, Q, res);
+  if (st != WADG_OK) return st;
+  st = ensure_tables(b, Q, res, b->key_dt == b->key_dt ? b->key_dt : 0.0);
+  if (st != WADG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nsm = b->meshes[0]->num_sms;
+  std::vector<int> cands;
+  for (int mult : {1, 2, 3, 4, 6, 8})
+    if (mult * nsm <= b->max_grid) cands.push_back(mult * nsm);
+  cands.push_back(std::min(b->nitems, 65535 * 16));
+  cudaEvent_t e0, e1;
+  BCUDA(b, cudaEventCreate(&e0));
+  BCUDA(b, cudaEventCreate(&e1));
+  const size_t nm = b->meshes.size();
+  float best = 1e30f;
+  int best_g = b->grid;
+  for (int g : cands) {
+    g = std::max(1, std::min(g, b->nitems));
+    for (int rep = 0; rep < 2; ++rep)
+      launch_batch_stage(0, b->d_params + 10 * nm, b->d_item_mesh, b->d_item_blk, b->d_mesh_N, b->nitems, g, b->smem,
+                         s);
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 5; ++rep)
+      launch_batch_stage(0, b->d_params + 10 * nm, b->d_item_mesh, b->d_item_blk, b->d_mesh_N, b->nitems, g, b->smem,
+                         s);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return bfail(b, WADG_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_g = g;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->grid = best_g;
+  if (grid_out) *grid_out = best_g;
+  return WADG_OK;
+}
+
+int wadg_batch_solve(wadg_batch* b, void* const* Q, void* const* res, double t0, double T, double dt_max,
+                     int* nsteps_out, wadg_stream stream) {
+  if (!b) return WADG_EINVAL;
+  int st = check_buffers(b, Q, res);
+  if (st != WADG_OK) return st;
+  if (!(T > 0) || !(dt_max > 0) || !std::isfinite(T) || !std::isfinite(t0)) return bfail(b, WADG_EINVAL, "T, dt");
+  const double ratio = std::ceil(T / dt_max - 1e-12);
+  if (ratio > 1e8) return bfail(b, WADG_EINVAL, "too many steps");
+  const int nsteps = std::max(1, (int)ratio);
+  const double dt = T / nsteps;
+  if (nsteps_out) *nsteps_out = nsteps;
+  st = ensure_tables(b, Q, res, dt);
+  if (st != WADG_OK) return st;
+  if (!b->stream) {
+    BCUDA(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    BCUDA(b, cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+    BCUDA(b, cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+  }
+  const size_t nm = b->meshes.size();
+  bool same = b->exec && b->gkey_t0 == t0 && b->gkey_dt == dt && b->gkey_n == nsteps;
+  for (size_t i = 0; same && i < nm; ++i) same = b->gkeyQ[i] == Q[i] && b->gkeyR[i] == res[i];
+  if (!same) {
+    if (b->exec) {
+      BCUDA(b, cudaStreamSynchronize(b->stream));
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_steps(b, Q, nsteps, b->stream);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (rc != WADG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return bfail(b, WADG_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      return bfail(b, WADG_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    }
+    b->gkeyQ.assign(Q, Q + nm);
+    b->gkeyR.assign(res, res + nm);
+    b->gkey_t0 = t0;
+    b->gkey_dt = dt;
+    b->gkey_n = nsteps;
+  }
+  BCUDA(b, cudaEventRecord(b->ev_in, (cudaStream_t)stream));
+  BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+  BCUDA(b, cudaGraphLaunch(b->exec, b->stream));
+  BCUDA(b, cudaEventRecord(b->ev_out, b->stream));
+  BCUDA(b, cudaStreamWaitEvent((cudaStream_t)stream, b->ev_out, 0));
+  return WADG_OK;
+}
+
+const char* wadg_batch_last_error(const wadg_batch* b) { return b ? b->last_error.c_str() : ""; }
+
+}  // extern "C"

@@ -45,16 +45,6 @@ cudaError_t launch_adj_update(int N, const AdjUpdateParams<T>& p, int lsrk, cuda
   }
 }
 
-// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients
-// (the scheme named in Sec. 5.2 of the paper, which does not print them).
-static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
-                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
-static const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
-                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
-                               2277821191437.0 / 14882151754819.0};
-static const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
-                               2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
-
 static const int kFaceV[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
 
 }  // namespace wadg

@@ -130,15 +130,15 @@ __device__ __forceinline__ void tile_dot(const T* __restrict__ A, const T* in, i
   }
 }
 
+// One block's tile: columns [blk*E, blk*E + E) of the mesh described by p.
 template <typename T, int N, int E, int MODE>
-__global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<T> p) {
+__device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk, unsigned char* smem_raw) {
   using Dm = Dims<N>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NFP = Dm::NFP, NFQ = Dm::NFQ;
   constexpr int NQP = Dm::NQP, NPP = Dm::NPP, NFQP = Dm::NFQP, NFPP = Dm::NFPP;
   constexpr int NG = E / 4;
   constexpr int NT = kStageThreads;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sQ = reinterpret_cast<T*>(smem_raw);  // [4][NP][E]
   T* sR = sQ + 4 * NP * E;                 // [4][NP][E]  load vector b (un-inverted)
   T* sP = sR + 4 * NP * E;                 // [2][NP][E]  partial pressure volume terms
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
   T* sFQ = sX + 7 * 4 * NFP * E;           // [7][4 NFQ][E] face-point values
 
   const int tid = threadIdx.x;
-  const int64_t col0 = (int64_t)blockIdx.x * E;
+  const int64_t col0 = blk * E;
   const int64_t ncols = p.ncols;
   const int64_t fs = ncols * NP;  // field stride
   const int S = p.S;
@@ -434,6 +434,12 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
       }
     }
   }
+}
+
+template <typename T, int N, int E, int MODE>
+__global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage_tile<T, N, E, MODE>(p, blockIdx.x, smem_raw);
 }
 
 template <typename T, int N, int MODE>

@@ -13,6 +13,16 @@
 
 namespace wadg {
 
+// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients
+// (the scheme named in Sec. 5.2 of the paper, which does not print them).
+inline constexpr double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                                   -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+inline constexpr double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                                   1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                                   2277821191437.0 / 14882151754819.0};
+inline constexpr double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                                   2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
 // Device copies of the reference operators in precision T, stored "k-major"
 // (A[k][m], consecutive output rows m contiguous, the row count m padded with
 // zero rows to a multiple of 4: Nq -> NQP etc.) so that a thread owning 4
@@ -82,6 +92,13 @@ struct TcStageParams {
 };
 cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int grid, cudaStream_t stream);
 bool pack_tc_ops(int N, const RefOps& o, std::vector<uint8_t>& out);
+
+// Batches of FP32 meshes (batch.cu).
+int batch_cols_per_block(int N);
+size_t batch_smem_bytes(int N);
+int batch_max_blocks_per_sm(size_t smem);
+cudaError_t launch_batch_stage(int mode, const StageParams<float>* params, const int* item_mesh, const int* item_blk,
+                               const int* mesh_N, int nitems, int grid, size_t smem, cudaStream_t st);
 
 // Launchers, one per (precision, degree); modes as in StageMode.
 template <typename T>

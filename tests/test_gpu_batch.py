@@ -1,0 +1,68 @@
+"""Batches of meshes of uneven size and degree: one persistent launch per
+stage gives bitwise the per-mesh results; the autotuner and the captured
+solve keep them."""
+import numpy as np
+import pytest
+
+from gpu_util import library_mesh, make_mesh_inputs, random_Q, to_torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1608_03836_gb300 as lib
+    return lib
+
+
+def _meshes(W, spec):
+    ms = []
+    for i, (n, N, S) in enumerate(spec):
+        VXYZ, EToV, geom = make_mesh_inputs(n, N)
+        ms.append(library_mesh(VXYZ, EToV, geom, N, "fp32", shots=S, c2="heterogeneous"))
+    return ms
+
+
+def test_batch_step_equals_per_mesh_steps(W):
+    import torch
+    spec = [(2, 2, 1), (3, 5, 1), (2, 3, 2), (1, 6, 1), (2, 4, 1), (2, 1, 3)]
+    ms = _meshes(W, spec)
+    Q0 = [to_torch(random_Q(m.K, m.S, m.Np, 40 + i), torch.float32) for i, m in enumerate(ms)]
+    dt, ns = 1e-3, 3
+    ref = []
+    for m, q in zip(ms, Q0):
+        Q, R = q.clone(), torch.zeros_like(q)
+        W.wadg_step(m, Q, R, 0.0, dt, ns)
+        ref.append((Q, R))
+    b = W.wadg_batch_create(ms)
+    info = W.wadg_batch_info(b)
+    assert info["meshes"] == len(ms) and info["items"] > 0
+    Qs = [q.clone() for q in Q0]
+    Rs = [torch.zeros_like(q) for q in Q0]
+    g = W.wadg_batch_autotune(b, Qs, Rs)
+    assert 1 <= g
+    W.wadg_batch_step(b, Qs, Rs, 0.0, dt, ns)
+    torch.cuda.synchronize()
+    for (Qr, Rr), Q, R, q0 in zip(ref, Qs, Rs, Q0):
+        assert torch.equal(Qr, Q) and torch.equal(Rr, R)
+        assert not torch.equal(Q, q0)
+    # captured solve, replayed twice from the same start
+    for _ in range(2):
+        Qg = [q.clone() for q in Q0]
+        Rg = [torch.zeros_like(q) for q in Q0]
+        n = W.wadg_batch_solve(b, Qg, Rg, 0.0, dt * ns, dt)
+        torch.cuda.synchronize()
+        assert n == ns
+        for (Qr, Rr), Q, R in zip(ref, Qg, Rg):
+            assert torch.equal(Qr, Q) and torch.equal(Rr, R)
+
+
+def test_batch_rejects_other_precisions(W):
+    VXYZ, EToV, geom = make_mesh_inputs(1, 2)
+    m = library_mesh(VXYZ, EToV, geom, 2, "fp64")
+    with pytest.raises(W.WadgError) as e:
+        W.wadg_batch_create([m])
+    assert e.value.status == -5
