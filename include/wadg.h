@@ -233,16 +233,20 @@ typedef struct wadg_batch wadg_batch;
 int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out);
 
 /* info[0..3] = meshes, work items, persistent blocks in use, largest
- * resident grid (occupancy x SMs). */
+ * resident grid (occupancy x SMs) for the tile rule in use. */
 int wadg_batch_info(const wadg_batch* batch, int64_t info[4]);
 
 /* Number of persistent blocks (clamped to the number of work items). */
 int wadg_batch_set_grid(wadg_batch* batch, int grid);
 
-/* Autotuner: times right-hand-side launches of the whole batch for
- * 1, 2, 3, 4, 6, 8 blocks per SM (as occupancy allows) and one block per item,
- * keeps the fastest and returns it in grid_out (nullable).  Q and res are not
- * modified; each mesh's work buffer is overwritten.  Synchronises `stream`. */
+/* Autotuner: for each of two tile rules (the single-mesh columns-per-tile
+ * rule, and one capped so that every degree fits three blocks per SM), times
+ * right-hand-side launches of the whole batch with 1, 2, 3, 4, 6, 8 blocks
+ * per SM (as occupancy allows) and one block per item; keeps the fastest rule
+ * and grid and returns the grid in grid_out (nullable).  Q and res are not
+ * modified; each mesh's work buffer is overwritten.  Synchronises `stream`.
+ * Either rule gives bitwise the results of wadg_step: every column's
+ * products are accumulated in the same order whatever the tile width. */
 int wadg_batch_autotune(wadg_batch* batch, void* const* Q, void* const* res, int* grid_out, wadg_stream stream);
 
 /* nsteps LSRK(5,4) steps of every mesh (5 launches per step in total). */

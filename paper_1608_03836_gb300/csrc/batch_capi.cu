@@ -13,13 +13,16 @@ using namespace wadg;
 struct wadg_batch {
   std::vector<wadg_mesh*> meshes;
   int device = 0;
-  int nitems = 0;
-  int* d_item_mesh = nullptr;
-  int* d_item_blk = nullptr;
+  // work lists for the two tile rules (see batch.cu)
+  int rule = 0;
+  int nitems_r[2] = {0, 0};
+  int* d_item_mesh_r[2] = {nullptr, nullptr};
+  int* d_item_blk_r[2] = {nullptr, nullptr};
+  size_t smem_r[2] = {0, 0};
+  int max_grid_r[2] = {0, 0};
   int* d_mesh_N = nullptr;
-  size_t smem = 0;
   int grid = 0;
-  int max_grid = 0;
+  int nitems() const { return nitems_r[rule]; }
   // parameter tables: slot 2*s + parity for LSRK stage s, slot 10 for the RHS
   StageParams<float>* d_params = nullptr;
   std::vector<StageParams<float>> h_params;
@@ -111,8 +114,9 @@ int enqueue_steps(wadg_batch* b, void* const* Q, int nsteps, cudaStream_t st) {
   for (int n = 0; n < nsteps; ++n)
     for (int s = 0; s < 5; ++s) {
       const int par = (5 * n + s) & 1;
-      cudaError_t e = launch_batch_stage(1, b->d_params + (2 * s + par) * nm, b->d_item_mesh, b->d_item_blk,
-                                         b->d_mesh_N, b->nitems, b->grid, b->smem, st);
+      const int r = b->rule;
+      cudaError_t e = launch_batch_stage(1, r, b->d_params + (2 * s + par) * nm, b->d_item_mesh_r[r],
+                                         b->d_item_blk_r[r], b->d_mesh_N, b->nitems_r[r], b->grid, b->smem_r[r], st);
       if (e != cudaSuccess) return bfail(b, WADG_ECUDA, std::string("batch stage: ") + cudaGetErrorString(e));
     }
   if ((5 * nsteps) & 1)
@@ -135,8 +139,10 @@ void wadg_batch_destroy(wadg_batch* b) {
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->stream) cudaStreamDestroy(b->stream);
-  cudaFree(b->d_item_mesh);
-  cudaFree(b->d_item_blk);
+  for (int r = 0; r < 2; ++r) {
+    cudaFree(b->d_item_mesh_r[r]);
+    cudaFree(b->d_item_blk_r[r]);
+  }
   cudaFree(b->d_mesh_N);
   cudaFree(b->d_params);
   delete b;
@@ -155,39 +161,41 @@ int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
     }
   }
   b->device = meshes[0]->device;
-  // work items, heaviest degree first
+  // work items for each tile rule, heaviest degree first
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return meshes[x]->N > meshes[y]->N; });
-  std::vector<int> im, ib, mn(count);
-  for (int i = 0; i < count; ++i) {
-    mn[i] = meshes[i]->N;
-    b->smem = std::max(b->smem, batch_smem_bytes(meshes[i]->N));
-  }
-  for (int oi : order) {
-    const wadg_mesh* m = meshes[oi];
-    const int E = batch_cols_per_block(m->N);
-    const int64_t blocks = (m->K * m->S + E - 1) / E;
-    for (int64_t k = 0; k < blocks; ++k) {
-      im.push_back(oi);
-      ib.push_back((int)k);
-    }
-  }
-  b->nitems = (int)im.size();
-  int nsm = meshes[0]->num_sms;
-  b->max_grid = batch_max_blocks_per_sm(b->smem) * nsm;
-  b->grid = std::min(b->max_grid, std::max(1, b->nitems));
-  bool ok = cudaMalloc((void**)&b->d_item_mesh, im.size() * sizeof(int)) == cudaSuccess &&
-            cudaMalloc((void**)&b->d_item_blk, ib.size() * sizeof(int)) == cudaSuccess &&
-            cudaMalloc((void**)&b->d_mesh_N, mn.size() * sizeof(int)) == cudaSuccess &&
+  std::vector<int> mn(count);
+  for (int i = 0; i < count; ++i) mn[i] = meshes[i]->N;
+  const int nsm = meshes[0]->num_sms;
+  bool ok = cudaMalloc((void**)&b->d_mesh_N, mn.size() * sizeof(int)) == cudaSuccess &&
             cudaMalloc((void**)&b->d_params, 11 * count * sizeof(StageParams<float>)) == cudaSuccess &&
-            cudaMemcpy(b->d_item_mesh, im.data(), im.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(b->d_item_blk, ib.data(), ib.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b->d_mesh_N, mn.data(), mn.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+  for (int r = 0; r < 2 && ok; ++r) {
+    std::vector<int> im, ib;
+    for (int i = 0; i < count; ++i) b->smem_r[r] = std::max(b->smem_r[r], batch_smem_bytes(meshes[i]->N, r));
+    for (int oi : order) {
+      const wadg_mesh* m = meshes[oi];
+      const int E = batch_cols_per_block(m->N, r);
+      const int64_t blocks = (m->K * m->S + E - 1) / E;
+      for (int64_t k = 0; k < blocks; ++k) {
+        im.push_back(oi);
+        ib.push_back((int)k);
+      }
+    }
+    b->nitems_r[r] = (int)im.size();
+    b->max_grid_r[r] = batch_max_blocks_per_sm(r, b->smem_r[r]) * nsm;
+    ok = cudaMalloc((void**)&b->d_item_mesh_r[r], im.size() * sizeof(int)) == cudaSuccess &&
+         cudaMalloc((void**)&b->d_item_blk_r[r], ib.size() * sizeof(int)) == cudaSuccess &&
+         cudaMemcpy(b->d_item_mesh_r[r], im.data(), im.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->d_item_blk_r[r], ib.data(), ib.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
   if (!ok) {
     wadg_batch_destroy(b);
     return WADG_ENOMEM;
   }
+  b->rule = 0;
+  b->grid = std::min(b->max_grid_r[0], std::max(1, b->nitems_r[0]));
   *out = b;
   return WADG_OK;
 }
@@ -195,15 +203,15 @@ int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
 int wadg_batch_info(const wadg_batch* b, int64_t info[4]) {
   if (!b || !info) return WADG_EINVAL;
   info[0] = (int64_t)b->meshes.size();
-  info[1] = b->nitems;
+  info[1] = b->nitems();
   info[2] = b->grid;
-  info[3] = b->max_grid;
+  info[3] = b->max_grid_r[b->rule];
   return WADG_OK;
 }
 
 int wadg_batch_set_grid(wadg_batch* b, int grid) {
   if (!b || grid < 1) return WADG_EINVAL;
-  b->grid = std::min(grid, std::max(1, b->nitems));
+  b->grid = std::min(grid, std::max(1, b->nitems()));
   return WADG_OK;
 }
 
@@ -228,39 +236,44 @@ int wadg_batch_autotune(wadg_batch* b, void* const* Q, void* const* res, int* gr
   if (st != WADG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int nsm = b->meshes[0]->num_sms;
-  std::vector<int> cands;
-  for (int mult : {1, 2, 3, 4, 6, 8})
-    if (mult * nsm <= b->max_grid) cands.push_back(mult * nsm);
-  cands.push_back(std::min(b->nitems, 65535 * 16));
   cudaEvent_t e0, e1;
   BCUDA(b, cudaEventCreate(&e0));
   BCUDA(b, cudaEventCreate(&e1));
   const size_t nm = b->meshes.size();
   float best = 1e30f;
-  int best_g = b->grid;
-  for (int g : cands) {
-    g = std::max(1, std::min(g, b->nitems));
-    for (int rep = 0; rep < 2; ++rep)
-      launch_batch_stage(0, b->d_params + 10 * nm, b->d_item_mesh, b->d_item_blk, b->d_mesh_N, b->nitems, g, b->smem,
-                         s);
-    cudaEventRecord(e0, s);
-    for (int rep = 0; rep < 5; ++rep)
-      launch_batch_stage(0, b->d_params + 10 * nm, b->d_item_mesh, b->d_item_blk, b->d_mesh_N, b->nitems, g, b->smem,
-                         s);
-    cudaEventRecord(e1, s);
-    cudaError_t e = cudaEventSynchronize(e1);
-    if (e != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return bfail(b, WADG_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      best_g = g;
+  int best_g = b->grid, best_r = b->rule;
+  for (int r = 0; r < 2; ++r) {
+    std::vector<int> cands;
+    for (int mult : {1, 2, 3, 4, 6, 8})
+      if (mult * nsm <= b->max_grid_r[r]) cands.push_back(mult * nsm);
+    cands.push_back(std::min(b->nitems_r[r], 1 << 20));
+    for (int g : cands) {
+      g = std::max(1, std::min(g, b->nitems_r[r]));
+      auto run = [&]() {
+        return launch_batch_stage(0, r, b->d_params + 10 * nm, b->d_item_mesh_r[r], b->d_item_blk_r[r], b->d_mesh_N,
+                                  b->nitems_r[r], g, b->smem_r[r], s);
+      };
+      run();
+      run();
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 5; ++rep) run();
+      cudaEventRecord(e1, s);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return bfail(b, WADG_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_g = g;
+        best_r = r;
+      }
     }
   }
+  b->rule = best_r;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->grid = best_g;

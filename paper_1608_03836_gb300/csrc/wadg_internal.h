@@ -94,11 +94,12 @@ cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int grid, c
 bool pack_tc_ops(int N, const RefOps& o, std::vector<uint8_t>& out);
 
 // Batches of FP32 meshes (batch.cu).
-int batch_cols_per_block(int N);
-size_t batch_smem_bytes(int N);
-int batch_max_blocks_per_sm(size_t smem);
-cudaError_t launch_batch_stage(int mode, const StageParams<float>* params, const int* item_mesh, const int* item_blk,
-                               const int* mesh_N, int nitems, int grid, size_t smem, cudaStream_t st);
+int batch_cols_per_block(int N, int rule);
+size_t batch_smem_bytes(int N, int rule);
+int batch_max_blocks_per_sm(int rule, size_t smem);
+cudaError_t launch_batch_stage(int mode, int rule, const StageParams<float>* params, const int* item_mesh,
+                               const int* item_blk, const int* mesh_N, int nitems, int grid, size_t smem,
+                               cudaStream_t st);
 
 // Launchers, one per (precision, degree); modes as in StageMode.
 template <typename T>
