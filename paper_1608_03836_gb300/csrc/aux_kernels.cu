@@ -123,6 +123,39 @@ __global__ void geo_pack_kernel(int64_t K, int Nq, int Nfq, const double* __rest
   }
 }
 
+// Column-interleaved FP32 copies for the tensor-core stage, where one thread
+// owns one element and a warp owns 32 consecutive elements:
+//   vgeo_il[((k/128) * 11 + c) * Nq + q][k % 128],  fgeo_il[((k/128) * 3 + d) * 4 Nfq + qf][k % 128].
+__global__ void geo_pack_il_kernel(int64_t K, int Nq, int Nfq, const double* __restrict__ J, const double* __restrict__ G,
+                                   const double* __restrict__ c2, const double* __restrict__ nJ, float* __restrict__ vgeo,
+                                   float* __restrict__ fgeo) {
+  const int64_t nv = K * 11 * Nq, nf = K * 12 * Nfq;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nv + nf; it += (int64_t)gridDim.x * blockDim.x) {
+    if (it < nv) {
+      const int64_t k = it % K;
+      const int64_t r = it / K;  // c * Nq + q
+      const int c = (int)(r / Nq), q = (int)(r % Nq);
+      const double Jq = J[k * Nq + q];
+      double v;
+      if (c < 9) v = G[(k * 9 + c) * Nq + q];
+      else if (c == 9) v = (c2 ? c2[k * Nq + q] : 1.0) / Jq;
+      else v = 1.0 / Jq;
+      vgeo[(((k >> 7) * 11 * Nq) + r) * 128 + (k & 127)] = (float)v;
+    } else {
+      const int64_t j = it - nv;
+      const int64_t k = j % K;
+      const int64_t r = j / K;  // d * 4 Nfq + qf
+      fgeo[(((k >> 7) * 12 * Nfq) + r) * 128 + (k & 127)] = (float)nJ[k * 12 * Nfq + r];
+    }
+  }
+}
+
+cudaError_t launch_geo_pack_il(int64_t K, int Nq, int Nfq, const double* J, const double* G, const double* c2,
+                               const double* nJ, float* vgeo_il, float* fgeo_il, cudaStream_t st) {
+  geo_pack_il_kernel<<<2048, 256, 0, st>>>(K, Nq, Nfq, J, G, c2, nJ, vgeo_il, fgeo_il);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Pseudo-projection P_N u = Pi_N(J^{-1} Pi_N(u J)) (Sec. 3, Theorem), with
 // Pi_N g = P_q g_q.  One block per column, FP64 arithmetic.

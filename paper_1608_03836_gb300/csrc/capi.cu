@@ -313,6 +313,8 @@ void wadg_mesh_destroy(wadg_mesh* m) {
   dfree(m->d_Qtmp);
   dfree(m->d_red);
   dfree(m->d_tcops);
+  dfree(m->d_vgeo_il);
+  dfree(m->d_fgeo_il);
   dfree(m->d_err);
   dfree(m->d_src_elem);
   dfree(m->d_src_vec);
@@ -564,11 +566,17 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
       int st = upload_ops<float>(m, m->ops32);
       if (st != WADG_OK) return st;
     }
-    if (precision == WADG_FP32_3XBF16 && !m->d_tcops) {
-      std::vector<uint8_t> packed;
-      if (!pack_tc_ops(m->N, m->ref, packed)) return fail(m, WADG_EUNSUPPORTED, "tensor-core tables");
-      WADG_CUDA(m, cudaMalloc((void**)&m->d_tcops, packed.size()));
-      WADG_CUDA(m, cudaMemcpy(m->d_tcops, packed.data(), packed.size(), cudaMemcpyHostToDevice));
+    if (precision == WADG_FP32_3XBF16) {
+      if (!m->d_tcops) {
+        std::vector<uint8_t> packed;
+        if (!pack_tc_ops(m->N, m->ref, packed)) return fail(m, WADG_EUNSUPPORTED, "tensor-core tables");
+        WADG_CUDA(m, cudaMalloc((void**)&m->d_tcops, packed.size()));
+        WADG_CUDA(m, cudaMemcpy(m->d_tcops, packed.data(), packed.size(), cudaMemcpyHostToDevice));
+      }
+      const int64_t Kt = (K + 127) / 128;
+      if (!m->d_vgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_vgeo_il, (size_t)Kt * 128 * 11 * Nq * sizeof(float)));
+      if (!m->d_fgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_fgeo_il, (size_t)Kt * 128 * 12 * Nfq * sizeof(float)));
+      WADG_CUDA(m, launch_geo_pack_il(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, m->d_nJ, m->d_vgeo_il, m->d_fgeo_il, 0));
     }
   }
   if (!m->d_err) {
@@ -636,6 +644,8 @@ cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p,
     P.s = p;
     P.ops = m->d_tcops;
     P.err = m->d_err;
+    P.vgeo_il = m->d_vgeo_il;
+    P.fgeo_il = m->d_fgeo_il;
     return launch_stage_tc(m->N, P, mode, m->num_sms, st);
   }
   return launch_stage<float>(m->N, p, mode, st);

@@ -11,9 +11,13 @@
 //     U^a = sum_i G_ai u_i and -(J grad p)_i (epilogue, one thread per column),
 //     b_p += sum_a (V_q^a)^T diag(w) U^a, b_ui -= V_q^T diag(w) (J grad p)_i
 //     (MMA, accumulated in TMEM over the chunks);
-//   surface (Sec. 6.4): on CUDA cores, 16 columns at a time, exactly as the
-//     CUDA-core stage kernel (gather in the owner's node order, V_tri, flux,
-//     V_tri^T diag(w_f), scatter), into a shared-memory accumulator;
+//   surface (Sec. 6.4), face by face: the face-node combinations [p], {u},
+//     [u] are gathered in the owner's node order (CUDA cores), interpolated
+//     to the face points by V_tri (MMA), turned into the strong-weak flux with
+//     n J^f (epilogue), lifted by V_tri^T diag(w_f) (MMA) and added to a
+//     shared-memory accumulator at the volume nodes (epilogue);
+//   geometric factors are read from column-interleaved copies, so that the 32
+//   lanes of a warp (32 consecutive elements) read 128 contiguous bytes;
 //   update (Sec. 6.2, Eq. (matfree); Sec. 7): b is split into an A operand;
 //     per chunk, (V_q M^^{-1}) b (MMA), times W = c^2/J or 1/J (epilogue),
 //     P_q (...) accumulated in TMEM (MMA);
@@ -45,21 +49,33 @@ struct TcDims {
   static constexpr int SZ_OPV = 2 * B_V + 2 * 3 * B_V + 2 * 3 * B_P + 2 * B_P;
   static constexpr int SZ_OPU = 2 * B_V + 2 * B_P;
   static constexpr int SZ_OP = SZ_OPV > SZ_OPU ? SZ_OPV : SZ_OPU;
-  static constexpr int FE = 16, FLD = 20;         // face sub-tile columns and row stride
-  static constexpr int SZ_FACE = (7 * 4 * NFP + 7 * 4 * NFQ) * FLD * 4;
-  static constexpr int SZ_BF = 4 * NP * TILE * 4;
+  static constexpr int SZ_BF = 4 * NP * TILE * 4;  // surface terms, FP32 [4][NP][128]
+  // surface products on the tensor cores: face nodes padded to NFP16 (K of the
+  // interpolation, N of the lift), face points to NFQ16 (N, then K)
+  static constexpr int NFP16 = (NFP + 15) / 16 * 16, NFQ16 = (NFQ + 15) / 16 * 16;
+  static constexpr int A_FN = TILE * NFP16 * 2;    // one part of a [128 x NFP16] combination tile
+  static constexpr int A_FQ = TILE * NFQ16 * 2;    // one part of a [128 x NFQ16] flux tile
+  static constexpr int SZ_FACE = (7 * 2 * A_FN > 4 * 2 * A_FQ ? 7 * 2 * A_FN : 4 * 2 * A_FQ);
+  static constexpr int B_TRI = NFQ16 * NFP16 * 2;  // one part of V_tri [NFQ16 x NFP16] or its lift
   static constexpr int OFF_AX = SZ_AQ;
   static constexpr int OFF_OP = SZ_AQ + SZ_AX;
-  static constexpr int OFF_BF = ((SZ_AQ > SZ_FACE ? SZ_AQ : SZ_FACE) + 127) / 128 * 128;
+  static constexpr int OFF_BF = ((SZ_FACE > SZ_AQ ? SZ_FACE : SZ_AQ) + 127) / 128 * 128;
   static constexpr int END1 = OFF_OP + SZ_OP, END2 = OFF_BF + SZ_BF;
   static constexpr int MAIN = END1 > END2 ? END1 : END2;
-  static constexpr int SMEM = MAIN + 128;         // + mbarrier and TMEM slot
+  static constexpr int OFF_FT = MAIN + 128;       // face B operands: V_tri (hi, lo), lift (hi, lo)
+  static constexpr int SMEM = OFF_FT + 4 * B_TRI;
+  static constexpr int SZ_FOPS = 4 * B_TRI;       // packed after the volume and update chunks
   // TMEM columns
   static constexpr int TV = 0;                    // chunk outputs: u1 u2 u3 (16 each), dp (48)
   static constexpr int TB = 128;                  // b accumulators, 4 x KP
   static constexpr int TU = 0;                    // update chunk: 4 x 16
   static constexpr int TR = 320;                  // r accumulators, 4 x KP
   static_assert(TB + 4 * KP <= 512 && TR + 4 * KP <= 512 && TV + 96 <= TB, "TMEM plan");
+  // TMEM for the surface products: combinations 0-3 in [0, 4 NFQ16), 4-6 at
+  // [TR, TR + 3 NFQ16), lifted fluxes after them
+  static constexpr int TI_LO = 0, TI_HI = TR, TL = TR + 3 * NFQ16;
+  static_assert(4 * NFQ16 <= TB && TL + 4 * NFP16 <= 512, "TMEM plan (surface)");
+
 };
 
 namespace {
@@ -99,7 +115,7 @@ template <int N, int MODE>
 __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P) {
   using T = TcDims<N>;
   constexpr int NP = T::NP, NQ = T::NQ, NFP = T::NFP, NFQ = T::NFQ, KP = T::KP, QC = T::QC;
-  constexpr int FE = T::FE, FLD = T::FLD, TILE = T::TILE;
+  constexpr int TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16;
   const StageParams<float>& p = P.s;
   const DevOps<float>& ops = p.ops;
 
@@ -108,8 +124,8 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
   uint8_t* sAX = smem + T::OFF_AX;     // A operand: chunk arrays
   uint8_t* sOP = smem + T::OFF_OP;     // B operand staging
   float* sBF = reinterpret_cast<float*>(smem + T::OFF_BF);  // [4][NP][128] surface terms
-  float* sFN = reinterpret_cast<float*>(smem);              // face sub-tile arrays
-  float* sFQ = sFN + 7 * 4 * NFP * FLD;
+  uint8_t* sFA = smem;                                       // per face: A operands (combinations, then fluxes)
+  uint8_t* sFT = smem + T::OFF_FT;                           // face B operands
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + T::MAIN);
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + T::MAIN + 8);
   int* sflag = reinterpret_cast<int*>(smem + T::MAIN + 16);
@@ -127,6 +143,7 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
     *sflag = 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), 512);
+  stage_copy(sFT, P.ops + (size_t)T::NCH * (T::SZ_OPV + T::SZ_OPU), T::SZ_FOPS);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -145,6 +162,7 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
   };
 
   const uint32_t aq = tc::smem_addr(sAQ), ax = tc::smem_addr(sAX), op = tc::smem_addr(sOP);
+  const uint32_t fa = tc::smem_addr(sFA), ft = tc::smem_addr(sFT);
   const uint32_t sbo_KP = (KP / 8) * 128, sbo_16 = 2 * 128;
 
   for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
@@ -154,12 +172,23 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
     cm = valid ? cm : ncols - 1;
     const int64_t km = cm / S;
 
-    // ---- fields -> split A operand (each half loads two fields of its column) ----
-    for (int f = 2 * half; f < 2 * half + 2; ++f) {
-      uint8_t* hi = sAQ + (2 * f) * T::A_FIELD;
-      uint8_t* lo = hi + T::A_FIELD;
-      const float* q = p.Qin + f * fs + cm * NP;
-      for (int n = 0; n < KP; ++n) put_split(hi, lo, tc::kmajor_offset(mrow, n, KP), n < NP ? __ldg(q + n) : 0.f);
+    // ---- fields -> split A operand: coalesced FP32 tile in the (free) A_X/B
+    // staging area, then each half splits two fields of its column ----
+    {
+      float* stg = reinterpret_cast<float*>(sAX);  // [4][TILE * NP]
+      const int64_t nval = (ncols - col0 < TILE ? ncols - col0 : TILE) * NP;
+      for (int f = 0; f < 4; ++f) {
+        const float* src = p.Qin + f * fs + col0 * NP;
+        for (int i = tid; i < TILE * NP; i += 256) stg[f * TILE * NP + i] = i < nval ? __ldg(src + i) : 0.f;
+      }
+      __syncthreads();
+      for (int f = 2 * half; f < 2 * half + 2; ++f) {
+        uint8_t* hi = sAQ + (2 * f) * T::A_FIELD;
+        uint8_t* lo = hi + T::A_FIELD;
+        const float* q = stg + f * TILE * NP + mrow * NP;
+        for (int n = 0; n < KP; ++n) put_split(hi, lo, tc::kmajor_offset(mrow, n, KP), n < NP ? q[n] : 0.f);
+      }
+      __syncthreads();  // the staging area is reused by the operator chunks
     }
 
     // ---- volume terms, chunk by chunk ----
@@ -180,29 +209,38 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
              tc::idesc_bf16(128, 48), false);
         tc::commit(mb);
       }
+      // geometric factors of this thread's 8 quadrature points, loaded while the MMA runs
+      float G[9][8];
+      {
+        const float* gk = P.vgeo_il + (km >> 7) * 11 * NQ * 128 + (km & 127);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int q = ch * QC + 8 * half + j;
+#pragma unroll
+          for (int c = 0; c < 9; ++c) G[c][j] = q < NQ ? __ldg(gk + (size_t)(c * NQ + q) * 128) : 0.f;
+        }
+      }
       wait_mma();
       if (failed) break;
       // epilogue: U^a and -(J grad p)_i at this thread's 8 quadrature points
       {
         float u[3][8], d[3][8];
-        for (int i = 0; i < 3; ++i) tc::tmem_ld8(lane_base + T::TV + 16 * i + 8 * half, u[i]);
-        for (int a = 0; a < 3; ++a) tc::tmem_ld8(lane_base + T::TV + 48 + 16 * a + 8 * half, d[a]);
-        const float* gk = p.vgeo + km * 11 * NQ;
+        tc::tmem_ld24(lane_base + T::TV + 8 * half, lane_base + T::TV + 16 + 8 * half, lane_base + T::TV + 32 + 8 * half,
+                      u[0], u[1], u[2]);
+        tc::tmem_ld24(lane_base + T::TV + 48 + 8 * half, lane_base + T::TV + 64 + 8 * half,
+                      lane_base + T::TV + 80 + 8 * half, d[0], d[1], d[2]);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const int ql = 8 * half + j, q = ch * QC + ql;
-          float G[9];
-#pragma unroll
-          for (int c = 0; c < 9; ++c) G[c] = q < NQ ? __ldg(gk + c * NQ + q) : 0.f;
+          const int ql = 8 * half + j;
           const uint32_t off = tc::kmajor_offset(mrow, ql, QC);
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
-            const float U = G[a * 3] * u[0][j] + G[a * 3 + 1] * u[1][j] + G[a * 3 + 2] * u[2][j];
+            const float U = G[a * 3][j] * u[0][j] + G[a * 3 + 1][j] * u[1][j] + G[a * 3 + 2][j] * u[2][j];
             put_split(sAX + (2 * a) * T::A_CH, sAX + (2 * a + 1) * T::A_CH, off, U);
           }
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            const float g = -(G[i] * d[0][j] + G[3 + i] * d[1][j] + G[6 + i] * d[2][j]);
+            const float g = -(G[i][j] * d[0][j] + G[3 + i][j] * d[1][j] + G[6 + i][j] * d[2][j]);
             put_split(sAX + (2 * (3 + i)) * T::A_CH, sAX + (2 * (3 + i) + 1) * T::A_CH, off, g);
           }
         }
@@ -225,107 +263,150 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
     }
     if (failed) break;
 
-    // ---- surface terms on CUDA cores, FE columns at a time, into sBF ----
-    for (int sub = 0; sub < TILE / FE; ++sub) {
-      const int64_t s0 = col0 + sub * FE;
-      // face nodes: [p], {u}, [u] in the owner's node order
-      for (int it = tid; it < 4 * NFP * FE; it += 256) {
-        const int j = it % NFP, f = (it / NFP) % 4, e = it / (4 * NFP);
-        int64_t c = s0 + e;
-        c = c < ncols ? c : ncols - 1;
-        const int64_t k = c / S;
-        const int sh = (int)(c - k * S);
-        const int code = p.fcode[k * 4 + f];
+    // ---- surface terms (Sec. 6.4), face by face: gather on CUDA cores, V_tri
+    // and the lift V_tri^T diag(w_f) on the tensor cores, flux in between ----
+    for (int i = tid; i < 4 * NP * TILE; i += 256) sBF[i] = 0.f;
+    for (int f = 0; f < 4 && !failed; ++f) {
+      const int col = mrow;
+      int pio_f;
+      // (i) [p], {u}, [u] at the face nodes, owner's node order -> split A operands
+      {
+        constexpr int JH = NFP16 / 2;
+        const int code = p.fcode[km * 4 + f];
         const int pio = code % 6, pin = (code / 6) % 6, fn = code / 36;
-        const int64_t bo = c * NP + ops.gidx[(f * 6 + pio) * NFP + j];
-        const float pm = __ldg(p.Qin + bo), u1m = __ldg(p.Qin + fs + bo), u2m = __ldg(p.Qin + 2 * fs + bo),
-                    u3m = __ldg(p.Qin + 3 * fs + bo);
-        const int64_t kn = p.EToE[k * 4 + f];
-        float pp, u1p, u2p, u3p;
-        if (kn >= 0) {
-          const int64_t b = (kn * S + sh) * NP + ops.gidx[(fn * 6 + pin) * NFP + j];
-          pp = __ldg(p.Qin + b);
-          u1p = __ldg(p.Qin + fs + b);
-          u2p = __ldg(p.Qin + 2 * fs + b);
-          u3p = __ldg(p.Qin + 3 * fs + b);
-        } else {
-          pp = -pm;
-          u1p = u1m;
-          u2p = u2m;
-          u3p = u3m;
+        pio_f = pio;
+        const int sh = (int)(cm - km * S);
+        const int64_t kn = p.EToE[km * 4 + f];
+        const int16_t* go = ops.gidx + (f * 6 + pio) * NFP;
+        const int16_t* gn = ops.gidx + (fn * 6 + pin) * NFP;
+        const int64_t nb = kn >= 0 ? (kn * S + sh) * NP : 0;
+#pragma unroll
+        for (int jj = 0; jj < JH; ++jj) {
+          const int j = half * JH + jj;
+          float cv[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          if (j < NFP) {
+            const int64_t bo = cm * NP + go[j];
+            const float pm = __ldg(p.Qin + bo), u1m = __ldg(p.Qin + fs + bo), u2m = __ldg(p.Qin + 2 * fs + bo),
+                        u3m = __ldg(p.Qin + 3 * fs + bo);
+            float pp, u1p, u2p, u3p;
+            if (kn >= 0) {
+              const int64_t b = nb + gn[j];
+              pp = __ldg(p.Qin + b);
+              u1p = __ldg(p.Qin + fs + b);
+              u2p = __ldg(p.Qin + 2 * fs + b);
+              u3p = __ldg(p.Qin + 3 * fs + b);
+            } else {  // Dirichlet ghost state (Sec. 4.1)
+              pp = -pm;
+              u1p = u1m;
+              u2p = u2m;
+              u3p = u3m;
+            }
+            cv[0] = pp - pm;
+            cv[1] = 0.5f * (u1p + u1m);
+            cv[2] = 0.5f * (u2p + u2m);
+            cv[3] = 0.5f * (u3p + u3m);
+            cv[4] = u1p - u1m;
+            cv[5] = u2p - u2m;
+            cv[6] = u3p - u3m;
+          }
+          const uint32_t off = tc::kmajor_offset(col, j, NFP16);
+#pragma unroll
+          for (int c = 0; c < 7; ++c) put_split(sFA + (2 * c) * T::A_FN, sFA + (2 * c + 1) * T::A_FN, off, cv[c]);
         }
-        const int row = f * NFP + j;
-        sFN[(0 * 4 * NFP + row) * FLD + e] = pp - pm;
-        sFN[(1 * 4 * NFP + row) * FLD + e] = 0.5f * (u1p + u1m);
-        sFN[(2 * 4 * NFP + row) * FLD + e] = 0.5f * (u2p + u2m);
-        sFN[(3 * 4 * NFP + row) * FLD + e] = 0.5f * (u3p + u3m);
-        sFN[(4 * 4 * NFP + row) * FLD + e] = u1p - u1m;
-        sFN[(5 * 4 * NFP + row) * FLD + e] = u2p - u2m;
-        sFN[(6 * 4 * NFP + row) * FLD + e] = u3p - u3m;
       }
+      tc::fence_async_smem();
+      tc::fence_before();
       __syncthreads();
+      tc::fence_after();
+      if (tid == 0) {
+        for (int c = 0; c < 7; ++c) {
+          const uint32_t d = tmem + (c < 4 ? T::TI_LO + c * NFQ16 : T::TI_HI + (c - 4) * NFQ16);
+          mma3(d, fa + (2 * c) * T::A_FN, fa + (2 * c + 1) * T::A_FN, (NFP16 / 8) * 128, ft, ft + T::B_TRI,
+               (NFP16 / 8) * 128, NFP16 / 16, tc::idesc_bf16(128, NFQ16), false);
+        }
+        tc::commit(mb);
+      }
+      // normals x surface Jacobian at this thread's face points, loaded while the MMA runs
+      constexpr int QH = NFQ16 / 2;
+      float nv[3][QH];
       {
-        constexpr int RG = Dims<N>::NFQP / 4, NG = FE / 4;
-        for (int it = tid; it < 28 * RG * NG; it += 256) {
-          const int g = it % NG, m0 = ((it / NG) % RG) * 4, job = it / (RG * NG);
-          float acc[4][4];
-          tile_dot<float, FLD, 4, Dims<N>::NFQP, NFP>(ops.VtriT, sFN + job * NFP * FLD + g * 4, m0, acc);
+        const float* nfg = P.fgeo_il + ((km >> 7) * 12 * NFQ + f * NFQ) * 128 + (km & 127);
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
-            if (m0 + r < NFQ) sts_cols(sFQ + (job * NFQ + m0 + r) * FLD + g * 4, acc[r]);
+        for (int qq = 0; qq < QH; ++qq) {
+          const int q = half * QH + qq;
+#pragma unroll
+          for (int dd = 0; dd < 3; ++dd) nv[dd][qq] = q < NFQ ? __ldg(nfg + (size_t)(dd * 4 * NFQ + q) * 128) : 0.f;
         }
       }
-      __syncthreads();
-      for (int it = tid; it < 4 * NFQ * FE; it += 256) {
-        const int qf = it % (4 * NFQ), e = it / (4 * NFQ);
-        int64_t c = s0 + e;
-        c = c < ncols ? c : ncols - 1;
-        const float* fg = p.fgeo + (c / S) * 3 * 4 * NFQ + qf;
-        const float nx = __ldg(fg), ny = __ldg(fg + 4 * NFQ), nz = __ldg(fg + 8 * NFQ);
-        const float Jf = sqrtf(nx * nx + ny * ny + nz * nz);
-        const float jp = sFQ[(0 * 4 * NFQ + qf) * FLD + e];
-        const float a1 = sFQ[(1 * 4 * NFQ + qf) * FLD + e], a2 = sFQ[(2 * 4 * NFQ + qf) * FLD + e],
-                    a3 = sFQ[(3 * 4 * NFQ + qf) * FLD + e];
-        const float j1 = sFQ[(4 * 4 * NFQ + qf) * FLD + e], j2 = sFQ[(5 * 4 * NFQ + qf) * FLD + e],
-                    j3 = sFQ[(6 * 4 * NFQ + qf) * FLD + e];
-        const float aun = a1 * nx + a2 * ny + a3 * nz;
-        const float jun = (j1 * nx + j2 * ny + j3 * nz) / Jf;
-        const float Fp = -aun + 0.5f * p.tau_p * jp * Jf;
-        const float sc = -0.5f * (jp - p.tau_u * jun);
-        sFQ[(0 * 4 * NFQ + qf) * FLD + e] = Fp;
-        sFQ[(1 * 4 * NFQ + qf) * FLD + e] = sc * nx;
-        sFQ[(2 * 4 * NFQ + qf) * FLD + e] = sc * ny;
-        sFQ[(3 * 4 * NFQ + qf) * FLD + e] = sc * nz;
-      }
-      __syncthreads();
+      wait_mma();
+      if (failed) break;
+      // (ii) strong-weak flux (Sec. 4.1) at this thread's face points -> split A operands
       {
-        constexpr int RG = Dims<N>::NFPP / 2, NG = FE / 4;
-        for (int it = tid; it < 16 * RG * NG; it += 256) {
-          const int g = it % NG, m0 = ((it / NG) % RG) * 2, job = it / (RG * NG);
-          float acc[2][4];
-          tile_dot<float, FLD, 2, Dims<N>::NFPP, NFQ>(ops.VtriTwT, sFQ + job * NFQ * FLD + g * 4, m0, acc);
+        float v[7][QH];
 #pragma unroll
-          for (int r = 0; r < 2; ++r)
-            if (m0 + r < NFP) sts_cols(sFN + (job * NFP + m0 + r) * FLD + g * 4, acc[r]);
+        for (int c = 0; c < 7; ++c) {
+          const uint32_t base = lane_base + (c < 4 ? T::TI_LO + c * NFQ16 : T::TI_HI + (c - 4) * NFQ16) + half * QH;
+#pragma unroll
+          for (int q8 = 0; q8 < QH; q8 += 8) {
+            float x[8];
+            tc::tmem_ld8(base + q8, x);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[c][q8 + j] = x[j];
+          }
+        }
+#pragma unroll
+        for (int qq = 0; qq < QH; ++qq) {
+          const int q = half * QH + qq;
+          const float nx = nv[0][qq], ny = nv[1][qq], nz = nv[2][qq];
+          float F[4] = {0.f, 0.f, 0.f, 0.f};
+          if (q < NFQ) {
+            const float Jf = sqrtf(nx * nx + ny * ny + nz * nz);
+            const float aun = v[1][qq] * nx + v[2][qq] * ny + v[3][qq] * nz;
+            const float jun = (v[4][qq] * nx + v[5][qq] * ny + v[6][qq] * nz) / Jf;
+            F[0] = -aun + 0.5f * p.tau_p * v[0][qq] * Jf;
+            const float sc = -0.5f * (v[0][qq] - p.tau_u * jun);
+            F[1] = sc * nx;
+            F[2] = sc * ny;
+            F[3] = sc * nz;
+          }
+          const uint32_t off = tc::kmajor_offset(col, q, NFQ16);
+#pragma unroll
+          for (int fld = 0; fld < 4; ++fld)
+            put_split(sFA + (2 * fld) * T::A_FQ, sFA + (2 * fld + 1) * T::A_FQ, off, F[fld]);
         }
       }
+      tc::fence_async_smem();
+      tc::fence_before();
       __syncthreads();
-      for (int it = tid; it < 4 * NP * FE; it += 256) {
-        const int e = it % FE, n = (it / FE) % NP, fld = it / (FE * NP);
-        int64_t c = s0 + e;
-        c = c < ncols ? c : ncols - 1;
-        const int64_t k = c / S;
-        float acc = 0.f;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int pio = p.fcode[k * 4 + f] % 6;
-          const int jo = ops.ginv[(f * 6 + pio) * NP + n];
-          if (jo >= 0) acc += sFN[((fld * 4 + f) * NFP + jo) * FLD + e];
-        }
-        sBF[(fld * NP + n) * TILE + sub * FE + e] = acc;
+      tc::fence_after();
+      if (tid == 0) {
+        const uint32_t bl = ft + 2 * T::B_TRI;
+        for (int fld = 0; fld < 4; ++fld)
+          mma3(tmem + T::TL + fld * NFP16, fa + (2 * fld) * T::A_FQ, fa + (2 * fld + 1) * T::A_FQ, (NFQ16 / 8) * 128, bl,
+               bl + T::B_TRI, (NFQ16 / 8) * 128, NFQ16 / 16, tc::idesc_bf16(128, NFP16), false);
+        tc::commit(mb);
       }
+      wait_mma();
+      if (failed) break;
+      // (iii) add the lifted face terms to the volume nodes of this thread's two fields
+#pragma unroll
+      for (int fi = 0; fi < 2; ++fi) {
+        const int fld = 2 * half + fi;
+        const int16_t* go = ops.gidx + (f * 6 + pio_f) * NFP;
+#pragma unroll
+        for (int j8 = 0; j8 < NFP16; j8 += 8) {
+          float x[8];
+          tc::tmem_ld8(lane_base + T::TL + fld * NFP16 + j8, x);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (j8 + j < NFP) sBF[(fld * NP + go[j8 + j]) * TILE + col] += x[j];
+        }
+      }
+      tc::fence_before();
       __syncthreads();
+      tc::fence_after();
     }
+    if (failed) break;
 
     // ---- b = volume (TMEM) + surface (smem) + source -> split A operand ----
     {
@@ -366,19 +447,30 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
                op + T::B_V, sbo_KP, KP / 16, tc::idesc_bf16(128, 16), false);
         tc::commit(mb);
       }
+      // weights of this thread's two fields at the 16 points of the chunk, loaded while the MMA runs
+      float wt[2][16];
+#pragma unroll
+      for (int fi = 0; fi < 2; ++fi) {
+        const int f = 2 * half + fi;
+        const float* w = P.vgeo_il + ((km >> 7) * 11 + (f == 0 ? 9 : 10)) * NQ * 128 + (km & 127);
+#pragma unroll
+        for (int ql = 0; ql < 16; ++ql) {
+          const int q = ch * QC + ql;
+          wt[fi][ql] = q < NQ ? __ldg(w + (size_t)q * 128) : 0.f;
+        }
+      }
       wait_mma();
       if (failed) break;
-      for (int f = 2 * half; f < 2 * half + 2; ++f) {
-        const float* w = p.vgeo + (km * 11 + (f == 0 ? 9 : 10)) * NQ;
-        for (int h8 = 0; h8 < 2; ++h8) {
-          float v[8];
-          tc::tmem_ld8(lane_base + T::TU + 16 * f + 8 * h8, v);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int ql = 8 * h8 + j, q = ch * QC + ql;
-            const float x = q < NQ ? v[j] * __ldg(w + q) : 0.f;
-            put_split(sAX + (2 * f) * T::A_CH, sAX + (2 * f + 1) * T::A_CH, tc::kmajor_offset(mrow, ql, QC), x);
-          }
+      for (int fi = 0; fi < 2; ++fi) {
+        const int f = 2 * half + fi;
+        float v0[8], v1[8], vdummy[8];
+        tc::tmem_ld24(lane_base + T::TU + 16 * f, lane_base + T::TU + 16 * f + 8, lane_base + T::TU + 16 * f, v0, v1,
+                      vdummy);
+#pragma unroll
+        for (int ql = 0; ql < 16; ++ql) {
+          const float x = (ql < 8 ? v0[ql] : v1[ql - 8]) * wt[fi][ql];
+          put_split(sAX + (2 * f) * T::A_CH, sAX + (2 * f + 1) * T::A_CH, tc::kmajor_offset(mrow, ql, QC), x);
         }
       }
       tc::fence_async_smem();
@@ -460,10 +552,10 @@ cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int grid, c
 
 size_t tc_ops_bytes(int N) {
   switch (N) {
-    case 1: return (size_t)TcDims<1>::NCH * (TcDims<1>::SZ_OPV + TcDims<1>::SZ_OPU);
-    case 2: return (size_t)TcDims<2>::NCH * (TcDims<2>::SZ_OPV + TcDims<2>::SZ_OPU);
-    case 3: return (size_t)TcDims<3>::NCH * (TcDims<3>::SZ_OPV + TcDims<3>::SZ_OPU);
-    case 4: return (size_t)TcDims<4>::NCH * (TcDims<4>::SZ_OPV + TcDims<4>::SZ_OPU);
+    case 1: return (size_t)TcDims<1>::NCH * (TcDims<1>::SZ_OPV + TcDims<1>::SZ_OPU) + TcDims<1>::SZ_FOPS;
+    case 2: return (size_t)TcDims<2>::NCH * (TcDims<2>::SZ_OPV + TcDims<2>::SZ_OPU) + TcDims<2>::SZ_FOPS;
+    case 3: return (size_t)TcDims<3>::NCH * (TcDims<3>::SZ_OPV + TcDims<3>::SZ_OPU) + TcDims<3>::SZ_FOPS;
+    case 4: return (size_t)TcDims<4>::NCH * (TcDims<4>::SZ_OPV + TcDims<4>::SZ_OPU) + TcDims<4>::SZ_FOPS;
     default: return 0;
   }
 }
@@ -512,7 +604,7 @@ template <int N>
 void pack_n(const RefOps& o, std::vector<uint8_t>& out) {
   using T = TcDims<N>;
   const int Np = o.Np, Nq = o.Nq, KP = T::KP, QC = T::QC;
-  out.assign((size_t)T::NCH * (T::SZ_OPV + T::SZ_OPU), 0);
+  out.assign((size_t)T::NCH * (T::SZ_OPV + T::SZ_OPU) + T::SZ_FOPS, 0);
   for (int ch = 0; ch < T::NCH; ++ch) {
     uint8_t* v = out.data() + (size_t)ch * T::SZ_OPV;
     auto qn = [&](int r) { return ch * QC + r; };
@@ -543,6 +635,16 @@ void pack_n(const RefOps& o, std::vector<uint8_t>& out) {
       return (q < Nq && n < Np) ? o.Pq[n * Nq + q] : 0.0;
     });
   }
+  // face operators: V_tri as [NFQ16 rows (q) x NFP16 (j)], the lift
+  // V_tri^T diag(w_f) as [NFP16 rows (j) x NFQ16 (q)]
+  const int Nfp = o.Nfp, Nfq = o.Nfq;
+  uint8_t* fo = out.data() + (size_t)T::NCH * (T::SZ_OPV + T::SZ_OPU);
+  put_tile(fo, T::B_TRI, T::NFQ16, T::NFP16, [&](int q, int j) {
+    return (q < Nfq && j < Nfp) ? o.Vtri[q * Nfp + j] : 0.0;
+  });
+  put_tile(fo + 2 * T::B_TRI, T::B_TRI, T::NFP16, T::NFQ16, [&](int j, int q) {
+    return (q < Nfq && j < Nfp) ? o.VtriTw[j * Nfq + q] : 0.0;
+  });
 }
 
 }  // namespace

@@ -89,6 +89,8 @@ struct TcStageParams {
   StageParams<float> s;
   const uint8_t* ops = nullptr;  // packed split operators: NCH volume chunks, then NCH update chunks
   int* err = nullptr;            // set to 1 when a bounded wait expires
+  const float* vgeo_il = nullptr;  // column-interleaved geometric factors (see aux_kernels.cu)
+  const float* fgeo_il = nullptr;
 };
 cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int grid, cudaStream_t stream);
 bool pack_tc_ops(int N, const RefOps& o, std::vector<uint8_t>& out);
@@ -141,6 +143,8 @@ struct wadg_mesh {
   wadg::DevOps<double> ops64;
   wadg::DevOps<float> ops32;
   uint8_t* d_tcops = nullptr;  // split operators of the tensor-core stage
+  float* d_vgeo_il = nullptr;  // column-interleaved geometry for the tensor-core stage
+  float* d_fgeo_il = nullptr;
   int* d_err = nullptr;        // device error flag (bounded waits)
   int num_sms = 0;
   void* d_Qtmp = nullptr;      // ping-pong buffer for LSRK stages
