@@ -328,6 +328,23 @@ def cpu_baseline(budget_s: float = 20.0):
             "sample": o.describe(stages, t)}
 
 
+def max_over_ranks(ms: float, ws: int) -> float:
+    """Largest of the ranks' timings (every rank gets it); ws = 1 returns ms."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(dof_per_rank: int, stages: int, ms: float, ws: int) -> float:
+    """Whole-job DOF*stage/s: all ranks' work over the slowest rank's time."""
+    return ws * dof_per_rank * stages / (ms * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -395,13 +412,9 @@ def main():
     with ClockSampler(local) as clk:
         total_ms, stage_ms = time_steps(W, m, Q, args.steps, args.warmup)
     barrier()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws)
     ms_per_step = total_ms / args.steps
-    value = ws * dof * 5 / (ms_per_step * 1e-3)
+    value = job_value(dof, 5, ms_per_step, ws)
     e2e_ms, nbytes = e2e_steps(W, m, Q, max(2, args.steps // 2))
     e2e_value = ws * dof * 5 / (e2e_ms * 1e-3)
 

@@ -106,6 +106,13 @@ int wadg_set_operators(wadg_mesh* mesh, int precision, int shots, double tau_p, 
  * the last call (the flag is then cleared), WADG_OK otherwise. */
 int wadg_device_status(wadg_mesh* mesh, wadg_stream stream);
 
+/* Test hook for the failure path of the bounded device waits (no fault, trap
+ * or hang is involved): launches one block that waits, with the same bounded
+ * loop as the tensor-core kernels, max_iters times (1 .. 2^22) on an mbarrier
+ * that nothing arrives at.  The expired wait sets the device error flag, so
+ * the next wadg_device_status returns WADG_ETIMEOUT. */
+int wadg_selftest_bounded_wait(wadg_mesh* mesh, uint32_t max_iters, wadg_stream stream);
+
 /* Sizes: info[0..7] = N, K, Np, Nq, Nfp, Nfq, S, precision (S, precision are
  * -1 before wadg_set_operators). */
 int wadg_mesh_info(const wadg_mesh* mesh, int64_t info[8]);

@@ -16,6 +16,7 @@ from .api import (  # noqa: E402,F401
     WADG_FP64,
     WADG_FP32_3XBF16,
     wadg_device_status,
+    wadg_selftest_bounded_wait,
     BatchHandle,
     MeshHandle,
     wadg_batch_autotune,

@@ -103,6 +103,12 @@ def wadg_device_status(mesh: MeshHandle, stream=None):
     _check(load().wadg_device_status(mesh.handle, _stream(stream)), "wadg_device_status", mesh)
 
 
+def wadg_selftest_bounded_wait(mesh: MeshHandle, max_iters: int = 1000, stream=None):
+    """Launch the bounded-wait failure-path test (see include/wadg.h)."""
+    _check(load().wadg_selftest_bounded_wait(mesh.handle, int(max_iters), _stream(stream)),
+           "wadg_selftest_bounded_wait", mesh)
+
+
 def wadg_reference_rules(N: int):
     Nq, Nfq = (N + 1) ** 3, (N + 1) ** 2
     rst, w, rs, wf = np.zeros((Nq, 3)), np.zeros(Nq), np.zeros((Nfq, 2)), np.zeros(Nfq)

@@ -1080,3 +1080,12 @@ extern "C" int wadg_device_status(wadg_mesh* m, wadg_stream stream) {
   }
   return WADG_OK;
 }
+
+extern "C" int wadg_selftest_bounded_wait(wadg_mesh* m, uint32_t max_iters, wadg_stream stream) {
+  if (!m) return WADG_EINVAL;
+  if (!m->d_err) return fail(m, WADG_ESTATE, "wadg_set_operators has not been called");
+  if (max_iters < 1 || max_iters > (1u << 22)) return fail(m, WADG_EINVAL, "max_iters in [1, 2^22]");
+  DeviceGuard g(m->device);
+  cudaError_t e = launch_bounded_wait_selftest(m->d_err, max_iters, (cudaStream_t)stream);
+  return e == cudaSuccess ? WADG_OK : cuda_fail(m, e, "bounded-wait self test");
+}

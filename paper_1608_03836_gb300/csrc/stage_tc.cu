@@ -37,50 +37,55 @@ struct TcDims {
   using D = Dims<N>;
   static constexpr int NP = D::NP, NQ = D::NQ, NFP = D::NFP, NFQ = D::NFQ;
   static constexpr int KP = (NP + 15) / 16 * 16;  // node count padded to the MMA K / N granule
+  static constexpr int NPS = NP | 1;              // odd row stride of FP32 tiles in shared memory
   static constexpr int QC = 16;                   // quadrature points per chunk
   static constexpr int NCH = (NQ + QC - 1) / QC;
   static constexpr int TILE = 128;
-  static constexpr int A_FIELD = TILE * KP * 2;   // bytes of one bf16 part of one field tile
+  static constexpr int A_FIELD = TILE * KP * 2;   // bytes of one bf16 part of one [128 x KP] field tile
   static constexpr int SZ_AQ = 4 * 2 * A_FIELD;
-  static constexpr int A_CH = TILE * QC * 2;      // one part of a [128 x 16] array
+  static constexpr int A_CH = TILE * QC * 2;      // one part of a [128 x 16] chunk array
   static constexpr int SZ_AX = 6 * 2 * A_CH;
   static constexpr int B_V = QC * KP * 2;         // one part of a [16 x KP] operator chunk
   static constexpr int B_P = KP * QC * 2;         // one part of a [KP x 16] operator chunk
-  static constexpr int SZ_OPV = 2 * B_V + 2 * 3 * B_V + 2 * 3 * B_P + 2 * B_P;
-  static constexpr int SZ_OPU = 2 * B_V + 2 * B_P;
-  static constexpr int SZ_OP = SZ_OPV > SZ_OPU ? SZ_OPV : SZ_OPU;
-  static constexpr int SZ_BF = 4 * NP * TILE * 4;  // surface terms, FP32 [4][NP][128]
-  // surface products on the tensor cores: face nodes padded to NFP16 (K of the
-  // interpolation, N of the lift), face points to NFQ16 (N, then K)
+  // packed operators per chunk: volume A part (V_q, V_q^a), volume B part
+  // ((V_q^a)^T diag(w), V_q^T diag(w)), update A part (V_q M^^{-1}), update B part (P_q)
+  static constexpr int SZ_VA = 8 * B_V, SZ_VB = 8 * B_P, SZ_UA = 2 * B_V, SZ_UB = 2 * B_P;
+  static constexpr int SZ_OPV = SZ_VA + SZ_VB, SZ_OPU = SZ_UA + SZ_UB;
+  static constexpr int SZ_SLOT = SZ_VA > SZ_VB ? SZ_VA : SZ_VB;
   static constexpr int NFP16 = (NFP + 15) / 16 * 16, NFQ16 = (NFQ + 15) / 16 * 16;
-  static constexpr int A_FN = TILE * NFP16 * 2;    // one part of a [128 x NFP16] combination tile
-  static constexpr int A_FQ = TILE * NFQ16 * 2;    // one part of a [128 x NFQ16] flux tile
-  static constexpr int SZ_FACE = (7 * 2 * A_FN > 4 * 2 * A_FQ ? 7 * 2 * A_FN : 4 * 2 * A_FQ);
-  static constexpr int B_TRI = NFQ16 * NFP16 * 2;  // one part of V_tri [NFQ16 x NFP16] or its lift
-  static constexpr int OFF_AX = SZ_AQ;
-  static constexpr int OFF_OP = SZ_AQ + SZ_AX;
-  static constexpr int OFF_BF = ((SZ_FACE > SZ_AQ ? SZ_FACE : SZ_AQ) + 127) / 128 * 128;
-  static constexpr int END1 = OFF_OP + SZ_OP, END2 = OFF_BF + SZ_BF;
-  static constexpr int MAIN = END1 > END2 ? END1 : END2;
-  static constexpr int OFF_FT = MAIN + 128;       // face B operands: V_tri (hi, lo), lift (hi, lo)
-  static constexpr int SMEM = OFF_FT + 4 * B_TRI;
-  static constexpr int SZ_FOPS = 4 * B_TRI;       // packed after the volume and update chunks
+  static constexpr int A_FN = TILE * NFP16 * 2;    // one part of a [128 x NFP16] face-node tile
+  static constexpr int A_FQ = TILE * NFQ16 * 2;    // one part of a [128 x NFQ16] face-point tile
+  static constexpr int SZ_FA = (7 * 2 * A_FN > 4 * 2 * A_FQ ? 7 * 2 * A_FN : 4 * 2 * A_FQ);
+  static constexpr int SZ_LS = 4 * NFP16 * TILE * 4;  // lifted face values, [4][NFP16][128] FP32
+  static constexpr int SZ_T32 = 4 * TILE * NPS * 4;   // FP32 field tile [4][128][NPS]
+  static constexpr int R0A = SZ_AQ > SZ_FA + SZ_LS ? SZ_AQ : SZ_FA + SZ_LS;
+  static constexpr int SZ_R0 = ((R0A > SZ_T32 ? R0A : SZ_T32) + 127) / 128 * 128;
+  static constexpr int OFF_SLOT = SZ_R0;
+  static constexpr int OFF_AX = OFF_SLOT + 4 * SZ_SLOT;
+  static constexpr int OFF_QS = OFF_AX;  // FP32 input tile: from the load to the split (before the volume)
+  static constexpr int END_AX = OFF_AX + SZ_AX, END_QS = OFF_QS + SZ_T32;
+  static constexpr int OFF_FT = ((END_AX > END_QS ? END_AX : END_QS) + 127) / 128 * 128;
+  static constexpr int B_TRI = NFQ16 * NFP16 * 2;  // one part of V_tri [NFQ16 x NFP16] or of its lift
+  static constexpr int SZ_FOPS = 4 * B_TRI;
+  static constexpr int OFF_GI = OFF_FT + SZ_FOPS;
+  static constexpr int SZ_GI = (4 * 6 * NP * 2 + 15) / 16 * 16;
+  static constexpr int OFF_GX = OFF_GI + SZ_GI;
+  static constexpr int SZ_GX = (4 * 6 * NFP * 2 + 15) / 16 * 16;
+  static constexpr int OFF_BAR = OFF_GX + SZ_GX;
+  static constexpr int SMEM = OFF_BAR + 128;
   // TMEM columns
-  static constexpr int TV = 0;                    // chunk outputs: u1 u2 u3 (16 each), dp (48)
-  static constexpr int TB = 128;                  // b accumulators, 4 x KP
-  static constexpr int TU = 0;                    // update chunk: 4 x 16
-  static constexpr int TR = 320;                  // r accumulators, 4 x KP
-  static_assert(TB + 4 * KP <= 512 && TR + 4 * KP <= 512 && TV + 96 <= TB, "TMEM plan");
-  // TMEM for the surface products: combinations 0-3 in [0, 4 NFQ16), 4-6 at
-  // [TR, TR + 3 NFQ16), lifted fluxes after them
-  static constexpr int TI_LO = 0, TI_HI = TR, TL = TR + 3 * NFQ16;
-  static_assert(4 * NFQ16 <= TB && TL + 4 * NFP16 <= 512, "TMEM plan (surface)");
-
+  static constexpr int T1 = 96;                    // chunk outputs, two buffers at 0 and T1
+  static constexpr int TB = 320;                   // b accumulators b_p (a = r), b_u1..3 (4 x KP), then r
+  static constexpr int TBX = 224;                  // b_p for a = s, t (2 x KP), summed into b_p
+  static constexpr int TI = 0, TL = 7 * NFQ16;     // face interpolants (7 x NFQ16), lifted faces (4 x NFP16)
+  static_assert(2 * T1 <= TBX && TBX + 2 * KP <= TB && TB + 4 * KP <= 512 && TL + 4 * NFP16 <= TB, "TMEM plan");
+  static_assert(SMEM <= 232448, "shared memory");
 };
 
 namespace {
 
 constexpr uint32_t kWaitIters = 1u << 22;
+constexpr uint32_t kIssuers = 8;  // threads issuing tensor-core products (lane 0 of each warp)
 
 // Cooperative copy of `bytes` (multiple of 16) from global to shared memory.
 __device__ __forceinline__ void stage_copy(uint8_t* dst, const uint8_t* __restrict__ src, int bytes) {
@@ -89,23 +94,31 @@ __device__ __forceinline__ void stage_copy(uint8_t* dst, const uint8_t* __restri
   for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-__device__ __forceinline__ void put_split(uint8_t* base_hi, uint8_t* base_lo, uint32_t off, float x) {
-  __nv_bfloat16 h, l;
-  tc::split_bf16(x, h, l);
-  *reinterpret_cast<__nv_bfloat16*>(base_hi + off) = h;
-  *reinterpret_cast<__nv_bfloat16*>(base_lo + off) = l;
+// One product D (+)= A B^T with split operators (hi*hi + hi*lo + lo*hi).
+struct Mma3 {
+  uint32_t d, idesc;
+  uint64_t ah, al, bh, bl;  // descriptors of the first K step
+  bool acc;                 // accumulate onto D from the first instruction on
+};
+
+__device__ __forceinline__ Mma3 mk_mma3(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t a_sbo, uint32_t b_hi,
+                                        uint32_t b_lo, uint32_t b_sbo, uint32_t idesc, bool acc) {
+  return Mma3{d, idesc, tc::smem_desc(a_hi, 128, a_sbo), tc::smem_desc(a_lo, 128, a_sbo),
+              tc::smem_desc(b_hi, 128, b_sbo), tc::smem_desc(b_lo, 128, b_sbo), acc};
 }
 
-// D (+)= A B^T with split operators: hi*hi + hi*lo + lo*hi, K in steps of 16.
-__device__ __forceinline__ void mma3(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t a_sbo, uint32_t b_hi,
-                                     uint32_t b_lo, uint32_t b_sbo, int ksteps, uint32_t idesc, bool accumulate) {
-  for (int ks = 0; ks < ksteps; ++ks) {
-    const uint32_t o = (uint32_t)ks * 256u;
-    const uint64_t ah = tc::smem_desc(a_hi + o, 128, a_sbo), al = tc::smem_desc(a_lo + o, 128, a_sbo);
-    const uint64_t bh = tc::smem_desc(b_hi + o, 128, b_sbo), bl = tc::smem_desc(b_lo + o, 128, b_sbo);
-    tc::mma_bf16(d, ah, bh, idesc, (accumulate || ks > 0) ? 1u : 0u);
-    tc::mma_bf16(d, ah, bl, idesc, 1u);
-    tc::mma_bf16(d, al, bh, idesc, 1u);
+// One accumulator chain over KS steps of K = 16 (a K step moves the
+// descriptors' start address by 256 bytes, 16 in the address field).  A
+// thread blocks for about 100-200 cycles per tcgen05.mma it issues, so the
+// stage spreads its independent chains over eight issuing threads.
+template <int KS>
+__device__ __forceinline__ void mma3_chain(const Mma3& g) {
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    const uint64_t o = (uint64_t)(16 * ks);
+    tc::mma_bf16(g.d, g.ah + o, g.bh + o, g.idesc, (g.acc || ks > 0) ? 1u : 0u);
+    tc::mma_bf16(g.d, g.ah + o, g.bl + o, g.idesc, 1u);
+    tc::mma_bf16(g.d, g.al + o, g.bh + o, g.idesc, 1u);
   }
 }
 
@@ -114,24 +127,29 @@ __device__ __forceinline__ void mma3(uint32_t d, uint32_t a_hi, uint32_t a_lo, u
 template <int N, int MODE>
 __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P) {
   using T = TcDims<N>;
-  constexpr int NP = T::NP, NQ = T::NQ, NFP = T::NFP, NFQ = T::NFQ, KP = T::KP, QC = T::QC;
-  constexpr int TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16;
+  constexpr int NP = T::NP, NQ = T::NQ, NFP = T::NFP, NFQ = T::NFQ, KP = T::KP, QC = T::QC, NPS = T::NPS;
+  constexpr int TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16, NCH = T::NCH;
   const StageParams<float>& p = P.s;
   const DevOps<float>& ops = p.ops;
 
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sAQ = smem;                 // A operand: fields (volume), then b (update)
-  uint8_t* sAX = smem + T::OFF_AX;     // A operand: chunk arrays
-  uint8_t* sOP = smem + T::OFF_OP;     // B operand staging
-  float* sBF = reinterpret_cast<float*>(smem + T::OFF_BF);  // [4][NP][128] surface terms
-  uint8_t* sFA = smem;                                       // per face: A operands (combinations, then fluxes)
-  uint8_t* sFT = smem + T::OFF_FT;                           // face B operands
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + T::MAIN);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + T::MAIN + 8);
-  int* sflag = reinterpret_cast<int*>(smem + T::MAIN + 16);
+  uint8_t* sAQ = smem;                                        // A operand: fields, then b
+  uint8_t* sFA = smem;                                        // per face: combinations, then fluxes
+  float* sLS = reinterpret_cast<float*>(smem + T::SZ_FA);     // per face: lifted values [4][NFP16][128]
+  float* sTT = reinterpret_cast<float*>(smem);                // output tile [4][128][NPS]
+  uint8_t* sAX = smem + T::OFF_AX;                            // A operand: chunk arrays
+  float* sQS = reinterpret_cast<float*>(smem + T::OFF_QS);    // input tile [4][128][NPS]
+  uint8_t* sFT = smem + T::OFF_FT;                            // face B operands
+  int16_t* sGI = reinterpret_cast<int16_t*>(smem + T::OFF_GI);  // ginv [4][6][NP]
+  int16_t* sGX = reinterpret_cast<int16_t*>(smem + T::OFF_GX);  // gidx [4][6][NFP]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + T::OFF_BAR);
+  // bars: 0-3 operator slots, 4-5 first products of a chunk, 6 second products, 7 faces, 8 drain
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + T::OFF_BAR + 80);
+  int* sflag = reinterpret_cast<int*>(smem + T::OFF_BAR + 84);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quarter = warp & 3, half = warp >> 2;
+  const bool issuer = lane == 0;  // lane 0 of every warp issues one accumulator chain per product group
   const int mrow = quarter * 32 + lane;  // this thread's column within the tile (TMEM lane)
   const int64_t ncols = p.ncols;
   const int64_t fs = ncols * NP;
@@ -139,194 +157,135 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
   const int64_t ntiles = (ncols + TILE - 1) / TILE;
 
   if (tid == 0) {
-    tc::mbar_init(tc::smem_addr(mbar), 1);
+    for (int i = 0; i < 9; ++i) tc::mbar_init(tc::smem_addr(bars + i), i < 4 ? 1 : kIssuers);
     *sflag = 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), 512);
-  stage_copy(sFT, P.ops + (size_t)T::NCH * (T::SZ_OPV + T::SZ_OPU), T::SZ_FOPS);
+  stage_copy(sFT, P.ops + (size_t)NCH * (T::SZ_OPV + T::SZ_OPU), T::SZ_FOPS);
+  for (int i = tid; i < 4 * 6 * NP; i += 256) sGI[i] = ops.ginv[i];
+  for (int i = tid; i < 4 * 6 * NFP; i += 256) sGX[i] = ops.gidx[i];
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *slot;
   const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-  const uint32_t mb = tc::smem_addr(mbar);
-  uint32_t phase = 0;
+  const uint32_t bar0 = tc::smem_addr(bars);
+  auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+  uint32_t par_t1 = 0, par_m2 = 0, par_f = 0;  // phase parities (uniform)
+  uint32_t par_ld = 0, pend = 0;               // operator slots (loads by thread 0)
   bool failed = false;
 
-  auto wait_mma = [&]() {
-    if (!tc::mbar_wait(mb, phase, kWaitIters)) atomicExch(sflag, 1);
-    phase ^= 1u;
+  const uint32_t aq = tc::smem_addr(sAQ), ax = tc::smem_addr(sAX), fa = tc::smem_addr(sFA);
+  const uint32_t ft = tc::smem_addr(sFT), slots = tc::smem_addr(smem + T::OFF_SLOT);
+  auto slot_addr = [&](int s) { return slots + (uint32_t)(s * T::SZ_SLOT); };
+  const uint32_t sbo_KP = (KP / 8) * 128, sbo_16 = 2 * 128;
+  const uint8_t* vol_ops = P.ops;
+  const uint8_t* upd_ops = P.ops + (size_t)NCH * T::SZ_OPV;
+
+  // thread 0: operator slots (bulk copies completing on bars[s])
+  auto load_slot = [&](int s, const uint8_t* src, int bytes) {
+    tc::mbar_expect_tx(bar(s), (uint32_t)bytes);
+    tc::bulk_g2s(slot_addr(s), src, (uint32_t)bytes, bar(s));
+    pend |= 1u << s;
+  };
+  // every thread: the issuers wait for a slot's copy before reading it
+  auto wait_slot = [&](int s) {
+    if (issuer && !tc::mbar_wait(bar(s), (par_ld >> s) & 1u, kWaitIters)) atomicExch(sflag, 1);
+    par_ld ^= 1u << s;
+    pend &= ~(1u << s);
+  };
+  auto prefetch_volume = [&]() {
+    load_slot(0, vol_ops, T::SZ_VA);
+    load_slot(2, vol_ops + T::SZ_VA, T::SZ_VB);
+    if (NCH > 1) {
+      load_slot(1, vol_ops + T::SZ_OPV, T::SZ_VA);
+      load_slot(3, vol_ops + T::SZ_OPV + T::SZ_VA, T::SZ_VB);
+    }
+  };
+  // every thread: bounded wait on an mbarrier phase
+  auto wait_all = [&](int b, uint32_t parity) {
+    if (!tc::mbar_wait(bar(b), parity, kWaitIters)) atomicExch(sflag, 1);
     tc::fence_after();
+  };
+  auto sync_check = [&]() {
+    tc::fence_async_smem();
+    tc::fence_before();
     __syncthreads();
+    tc::fence_after();
     failed = *(volatile int*)sflag != 0;
   };
+  // volume products of chunk c
+  // volume and update products of chunk c, accumulator chain i of each group
+  auto issue_V = [&](int c, int i) {  // u_i = V_q u_i (N = 16 each), dp/dx^_a = V_q^a p (N = 48)
+    const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1);
+    if (i < 3)
+      mma3_chain<KP / 16>(mk_mma3(d + 16 * i, aq + (2 * (1 + i)) * T::A_FIELD, aq + (2 * (1 + i) + 1) * T::A_FIELD,
+                                  sbo_KP, sl, sl + T::B_V, sbo_KP, tc::idesc_bf16(128, 16), false));
+    else if (i == 3)
+      mma3_chain<KP / 16>(mk_mma3(d + 48, aq, aq + T::A_FIELD, sbo_KP, sl + 2 * T::B_V, sl + 5 * T::B_V, sbo_KP,
+                                  tc::idesc_bf16(128, 48), false));
+  };
+  // b_p += sum_a Dw_a U^a (one accumulator per a; a = r holds the surface
+  // term), b_ui += Vw g_i (onto the surface terms)
+  auto issue_DW = [&](int c, int i) {
+    const uint32_t sl = slot_addr(2 + (c & 1)), bvw = sl + 6 * T::B_P;
+    if (i < 3)
+      mma3_chain<1>(mk_mma3(tmem + (i == 0 ? T::TB : T::TBX + KP * (i - 1)), ax + (2 * i) * T::A_CH,
+                            ax + (2 * i + 1) * T::A_CH, sbo_16, sl + 2 * i * T::B_P, sl + (2 * i + 1) * T::B_P, sbo_16,
+                            tc::idesc_bf16(128, KP), i == 0 || c > 0));
+    else if (i < 6)
+      mma3_chain<1>(mk_mma3(tmem + T::TB + KP * (i - 2), ax + (2 * i) * T::A_CH, ax + (2 * i + 1) * T::A_CH, sbo_16,
+                            bvw, bvw + T::B_P, sbo_16, tc::idesc_bf16(128, KP), true));
+  };
+  auto issue_U1 = [&](int c, int f) {  // (V_q M^^{-1}) b per field (N = 16)
+    const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1);
+    if (f < 4)
+      mma3_chain<KP / 16>(mk_mma3(d + 16 * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP, sl,
+                                  sl + T::B_V, sbo_KP, tc::idesc_bf16(128, 16), false));
+  };
+  auto issue_U2 = [&](int c, int f) {  // r += P_q (W ...) per field (N = KP)
+    const uint32_t sl = slot_addr(2 + (c & 1));
+    if (f < 4)
+      mma3_chain<1>(mk_mma3(tmem + T::TB + KP * f, ax + (2 * f) * T::A_CH, ax + (2 * f + 1) * T::A_CH, sbo_16, sl,
+                            sl + T::B_P, sbo_16, tc::idesc_bf16(128, KP), c > 0));
+  };
 
-  const uint32_t aq = tc::smem_addr(sAQ), ax = tc::smem_addr(sAX), op = tc::smem_addr(sOP);
-  const uint32_t fa = tc::smem_addr(sFA), ft = tc::smem_addr(sFT);
-  const uint32_t sbo_KP = (KP / 8) * 128, sbo_16 = 2 * 128;
+  if (tid == 0 && (int64_t)blockIdx.x < ntiles) prefetch_volume();
 
   for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int64_t col0 = tile * TILE;
+    const int ncol_t = (int)(ncols - col0 < TILE ? ncols - col0 : TILE);
     int64_t cm = col0 + mrow;
-    const bool valid = cm < ncols;
-    cm = valid ? cm : ncols - 1;
+    cm = cm < ncols ? cm : ncols - 1;
     const int64_t km = cm / S;
+    const int sh = (int)(cm - km * S);
+    const int4 nbr4 = __ldg(reinterpret_cast<const int4*>(p.EToE) + km);
+    const uint32_t code4 = __ldg(reinterpret_cast<const unsigned int*>(p.fcode) + km);
 
-    // ---- fields -> split A operand: coalesced FP32 tile in the (free) A_X/B
-    // staging area, then each half splits two fields of its column ----
+    // ---- fields -> FP32 tile in shared memory (coalesced) ----
     {
-      float* stg = reinterpret_cast<float*>(sAX);  // [4][TILE * NP]
-      const int64_t nval = (ncols - col0 < TILE ? ncols - col0 : TILE) * NP;
-      for (int f = 0; f < 4; ++f) {
-        const float* src = p.Qin + f * fs + col0 * NP;
-        for (int i = tid; i < TILE * NP; i += 256) stg[f * TILE * NP + i] = i < nval ? __ldg(src + i) : 0.f;
+      const int nval = ncol_t * NP;
+#pragma unroll 10
+      for (int i = tid; i < 4 * TILE * NP; i += 256) {
+        const int f = i / (TILE * NP), r = i - f * (TILE * NP);
+        const int c = r / NP, n = r - c * NP;
+        sQS[(f * TILE + c) * NPS + n] = r < nval ? __ldg(p.Qin + f * fs + col0 * NP + r) : 0.f;
       }
-      __syncthreads();
-      for (int f = 2 * half; f < 2 * half + 2; ++f) {
-        uint8_t* hi = sAQ + (2 * f) * T::A_FIELD;
-        uint8_t* lo = hi + T::A_FIELD;
-        const float* q = stg + f * TILE * NP + mrow * NP;
-        for (int n = 0; n < KP; ++n) put_split(hi, lo, tc::kmajor_offset(mrow, n, KP), n < NP ? q[n] : 0.f);
-      }
-      __syncthreads();  // the staging area is reused by the operator chunks
     }
+    __syncthreads();
 
-    // ---- volume terms, chunk by chunk ----
-    for (int ch = 0; ch < T::NCH && !failed; ++ch) {
-      stage_copy(sOP, P.ops + (size_t)ch * T::SZ_OPV, T::SZ_OPV);
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      tc::fence_after();
-      if (tid == 0) {
-        // u_i = A(u_i) B(V_q chunk)^T, N = 16
-        const uint32_t bvq = op, bva = op + 2 * T::B_V;
-        for (int i = 0; i < 3; ++i)
-          mma3(tmem + T::TV + 16 * i, aq + (2 * (1 + i)) * T::A_FIELD, aq + (2 * (1 + i) + 1) * T::A_FIELD, sbo_KP,
-               bvq, bvq + T::B_V, sbo_KP, KP / 16, tc::idesc_bf16(128, 16), false);
-        // dp/dx^_a = A(p) B(V_q^a chunk)^T, N = 48 (rows a*16 + q)
-        mma3(tmem + T::TV + 48, aq, aq + T::A_FIELD, sbo_KP, bva, bva + 3 * T::B_V, sbo_KP, KP / 16,
-             tc::idesc_bf16(128, 48), false);
-        tc::commit(mb);
-      }
-      // geometric factors of this thread's 8 quadrature points, loaded while the MMA runs
-      float G[9][8];
-      {
-        const float* gk = P.vgeo_il + (km >> 7) * 11 * NQ * 128 + (km & 127);
+    // ---- surface terms (Sec. 4.1, Sec. 6.4), face by face; the lifted terms
+    // are gathered into registers at this thread's volume nodes ----
+    float bS[2][NP];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int q = ch * QC + 8 * half + j;
+    for (int fi = 0; fi < 2; ++fi)
 #pragma unroll
-          for (int c = 0; c < 9; ++c) G[c][j] = q < NQ ? __ldg(gk + (size_t)(c * NQ + q) * 128) : 0.f;
-        }
-      }
-      wait_mma();
-      if (failed) break;
-      // epilogue: U^a and -(J grad p)_i at this thread's 8 quadrature points
-      {
-        float u[3][8], d[3][8];
-        tc::tmem_ld24(lane_base + T::TV + 8 * half, lane_base + T::TV + 16 + 8 * half, lane_base + T::TV + 32 + 8 * half,
-                      u[0], u[1], u[2]);
-        tc::tmem_ld24(lane_base + T::TV + 48 + 8 * half, lane_base + T::TV + 64 + 8 * half,
-                      lane_base + T::TV + 80 + 8 * half, d[0], d[1], d[2]);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int ql = 8 * half + j;
-          const uint32_t off = tc::kmajor_offset(mrow, ql, QC);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const float U = G[a * 3][j] * u[0][j] + G[a * 3 + 1][j] * u[1][j] + G[a * 3 + 2][j] * u[2][j];
-            put_split(sAX + (2 * a) * T::A_CH, sAX + (2 * a + 1) * T::A_CH, off, U);
-          }
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const float g = -(G[i][j] * d[0][j] + G[3 + i][j] * d[1][j] + G[6 + i][j] * d[2][j]);
-            put_split(sAX + (2 * (3 + i)) * T::A_CH, sAX + (2 * (3 + i) + 1) * T::A_CH, off, g);
-          }
-        }
-      }
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      tc::fence_after();
-      if (tid == 0) {
-        const uint32_t bdw = op + 8 * T::B_V, bvw = bdw + 6 * T::B_P;
-        for (int a = 0; a < 3; ++a)
-          mma3(tmem + T::TB, ax + (2 * a) * T::A_CH, ax + (2 * a + 1) * T::A_CH, sbo_16, bdw + 2 * a * T::B_P,
-               bdw + (2 * a + 1) * T::B_P, sbo_16, 1, tc::idesc_bf16(128, KP), ch > 0 || a > 0);
-        for (int i = 0; i < 3; ++i)
-          mma3(tmem + T::TB + KP * (1 + i), ax + (2 * (3 + i)) * T::A_CH, ax + (2 * (3 + i) + 1) * T::A_CH, sbo_16,
-               bvw, bvw + T::B_P, sbo_16, 1, tc::idesc_bf16(128, KP), ch > 0);
-        tc::commit(mb);
-      }
-      wait_mma();
-    }
-    if (failed) break;
+      for (int n = 0; n < NP; ++n) bS[fi][n] = 0.f;
 
-    // ---- surface terms (Sec. 6.4), face by face: gather on CUDA cores, V_tri
-    // and the lift V_tri^T diag(w_f) on the tensor cores, flux in between ----
-    for (int i = tid; i < 4 * NP * TILE; i += 256) sBF[i] = 0.f;
     for (int f = 0; f < 4 && !failed; ++f) {
-      const int col = mrow;
-      int pio_f;
-      // (i) [p], {u}, [u] at the face nodes, owner's node order -> split A operands
-      {
-        constexpr int JH = NFP16 / 2;
-        const int code = p.fcode[km * 4 + f];
-        const int pio = code % 6, pin = (code / 6) % 6, fn = code / 36;
-        pio_f = pio;
-        const int sh = (int)(cm - km * S);
-        const int64_t kn = p.EToE[km * 4 + f];
-        const int16_t* go = ops.gidx + (f * 6 + pio) * NFP;
-        const int16_t* gn = ops.gidx + (fn * 6 + pin) * NFP;
-        const int64_t nb = kn >= 0 ? (kn * S + sh) * NP : 0;
-#pragma unroll
-        for (int jj = 0; jj < JH; ++jj) {
-          const int j = half * JH + jj;
-          float cv[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          if (j < NFP) {
-            const int64_t bo = cm * NP + go[j];
-            const float pm = __ldg(p.Qin + bo), u1m = __ldg(p.Qin + fs + bo), u2m = __ldg(p.Qin + 2 * fs + bo),
-                        u3m = __ldg(p.Qin + 3 * fs + bo);
-            float pp, u1p, u2p, u3p;
-            if (kn >= 0) {
-              const int64_t b = nb + gn[j];
-              pp = __ldg(p.Qin + b);
-              u1p = __ldg(p.Qin + fs + b);
-              u2p = __ldg(p.Qin + 2 * fs + b);
-              u3p = __ldg(p.Qin + 3 * fs + b);
-            } else {  // Dirichlet ghost state (Sec. 4.1)
-              pp = -pm;
-              u1p = u1m;
-              u2p = u2m;
-              u3p = u3m;
-            }
-            cv[0] = pp - pm;
-            cv[1] = 0.5f * (u1p + u1m);
-            cv[2] = 0.5f * (u2p + u2m);
-            cv[3] = 0.5f * (u3p + u3m);
-            cv[4] = u1p - u1m;
-            cv[5] = u2p - u2m;
-            cv[6] = u3p - u3m;
-          }
-          const uint32_t off = tc::kmajor_offset(col, j, NFP16);
-#pragma unroll
-          for (int c = 0; c < 7; ++c) put_split(sFA + (2 * c) * T::A_FN, sFA + (2 * c + 1) * T::A_FN, off, cv[c]);
-        }
-      }
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      tc::fence_after();
-      if (tid == 0) {
-        for (int c = 0; c < 7; ++c) {
-          const uint32_t d = tmem + (c < 4 ? T::TI_LO + c * NFQ16 : T::TI_HI + (c - 4) * NFQ16);
-          mma3(d, fa + (2 * c) * T::A_FN, fa + (2 * c + 1) * T::A_FN, (NFP16 / 8) * 128, ft, ft + T::B_TRI,
-               (NFP16 / 8) * 128, NFP16 / 16, tc::idesc_bf16(128, NFQ16), false);
-        }
-        tc::commit(mb);
-      }
-      // normals x surface Jacobian at this thread's face points, loaded while the MMA runs
+      const int code = (int)((code4 >> (8 * f)) & 0xffu);
+      const int pio = code % 6, pin = (code / 6) % 6, fn = code / 36;
+      // normals x surface Jacobian at this thread's face points, needed after the first products
       constexpr int QH = NFQ16 / 2;
       float nv[3][QH];
       {
@@ -338,116 +297,310 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
           for (int dd = 0; dd < 3; ++dd) nv[dd][qq] = q < NFQ ? __ldg(nfg + (size_t)(dd * 4 * NFQ + q) * 128) : 0.f;
         }
       }
-      wait_mma();
-      if (failed) break;
-      // (ii) strong-weak flux (Sec. 4.1) at this thread's face points -> split A operands
+      // (i) [p], {u}, [u] at the face nodes, owner's node order -> split A operands
       {
-        float v[7][QH];
+        const int64_t kn = f == 0 ? nbr4.x : f == 1 ? nbr4.y : f == 2 ? nbr4.z : nbr4.w;
+        const int16_t* go = sGX + (f * 6 + pio) * NFP;
+        const int16_t* gn = sGX + (fn * 6 + pin) * NFP;
+        const int64_t nb = kn >= 0 ? (kn * S + sh) * NP : 0;
+        // all neighbour loads first, from clamped (always valid) addresses
+        const int64_t nbv = kn >= 0 ? nb : cm * NP;
+        float qp[4][8], qm[4][8];
 #pragma unroll
-        for (int c = 0; c < 7; ++c) {
-          const uint32_t base = lane_base + (c < 4 ? T::TI_LO + c * NFQ16 : T::TI_HI + (c - 4) * NFQ16) + half * QH;
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = half * 8 + jj < NFP ? half * 8 + jj : 0;
+          const int64_t b = nbv + gn[j];
 #pragma unroll
-          for (int q8 = 0; q8 < QH; q8 += 8) {
-            float x[8];
-            tc::tmem_ld8(base + q8, x);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[c][q8 + j] = x[j];
-          }
+          for (int fl = 0; fl < 4; ++fl) qp[fl][jj] = __ldg(p.Qin + fl * fs + b);
         }
 #pragma unroll
-        for (int qq = 0; qq < QH; ++qq) {
-          const int q = half * QH + qq;
-          const float nx = nv[0][qq], ny = nv[1][qq], nz = nv[2][qq];
-          float F[4] = {0.f, 0.f, 0.f, 0.f};
-          if (q < NFQ) {
-            const float Jf = sqrtf(nx * nx + ny * ny + nz * nz);
-            const float aun = v[1][qq] * nx + v[2][qq] * ny + v[3][qq] * nz;
-            const float jun = (v[4][qq] * nx + v[5][qq] * ny + v[6][qq] * nz) / Jf;
-            F[0] = -aun + 0.5f * p.tau_p * v[0][qq] * Jf;
-            const float sc = -0.5f * (v[0][qq] - p.tau_u * jun);
-            F[1] = sc * nx;
-            F[2] = sc * ny;
-            F[3] = sc * nz;
-          }
-          const uint32_t off = tc::kmajor_offset(col, q, NFQ16);
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = half * 8 + jj < NFP ? half * 8 + jj : 0;
+          const int o = go[j];
 #pragma unroll
-          for (int fld = 0; fld < 4; ++fld)
-            put_split(sFA + (2 * fld) * T::A_FQ, sFA + (2 * fld + 1) * T::A_FQ, off, F[fld]);
+          for (int fl = 0; fl < 4; ++fl) qm[fl][jj] = sQS[(fl * TILE + mrow) * NPS + o];
         }
+        float cv[7][8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const bool on = half * 8 + jj < NFP;
+          // Dirichlet ghost state on the boundary (Sec. 4.1): p+ = -p-, u+ = u-
+          const float pp = kn >= 0 ? qp[0][jj] : -qm[0][jj];
+          float up[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) up[i] = kn >= 0 ? qp[1 + i][jj] : qm[1 + i][jj];
+          cv[0][jj] = on ? pp - qm[0][jj] : 0.f;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            cv[1 + i][jj] = on ? 0.5f * (up[i] + qm[1 + i][jj]) : 0.f;
+            cv[4 + i][jj] = on ? up[i] - qm[1 + i][jj] : 0.f;
+          }
+        }
+        const uint32_t off = tc::kmajor_offset(mrow, 8 * half, NFP16);
+#pragma unroll
+        for (int c = 0; c < 7; ++c) tc::split_store8(sFA + (2 * c) * T::A_FN + off, sFA + (2 * c + 1) * T::A_FN + off, cv[c]);
       }
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      tc::fence_after();
-      if (tid == 0) {
-        const uint32_t bl = ft + 2 * T::B_TRI;
-        for (int fld = 0; fld < 4; ++fld)
-          mma3(tmem + T::TL + fld * NFP16, fa + (2 * fld) * T::A_FQ, fa + (2 * fld + 1) * T::A_FQ, (NFQ16 / 8) * 128, bl,
-               bl + T::B_TRI, (NFQ16 / 8) * 128, NFQ16 / 16, tc::idesc_bf16(128, NFP16), false);
-        tc::commit(mb);
-      }
-      wait_mma();
+      sync_check();
       if (failed) break;
-      // (iii) add the lifted face terms to the volume nodes of this thread's two fields
+      if (issuer) {
+        if (warp < 7)
+          mma3_chain<NFP16 / 16>(mk_mma3(tmem + T::TI + warp * NFQ16, fa + (2 * warp) * T::A_FN,
+                                         fa + (2 * warp + 1) * T::A_FN, (NFP16 / 8) * 128, ft, ft + T::B_TRI,
+                                         (NFP16 / 8) * 128, tc::idesc_bf16(128, NFQ16), false));
+        tc::commit(bar(7));
+      }
+      wait_all(7, par_f);
+      par_f ^= 1u;
+      // (ii) strong-weak flux (Sec. 4.1) at this thread's face points -> split A operands
 #pragma unroll
-      for (int fi = 0; fi < 2; ++fi) {
-        const int fld = 2 * half + fi;
-        const int16_t* go = ops.gidx + (f * 6 + pio_f) * NFP;
+      for (int b8 = 0; b8 < QH; b8 += 8) {
+        const int q0 = half * QH + b8;
+        uint32_t v[7][8];
 #pragma unroll
-        for (int j8 = 0; j8 < NFP16; j8 += 8) {
-          float x[8];
-          tc::tmem_ld8(lane_base + T::TL + fld * NFP16 + j8, x);
+        for (int c = 0; c < 7; ++c) tc::tmem_ld8_nw(lane_base + T::TI + c * NFQ16 + q0, v[c]);
+        tc::wait_ld();
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (j8 + j < NFP) sBF[(fld * NP + go[j8 + j]) * TILE + col] += x[j];
+        for (int c = 0; c < 7; ++c) tc::pin8(v[c]);
+        float F[4][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float nx = nv[0][b8 + j], ny = nv[1][b8 + j], nz = nv[2][b8 + j];
+          const float jp = __uint_as_float(v[0][j]);
+          F[0][j] = F[1][j] = F[2][j] = F[3][j] = 0.f;
+          if (q0 + j < NFQ) {
+            const float nn = nx * nx + ny * ny + nz * nz;
+            const float rJ = rsqrtf(nn);  // 1 / J^f (|n J^f| = J^f)
+            const float Jf = nn * rJ;
+            const float aun = __uint_as_float(v[1][j]) * nx + __uint_as_float(v[2][j]) * ny +
+                              __uint_as_float(v[3][j]) * nz;
+            const float jun = (__uint_as_float(v[4][j]) * nx + __uint_as_float(v[5][j]) * ny +
+                               __uint_as_float(v[6][j]) * nz) *
+                              rJ;
+            F[0][j] = -aun + 0.5f * p.tau_p * jp * Jf;
+            const float sc = -0.5f * (jp - p.tau_u * jun);
+            F[1][j] = sc * nx;
+            F[2][j] = sc * ny;
+            F[3][j] = sc * nz;
+          }
+        }
+        const uint32_t off = tc::kmajor_offset(mrow, q0, NFQ16);
+#pragma unroll
+        for (int fld = 0; fld < 4; ++fld)
+          tc::split_store8(sFA + (2 * fld) * T::A_FQ + off, sFA + (2 * fld + 1) * T::A_FQ + off, F[fld]);
+      }
+      sync_check();
+      if (failed) break;
+      if (issuer) {
+        const uint32_t bl = ft + 2 * T::B_TRI;
+        if (warp < 4)
+          mma3_chain<NFQ16 / 16>(mk_mma3(tmem + T::TL + warp * NFP16, fa + (2 * warp) * T::A_FQ,
+                                         fa + (2 * warp + 1) * T::A_FQ, (NFQ16 / 8) * 128, bl, bl + T::B_TRI,
+                                         (NFQ16 / 8) * 128, tc::idesc_bf16(128, NFP16), false));
+        tc::commit(bar(7));
+      }
+      wait_all(7, par_f);
+      par_f ^= 1u;
+      // (iii) lifted values (owner's node order) -> this thread's scratch -> volume nodes
+      {
+        uint32_t L[2][NFP16 / 8][8];
+#pragma unroll
+        for (int fi = 0; fi < 2; ++fi)
+#pragma unroll
+          for (int j8 = 0; j8 < NFP16 / 8; ++j8)
+            tc::tmem_ld8_nw(lane_base + T::TL + (2 * half + fi) * NFP16 + 8 * j8, L[fi][j8]);
+        tc::wait_ld();
+#pragma unroll
+        for (int fi = 0; fi < 2; ++fi)
+#pragma unroll
+          for (int j8 = 0; j8 < NFP16 / 8; ++j8) tc::pin8(L[fi][j8]);
+#pragma unroll
+        for (int fi = 0; fi < 2; ++fi)
+#pragma unroll
+          for (int j = 0; j < NFP; ++j)
+            sLS[((2 * half + fi) * NFP16 + j) * TILE + mrow] = __uint_as_float(L[fi][j >> 3][j & 7]);
+        const int16_t* gi = sGI + (f * 6 + pio) * NP;
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          const int jj = gi[n];
+          if (jj >= 0) {
+#pragma unroll
+            for (int fi = 0; fi < 2; ++fi) bS[fi][n] += sLS[((2 * half + fi) * NFP16 + jj) * TILE + mrow];
+          }
         }
       }
-      tc::fence_before();
-      __syncthreads();
-      tc::fence_after();
     }
     if (failed) break;
 
-    // ---- b = volume (TMEM) + surface (smem) + source -> split A operand ----
+    // ---- surface (+ point source) -> b accumulators in TMEM; fields -> split A
+    // operands (over the lifted-value scratch: every thread has finished with it) ----
+    __syncthreads();
     {
-      const int sh = (int)(cm - km * S);
-      const bool src = p.src_elem != nullptr && p.src_elem[sh] == (int32_t)km;
-      for (int f = 2 * half; f < 2 * half + 2; ++f) {
-        uint8_t* hi = sAQ + (2 * f) * T::A_FIELD;
-        uint8_t* lo = hi + T::A_FIELD;
+      if (half == 0 && p.src_elem != nullptr && p.src_elem[sh] == (int32_t)km) {
+#pragma unroll
+        for (int n = 0; n < NP; ++n) bS[0][n] += p.src_amp * p.src_vec[sh * NP + n];
+      }
+#pragma unroll
+      for (int fi = 0; fi < 2; ++fi) {
+        const int f = 2 * half + fi;
+#pragma unroll
         for (int n0 = 0; n0 < KP; n0 += 8) {
-          float v[8];
-          tc::tmem_ld8(lane_base + T::TB + KP * f + n0, v);
+          float v[8], x[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const int n = n0 + j;
-            float b = 0.f;
-            if (n < NP) {
-              b = v[j] + sBF[(f * NP + n) * TILE + mrow];
-              if (f == 0 && src) b += p.src_amp * p.src_vec[sh * NP + n];
-            }
-            put_split(hi, lo, tc::kmajor_offset(mrow, n, KP), b);
+            v[j] = n0 + j < NP ? bS[fi][n0 + j] : 0.f;
+            x[j] = n0 + j < NP ? sQS[(f * TILE + mrow) * NPS + n0 + j] : 0.f;
           }
+          tc::tmem_st8(lane_base + T::TB + KP * f + n0, v);
+          const uint32_t off = tc::kmajor_offset(mrow, n0, KP);
+          tc::split_store8(sAQ + (2 * f) * T::A_FIELD + off, sAQ + (2 * f + 1) * T::A_FIELD + off, x);
+        }
+      }
+      tc::wait_st();
+    }
+    sync_check();
+    if (failed) break;
+
+    // ---- volume terms (Sec. 6.4), chunks of 16 quadrature points, pipelined:
+    // the products of chunk c + 2 and of chunk c run while the CUDA cores
+    // work on chunk c + 1 ----
+    wait_slot(0);
+    if (issuer) {
+      issue_V(0, warp);
+      tc::commit(bar(4));
+    }
+    if (NCH > 1) {
+      wait_slot(1);
+      if (issuer) {
+        issue_V(1, warp);
+        tc::commit(bar(5));
+      }
+    }
+    for (int c = 0; c < NCH; ++c) {
+      float G[9][8];
+      {
+        const float* gk = P.vgeo_il + (km >> 7) * 11 * NQ * 128 + (km & 127);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int q = c * QC + 8 * half + j;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) G[k][j] = q < NQ ? __ldg(gk + (size_t)(k * NQ + q) * 128) : 0.f;
+        }
+      }
+      wait_all(4 + (c & 1), (par_t1 >> (c & 1)) & 1u);
+      par_t1 ^= 1u << (c & 1);
+      if (tid == 0 && c + 2 < NCH) load_slot(c & 1, vol_ops + (size_t)(c + 2) * T::SZ_OPV, T::SZ_VA);
+      float U[3][8], g[3][8];
+      {
+        const uint32_t t = lane_base + (uint32_t)((c & 1) * T::T1) + 8 * half;
+        uint32_t u[3][8], d[3][8];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          tc::tmem_ld8_nw(t + 16 * i, u[i]);
+          tc::tmem_ld8_nw(t + 48 + 16 * i, d[i]);
+        }
+        tc::wait_ld();
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          tc::pin8(u[i]);
+          tc::pin8(d[i]);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float u0 = __uint_as_float(u[0][j]), u1 = __uint_as_float(u[1][j]), u2 = __uint_as_float(u[2][j]);
+          const float d0 = __uint_as_float(d[0][j]), d1 = __uint_as_float(d[1][j]), d2 = __uint_as_float(d[2][j]);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) U[a][j] = G[a * 3][j] * u0 + G[a * 3 + 1][j] * u1 + G[a * 3 + 2][j] * u2;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) g[i][j] = -(G[i][j] * d0 + G[3 + i][j] * d1 + G[6 + i][j] * d2);
+        }
+      }
+      if (c > 0) {  // the chunk arrays and the B slot of chunk c - 1 are free once its products complete
+        wait_all(6, par_m2);
+        par_m2 ^= 1u;
+        if (tid == 0 && c + 1 < NCH)
+          load_slot(2 + ((c + 1) & 1), vol_ops + (size_t)(c + 1) * T::SZ_OPV + T::SZ_VA, T::SZ_VB);
+      }
+      {
+        const uint32_t off = tc::kmajor_offset(mrow, 8 * half, QC);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          tc::split_store8(sAX + (2 * a) * T::A_CH + off, sAX + (2 * a + 1) * T::A_CH + off, U[a]);
+          tc::split_store8(sAX + (2 * (3 + a)) * T::A_CH + off, sAX + (2 * (3 + a) + 1) * T::A_CH + off, g[a]);
+        }
+      }
+      sync_check();
+      if (failed) break;
+      wait_slot(2 + (c & 1));
+      if (issuer) {
+        issue_DW(c, warp);
+        tc::commit(bar(6));
+      }
+      if (c + 2 < NCH) {
+        wait_slot(c & 1);
+        if (issuer) {
+          issue_V(c + 2, warp);
+          tc::commit(bar(4 + (c & 1)));
         }
       }
     }
-
-    // ---- weight-adjusted update, chunk by chunk ----
-    for (int ch = 0; ch < T::NCH && !failed; ++ch) {
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      stage_copy(sOP, P.ops + (size_t)T::NCH * T::SZ_OPV + (size_t)ch * T::SZ_OPU, T::SZ_OPU);
-      tc::fence_async_smem();
-      __syncthreads();
-      tc::fence_after();
-      if (tid == 0) {
-        for (int f = 0; f < 4; ++f)
-          mma3(tmem + T::TU + 16 * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP, op,
-               op + T::B_V, sbo_KP, KP / 16, tc::idesc_bf16(128, 16), false);
-        tc::commit(mb);
+    if (failed) break;
+    wait_all(6, par_m2);
+    par_m2 ^= 1u;
+    if (tid == 0) {  // update operators of chunks 0 and 1
+      load_slot(0, upd_ops, T::SZ_UA);
+      load_slot(2, upd_ops + T::SZ_UA, T::SZ_UB);
+      if (NCH > 1) {
+        load_slot(1, upd_ops + T::SZ_OPU, T::SZ_UA);
+        load_slot(3, upd_ops + T::SZ_OPU + T::SZ_UA, T::SZ_UB);
       }
-      // weights of this thread's two fields at the 16 points of the chunk, loaded while the MMA runs
+    }
+
+    // ---- b -> split A operand ----
+#pragma unroll
+    for (int fi = 0; fi < 2; ++fi) {
+      const int f = 2 * half + fi;
+#pragma unroll
+      for (int n0 = 0; n0 < KP; n0 += 8) {
+        uint32_t v[8], v1[8], v2[8];
+        tc::tmem_ld8_nw(lane_base + T::TB + KP * f + n0, v);
+        if (f == 0) {  // b_p = sum over the three derivative directions
+          tc::tmem_ld8_nw(lane_base + T::TBX + n0, v1);
+          tc::tmem_ld8_nw(lane_base + T::TBX + KP + n0, v2);
+        }
+        tc::wait_ld();
+        tc::pin8(v);
+        float x[8];
+        if (f == 0) {
+          tc::pin8(v1);
+          tc::pin8(v2);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            x[j] = n0 + j < NP ? __uint_as_float(v[j]) + __uint_as_float(v1[j]) + __uint_as_float(v2[j]) : 0.f;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) x[j] = n0 + j < NP ? __uint_as_float(v[j]) : 0.f;
+        }
+        const uint32_t off = tc::kmajor_offset(mrow, n0, KP);
+        tc::split_store8(sAQ + (2 * f) * T::A_FIELD + off, sAQ + (2 * f + 1) * T::A_FIELD + off, x);
+      }
+    }
+    sync_check();
+    if (failed) break;
+
+    // ---- weight-adjusted update (Sec. 6.2, Eq. (matfree); Sec. 7), pipelined like the volume ----
+    wait_slot(0);
+    if (issuer) {
+      issue_U1(0, warp);
+      tc::commit(bar(4));
+    }
+    if (NCH > 1) {
+      wait_slot(1);
+      if (issuer) {
+        issue_U1(1, warp);
+        tc::commit(bar(5));
+      }
+    }
+    for (int c = 0; c < NCH; ++c) {
       float wt[2][16];
 #pragma unroll
       for (int fi = 0; fi < 2; ++fi) {
@@ -455,69 +608,135 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
         const float* w = P.vgeo_il + ((km >> 7) * 11 + (f == 0 ? 9 : 10)) * NQ * 128 + (km & 127);
 #pragma unroll
         for (int ql = 0; ql < 16; ++ql) {
-          const int q = ch * QC + ql;
+          const int q = c * QC + ql;
           wt[fi][ql] = q < NQ ? __ldg(w + (size_t)q * 128) : 0.f;
         }
       }
-      wait_mma();
-      if (failed) break;
+      wait_all(4 + (c & 1), (par_t1 >> (c & 1)) & 1u);
+      par_t1 ^= 1u << (c & 1);
+      if (tid == 0 && c + 2 < NCH) load_slot(c & 1, upd_ops + (size_t)(c + 2) * T::SZ_OPU, T::SZ_UA);
+      float x[2][16];
+      {
+        const uint32_t t = lane_base + (uint32_t)((c & 1) * T::T1);
+        uint32_t v[2][2][8];
+#pragma unroll
+        for (int fi = 0; fi < 2; ++fi) {
+          tc::tmem_ld8_nw(t + 16 * (2 * half + fi), v[fi][0]);
+          tc::tmem_ld8_nw(t + 16 * (2 * half + fi) + 8, v[fi][1]);
+        }
+        tc::wait_ld();
+#pragma unroll
+        for (int fi = 0; fi < 2; ++fi) {
+          tc::pin8(v[fi][0]);
+          tc::pin8(v[fi][1]);
+#pragma unroll
+          for (int ql = 0; ql < 16; ++ql) x[fi][ql] = __uint_as_float(v[fi][ql >> 3][ql & 7]) * wt[fi][ql];
+        }
+      }
+      if (c > 0) {
+        wait_all(6, par_m2);
+        par_m2 ^= 1u;
+        if (tid == 0 && c + 1 < NCH)
+          load_slot(2 + ((c + 1) & 1), upd_ops + (size_t)(c + 1) * T::SZ_OPU + T::SZ_UA, T::SZ_UB);
+      }
 #pragma unroll
       for (int fi = 0; fi < 2; ++fi) {
         const int f = 2 * half + fi;
-        float v0[8], v1[8], vdummy[8];
-        tc::tmem_ld24(lane_base + T::TU + 16 * f, lane_base + T::TU + 16 * f + 8, lane_base + T::TU + 16 * f, v0, v1,
-                      vdummy);
 #pragma unroll
-        for (int ql = 0; ql < 16; ++ql) {
-          const float x = (ql < 8 ? v0[ql] : v1[ql - 8]) * wt[fi][ql];
-          put_split(sAX + (2 * f) * T::A_CH, sAX + (2 * f + 1) * T::A_CH, tc::kmajor_offset(mrow, ql, QC), x);
+        for (int h8 = 0; h8 < 2; ++h8) {
+          const uint32_t off = tc::kmajor_offset(mrow, 8 * h8, QC);
+          float y[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) y[j] = x[fi][8 * h8 + j];
+          tc::split_store8(sAX + (2 * f) * T::A_CH + off, sAX + (2 * f + 1) * T::A_CH + off, y);
         }
       }
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      tc::fence_after();
-      if (tid == 0) {
-        const uint32_t bpq = op + 2 * T::B_V;
-        for (int f = 0; f < 4; ++f)
-          mma3(tmem + T::TR + KP * f, ax + (2 * f) * T::A_CH, ax + (2 * f + 1) * T::A_CH, sbo_16, bpq, bpq + T::B_P,
-               sbo_16, 1, tc::idesc_bf16(128, KP), ch > 0);
-        tc::commit(mb);
+      sync_check();
+      if (failed) break;
+      wait_slot(2 + (c & 1));
+      if (issuer) {
+        issue_U2(c, warp);
+        tc::commit(bar(6));
       }
-      wait_mma();
+      if (c + 2 < NCH) {
+        wait_slot(c & 1);
+        if (issuer) {
+          issue_U1(c + 2, warp);
+          tc::commit(bar(4 + (c & 1)));
+        }
+      }
     }
     if (failed) break;
+    wait_all(6, par_m2);
+    par_m2 ^= 1u;
+    if (tid == 0 && tile + gridDim.x < ntiles) prefetch_volume();
 
-    // ---- epilogue: RHS or LSRK ----
-    for (int f = 2 * half; f < 2 * half + 2; ++f) {
-      for (int n0 = 0; n0 < KP; n0 += 8) {
-        float v[8];
-        tc::tmem_ld8(lane_base + T::TR + KP * f + n0, v);
-        if (!valid) continue;
+    // ---- epilogue: r -> FP32 tile -> coalesced dQ/dt, or the LSRK update (Sec. 5.2) ----
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int n = n0 + j;
-          if (n >= NP) continue;
-          const int64_t idx = f * fs + cm * NP + n;
-          if (MODE == kRhs) {
-            p.out[idx] = v[j];
-          } else {
-            const float r = p.rk_a * p.res[idx] + p.dt * v[j];
-            p.res[idx] = r;
-            p.Qout[idx] = __ldg(p.Qin + idx) + p.rk_b * r;
-          }
+    for (int fi = 0; fi < 2; ++fi) {
+      const int f = 2 * half + fi;
+#pragma unroll
+      for (int n0 = 0; n0 < KP; n0 += 8) {
+        uint32_t v[8];
+        tc::tmem_ld8_nw(lane_base + T::TB + KP * f + n0, v);
+        tc::wait_ld();
+        tc::pin8(v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (n0 + j < NP) sTT[(f * TILE + mrow) * NPS + n0 + j] = __uint_as_float(v[j]);
+      }
+    }
+    sync_check();
+    {
+      const int nval = ncol_t * NP;
+#pragma unroll 4
+      for (int i = tid; i < 4 * TILE * NP; i += 256) {
+        const int f = i / (TILE * NP), r = i - f * (TILE * NP);
+        if (r >= nval) continue;
+        const int c = r / NP, n = r - c * NP;
+        const float v = sTT[(f * TILE + c) * NPS + n];
+        const int64_t idx = f * fs + col0 * NP + r;
+        if (MODE == kRhs) {
+          p.out[idx] = v;
+        } else {
+          const float rr = p.rk_a * p.res[idx] + p.dt * v;
+          p.res[idx] = rr;
+          p.Qout[idx] = __ldg(p.Qin + idx) + p.rk_b * rr;
         }
       }
     }
-    tc::fence_before();
     __syncthreads();
-    tc::fence_after();
   }
 
-  if (failed && tid == 0) atomicExch(P.err, 1);
+  // drain: operator copies still in flight and every issued product
+  if (tid == 0)
+    for (int s = 0; s < 4; ++s)
+      if (pend & (1u << s)) tc::mbar_wait(bar(s), (par_ld >> s) & 1u, kWaitIters);
+  if (issuer) {
+    tc::commit(bar(8));
+    tc::mbar_wait(bar(8), 0, kWaitIters);
+  }
+  __syncthreads();
+  if (tid == 0 && *(volatile int*)sflag != 0) atomicExch(P.err, 1);
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// Failure path of the bounded waits: one block waits, with the same loop the
+// stage kernel uses, on an mbarrier that nothing arrives at; the expired wait
+// sets the error flag exactly as in the stage kernel.
+__global__ void bounded_wait_selftest_kernel(int* err, uint32_t max_iters) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) tc::mbar_init(tc::smem_addr(&mbar), 1);
+  __syncthreads();
+  const bool ok = tc::mbar_wait(tc::smem_addr(&mbar), 0, max_iters);
+  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+cudaError_t launch_bounded_wait_selftest(int* err, uint32_t max_iters, cudaStream_t stream) {
+  bounded_wait_selftest_kernel<<<1, 32, 0, stream>>>(err, max_iters);
+  return cudaGetLastError();
 }
 
 template <int N>

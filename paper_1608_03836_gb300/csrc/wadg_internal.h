@@ -94,6 +94,7 @@ struct TcStageParams {
 };
 cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int grid, cudaStream_t stream);
 bool pack_tc_ops(int N, const RefOps& o, std::vector<uint8_t>& out);
+cudaError_t launch_bounded_wait_selftest(int* err, uint32_t max_iters, cudaStream_t stream);
 
 // Batches of FP32 meshes (batch.cu).
 int batch_cols_per_block(int N, int rule);

@@ -82,6 +82,24 @@ def test_shots_and_ragged_tail(W, precision):
         assert l2 < TOL[precision] and mx < 10 * TOL[precision], (s, l2, mx)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp32_3xbf16"])
+def test_more_tiles_than_blocks(W, precision):
+    """6,000 tets x 4 shots = 24,000 columns: more 128-column tiles (187.5)
+    than resident blocks, so persistent blocks take several tiles, the last
+    one ragged; heterogeneous c^2."""
+    N, S = 4, 4
+    VXYZ, EToV, geom = make_mesh_inputs(10, N)
+    om = oracle_case(VXYZ, EToV, geom, N)
+    m = library_mesh(VXYZ, EToV, geom, N, precision, shots=S, c2="heterogeneous")
+    Q = random_Q(m.K, S, m.Np, seed=31)
+    got = _gpu_rhs(W, m, Q)
+    W.wadg_device_status(m)
+    c2q = oracle_c2(om, "heterogeneous")
+    for s in range(S):
+        l2, mx = rel_errors(got[:, :, s], _oracle_rhs(om, Q[:, :, s], c2q=c2q))
+        assert l2 < TOL[precision] and mx < 10 * TOL[precision], (s, l2, mx)
+
+
 def test_single_element_all_boundary(W):
     VXYZ = np.array([[-1.0, -1, -1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]])
     EToV = np.array([[0, 1, 2, 3]])
@@ -207,3 +225,20 @@ def test_sources_and_receivers_match_oracle(W, precision):
         l2, _ = rel_errors(got_Q[:, :, s], om.ref.to_nodal(c))
         l2t, _ = rel_errors(got_tr[:, s], np.array(want_tr))
         assert l2 < TOL[precision] and l2t < TOL[precision], (s, l2, l2t)
+
+
+def test_bounded_wait_expiry_is_reported(W):
+    """A device wait that nothing completes gives up after its budget and the
+    host reads WADG_ETIMEOUT; the context stays usable and the flag clears."""
+    import torch
+    VXYZ, EToV, geom = make_mesh_inputs(1, 3)
+    m = library_mesh(VXYZ, EToV, geom, 3, "fp32_3xbf16")
+    W.wadg_selftest_bounded_wait(m, 2000)
+    with pytest.raises(W.WadgError) as e:
+        W.wadg_device_status(m)
+    assert e.value.status == -6
+    Q = torch.zeros((4, m.K, 1, m.Np), dtype=torch.float32, device="cuda")
+    out = torch.empty_like(Q)
+    W.wadg_rhs(m, Q, out)
+    W.wadg_device_status(m)
+    assert float(out.abs().max()) == 0.0
