@@ -66,7 +66,8 @@ enum wadg_precision {
     WADG_FP32_3XBF16 = 3    /* FP32 fields; the dense products of the stage on
                                the tensor cores with split bf16 operands
                                (hi*hi + hi*lo + lo*hi, FP32 accumulation);
-                               N <= 4.  Adjoint and diagnostics as WADG_FP32. */
+                               N <= 4 and K * shots * Np < 2^31.  Adjoint
+                               and diagnostics as WADG_FP32. */
 };
 
 /* Library version as major*10000 + minor*100 + patch. */

@@ -533,6 +533,8 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
   if (precision == WADG_FP32_3XBF16 && m->N > 4)
     return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 4");
   if (shots < 1 || shots > (1 << 20)) return fail(m, WADG_EINVAL, "shots=%d", shots);
+  if (precision == WADG_FP32_3XBF16 && (int64_t)m->K * shots * m->ref.Np >= ((int64_t)1 << 31))
+    return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage needs K * shots * Np < 2^31 (31-bit gather offsets)");
   if (!(tau_p >= 0) || !(tau_u >= 0)) return fail(m, WADG_EINVAL, "penalties must be >= 0");
   DeviceGuard g(m->device);
   const int64_t K = m->K;

@@ -71,7 +71,9 @@ struct TcDims {
   static constexpr int SZ_GI = (4 * 6 * NP * 2 + 15) / 16 * 16;
   static constexpr int OFF_GX = OFF_GI + SZ_GI;
   static constexpr int SZ_GX = (4 * 6 * NFP * 2 + 15) / 16 * 16;
-  static constexpr int OFF_BAR = OFF_GX + SZ_GX;
+  // per tile column: offset of each face's neighbour column (4 x uint32, top bit: boundary), face codes
+  static constexpr int OFF_NB = OFF_GX + SZ_GX;
+  static constexpr int OFF_BAR = OFF_NB + TILE * 20;
   static constexpr int SMEM = OFF_BAR + 128;
   // TMEM columns
   static constexpr int T1 = 96;                    // chunk outputs, two buffers at 0 and T1
@@ -85,7 +87,8 @@ struct TcDims {
 namespace {
 
 constexpr uint32_t kWaitIters = 1u << 22;
-constexpr uint32_t kIssuers = 8;  // threads issuing tensor-core products (lane 0 of each warp)
+constexpr int kThreads = 512;      // four threads per column of a 128-column tile
+constexpr uint32_t kIssuers = 16;  // threads issuing tensor-core products (lane 0 of each warp)
 
 // Cooperative copy of `bytes` (multiple of 16) from global to shared memory.
 __device__ __forceinline__ void stage_copy(uint8_t* dst, const uint8_t* __restrict__ src, int bytes) {
@@ -125,7 +128,7 @@ __device__ __forceinline__ void mma3_chain(const Mma3& g) {
 }  // namespace
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P) {
+__global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStageParams P) {
   using T = TcDims<N>;
   constexpr int NP = T::NP, NQ = T::NQ, NFP = T::NFP, NFQ = T::NFQ, KP = T::KP, QC = T::QC, NPS = T::NPS;
   constexpr int TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16, NCH = T::NCH;
@@ -142,14 +145,18 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
   uint8_t* sFT = smem + T::OFF_FT;                            // face B operands
   int16_t* sGI = reinterpret_cast<int16_t*>(smem + T::OFF_GI);  // ginv [4][6][NP]
   int16_t* sGX = reinterpret_cast<int16_t*>(smem + T::OFF_GX);  // gidx [4][6][NFP]
+  uint4* sNB = reinterpret_cast<uint4*>(smem + T::OFF_NB);                     // [128] neighbour offsets
+  uint32_t* sC4 = reinterpret_cast<uint32_t*>(smem + T::OFF_NB + TILE * 16);   // [128] face codes
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + T::OFF_BAR);
   // bars: 0-3 operator slots, 4-5 first products of a chunk, 6 second products, 7 faces, 8 drain
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + T::OFF_BAR + 80);
   int* sflag = reinterpret_cast<int*>(smem + T::OFF_BAR + 84);
 
+  // Four threads per column: warps w, w + 4, w + 8, w + 12 share the TMEM lanes
+  // of quarter w; the group g = w / 4 takes field g, or a quarter of the points.
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, half = warp >> 2;
-  const bool issuer = lane == 0;  // lane 0 of every warp issues one accumulator chain per product group
+  const int quarter = warp & 3, grp = warp >> 2;
+  const bool issuer = lane == 0;  // lane 0 of every warp issues at most one accumulator chain per step
   const int mrow = quarter * 32 + lane;  // this thread's column within the tile (TMEM lane)
   const int64_t ncols = p.ncols;
   const int64_t fs = ncols * NP;
@@ -162,8 +169,8 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), 512);
   stage_copy(sFT, P.ops + (size_t)NCH * (T::SZ_OPV + T::SZ_OPU), T::SZ_FOPS);
-  for (int i = tid; i < 4 * 6 * NP; i += 256) sGI[i] = ops.ginv[i];
-  for (int i = tid; i < 4 * 6 * NFP; i += 256) sGX[i] = ops.gidx[i];
+  for (int i = tid; i < 4 * 6 * NP; i += kThreads) sGI[i] = ops.ginv[i];
+  for (int i = tid; i < 4 * 6 * NFP; i += kThreads) sGX[i] = ops.gidx[i];
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -214,11 +221,13 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
     tc::fence_after();
     failed = *(volatile int*)sflag != 0;
   };
-  // volume products of chunk c
-  // volume and update products of chunk c, accumulator chain i of each group
-  auto issue_V = [&](int c, int i) {  // u_i = V_q u_i (N = 16 each), dp/dx^_a = V_q^a p (N = 48)
+  // Products of chunk c, one accumulator chain per issuing warp w: the V and
+  // U1 chains (9 instructions each at N = 4) on warps 8-11, the DW and U2
+  // chains (3 each) on warps 0-5.
+  auto issue_V = [&](int c, int w) {  // u_i = V_q u_i (N = 16 each), dp/dx^_a = V_q^a p (N = 48)
     const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1);
-    if (i < 3)
+    const int i = w - 8;
+    if (i >= 0 && i < 3)
       mma3_chain<KP / 16>(mk_mma3(d + 16 * i, aq + (2 * (1 + i)) * T::A_FIELD, aq + (2 * (1 + i) + 1) * T::A_FIELD,
                                   sbo_KP, sl, sl + T::B_V, sbo_KP, tc::idesc_bf16(128, 16), false));
     else if (i == 3)
@@ -237,9 +246,10 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
       mma3_chain<1>(mk_mma3(tmem + T::TB + KP * (i - 2), ax + (2 * i) * T::A_CH, ax + (2 * i + 1) * T::A_CH, sbo_16,
                             bvw, bvw + T::B_P, sbo_16, tc::idesc_bf16(128, KP), true));
   };
-  auto issue_U1 = [&](int c, int f) {  // (V_q M^^{-1}) b per field (N = 16)
+  auto issue_U1 = [&](int c, int w) {  // (V_q M^^{-1}) b per field (N = 16)
     const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1);
-    if (f < 4)
+    const int f = w - 8;
+    if (f >= 0 && f < 4)
       mma3_chain<KP / 16>(mk_mma3(d + 16 * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP, sl,
                                   sl + T::B_V, sbo_KP, tc::idesc_bf16(128, 16), false));
   };
@@ -259,14 +269,21 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
     cm = cm < ncols ? cm : ncols - 1;
     const int64_t km = cm / S;
     const int sh = (int)(cm - km * S);
-    const int4 nbr4 = __ldg(reinterpret_cast<const int4*>(p.EToE) + km);
     const uint32_t code4 = __ldg(reinterpret_cast<const unsigned int*>(p.fcode) + km);
+    if (grp == 0) {  // per column: the face codes and each face's neighbour column
+      const int4 e4 = __ldg(reinterpret_cast<const int4*>(p.EToE) + km);
+      auto nbo = [&](int kn) {  // element offset of the neighbour column; own column (top bit set) on the boundary
+        return kn >= 0 ? (uint32_t)(((int64_t)kn * S + sh) * NP) : ((uint32_t)(cm * NP) | 0x80000000u);
+      };
+      sNB[mrow] = make_uint4(nbo(e4.x), nbo(e4.y), nbo(e4.z), nbo(e4.w));
+      sC4[mrow] = code4;
+    }
 
     // ---- fields -> FP32 tile in shared memory (coalesced) ----
     {
       const int nval = ncol_t * NP;
-#pragma unroll 10
-      for (int i = tid; i < 4 * TILE * NP; i += 256) {
+#pragma unroll 5
+      for (int i = tid; i < 4 * TILE * NP; i += kThreads) {
         const int f = i / (TILE * NP), r = i - f * (TILE * NP);
         const int c = r / NP, n = r - c * NP;
         sQS[(f * TILE + c) * NPS + n] = r < nval ? __ldg(p.Qin + f * fs + col0 * NP + r) : 0.f;
@@ -275,70 +292,68 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
     __syncthreads();
 
     // ---- surface terms (Sec. 4.1, Sec. 6.4), face by face; the lifted terms
-    // are gathered into registers at this thread's volume nodes ----
-    float bS[2][NP];
-#pragma unroll
-    for (int fi = 0; fi < 2; ++fi)
-#pragma unroll
-      for (int n = 0; n < NP; ++n) bS[fi][n] = 0.f;
-
+    // are gathered at this thread's volume nodes and summed in the b
+    // accumulators in TMEM ----
     for (int f = 0; f < 4 && !failed; ++f) {
-      const int code = (int)((code4 >> (8 * f)) & 0xffu);
-      const int pio = code % 6, pin = (code / 6) % 6, fn = code / 36;
-      // normals x surface Jacobian at this thread's face points, needed after the first products
-      constexpr int QH = NFQ16 / 2;
-      float nv[3][QH];
+      const int pio = (int)((code4 >> (8 * f)) & 0xffu) % 6;
+      // normals x surface Jacobian at this thread's face points (8 per group), needed after the first products
+      const int q0 = 8 * grp;
+      float nv[3][8];
       {
         const float* nfg = P.fgeo_il + ((km >> 7) * 12 * NFQ + f * NFQ) * 128 + (km & 127);
 #pragma unroll
-        for (int qq = 0; qq < QH; ++qq) {
-          const int q = half * QH + qq;
+        for (int qq = 0; qq < 8; ++qq) {
+          const int q = q0 + qq;
 #pragma unroll
           for (int dd = 0; dd < 3; ++dd) nv[dd][qq] = q < NFQ ? __ldg(nfg + (size_t)(dd * 4 * NFQ + q) * 128) : 0.f;
         }
       }
-      // (i) [p], {u}, [u] at the face nodes, owner's node order -> split A operands
+      // (i) [p], {u}, [u] at the face nodes, owner's node order -> split A
+      // operands.  Sixteen lanes take the face nodes j of one column, so that
+      // the neighbour's values come from a few sectors of its row.
       {
-        const int64_t kn = f == 0 ? nbr4.x : f == 1 ? nbr4.y : f == 2 ? nbr4.z : nbr4.w;
-        const int16_t* go = sGX + (f * 6 + pio) * NFP;
-        const int16_t* gn = sGX + (fn * 6 + pin) * NFP;
-        const int64_t nb = kn >= 0 ? (kn * S + sh) * NP : 0;
-        // all neighbour loads first, from clamped (always valid) addresses
-        const int64_t nbv = kn >= 0 ? nb : cm * NP;
-        float qp[4][8], qm[4][8];
+        float qp[4][4], qm[4][4];
+        bool bnd[4];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int j = half * 8 + jj < NFP ? half * 8 + jj : 0;
-          const int64_t b = nbv + gn[j];
+        for (int it = 0; it < 4; ++it) {
+          const int r = it * 32 + (tid >> 4), j = tid & 15;
+          const uint32_t cd = (sC4[r] >> (8 * f)) & 0xffu;
+          const int po = (int)(cd % 6), pn = (int)((cd / 6) % 6), fnb = (int)(cd / 36);
+          const uint4 o4 = sNB[r];
+          const uint32_t nbo = f == 0 ? o4.x : f == 1 ? o4.y : f == 2 ? o4.z : o4.w;
+          const int jj = j < NFP ? j : 0;
+          const int64_t b = (int64_t)(nbo & 0x7fffffffu) + sGX[(fnb * 6 + pn) * NFP + jj];
+          const int o = sGX[(f * 6 + po) * NFP + jj];
+          bnd[it] = (nbo & 0x80000000u) != 0;
 #pragma unroll
-          for (int fl = 0; fl < 4; ++fl) qp[fl][jj] = __ldg(p.Qin + fl * fs + b);
-        }
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int j = half * 8 + jj < NFP ? half * 8 + jj : 0;
-          const int o = go[j];
-#pragma unroll
-          for (int fl = 0; fl < 4; ++fl) qm[fl][jj] = sQS[(fl * TILE + mrow) * NPS + o];
-        }
-        float cv[7][8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const bool on = half * 8 + jj < NFP;
-          // Dirichlet ghost state on the boundary (Sec. 4.1): p+ = -p-, u+ = u-
-          const float pp = kn >= 0 ? qp[0][jj] : -qm[0][jj];
-          float up[3];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) up[i] = kn >= 0 ? qp[1 + i][jj] : qm[1 + i][jj];
-          cv[0][jj] = on ? pp - qm[0][jj] : 0.f;
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            cv[1 + i][jj] = on ? 0.5f * (up[i] + qm[1 + i][jj]) : 0.f;
-            cv[4 + i][jj] = on ? up[i] - qm[1 + i][jj] : 0.f;
+          for (int fl = 0; fl < 4; ++fl) {
+            qp[it][fl] = __ldg(p.Qin + fl * fs + b);
+            qm[it][fl] = sQS[(fl * TILE + r) * NPS + o];
           }
         }
-        const uint32_t off = tc::kmajor_offset(mrow, 8 * half, NFP16);
 #pragma unroll
-        for (int c = 0; c < 7; ++c) tc::split_store8(sFA + (2 * c) * T::A_FN + off, sFA + (2 * c + 1) * T::A_FN + off, cv[c]);
+        for (int it = 0; it < 4; ++it) {
+          const int r = it * 32 + (tid >> 4), j = tid & 15;
+          const bool on = j < NFP;
+          // Dirichlet ghost state on the boundary (Sec. 4.1): p+ = -p-, u+ = u-
+          const float pp = bnd[it] ? -qm[it][0] : qp[it][0];
+          float cv[7];
+          cv[0] = on ? pp - qm[it][0] : 0.f;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const float up = bnd[it] ? qm[it][1 + i] : qp[it][1 + i];
+            cv[1 + i] = on ? 0.5f * (up + qm[it][1 + i]) : 0.f;
+            cv[4 + i] = on ? up - qm[it][1 + i] : 0.f;
+          }
+          const uint32_t off = tc::kmajor_offset(r, j, NFP16);
+#pragma unroll
+          for (int c = 0; c < 7; ++c) {
+            __nv_bfloat16 h, l;
+            tc::split_bf16(cv[c], h, l);
+            *reinterpret_cast<__nv_bfloat16*>(sFA + (2 * c) * T::A_FN + off) = h;
+            *reinterpret_cast<__nv_bfloat16*>(sFA + (2 * c + 1) * T::A_FN + off) = l;
+          }
+        }
       }
       sync_check();
       if (failed) break;
@@ -352,110 +367,111 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
       wait_all(7, par_f);
       par_f ^= 1u;
       // (ii) strong-weak flux (Sec. 4.1) at this thread's face points -> split A operands
+      if (q0 < NFQ16) {
 #pragma unroll
-      for (int b8 = 0; b8 < QH; b8 += 8) {
-        const int q0 = half * QH + b8;
-        uint32_t v[7][8];
+        for (int b4 = 0; b4 < 8; b4 += 4) {
+          uint32_t v[7][4];
 #pragma unroll
-        for (int c = 0; c < 7; ++c) tc::tmem_ld8_nw(lane_base + T::TI + c * NFQ16 + q0, v[c]);
-        tc::wait_ld();
+          for (int c = 0; c < 7; ++c) tc::tmem_ld4_nw(lane_base + T::TI + c * NFQ16 + q0 + b4, v[c]);
+          tc::wait_ld();
 #pragma unroll
-        for (int c = 0; c < 7; ++c) tc::pin8(v[c]);
-        float F[4][8];
+          for (int c = 0; c < 7; ++c) tc::pin4(v[c]);
+          float F[4][4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float nx = nv[0][b8 + j], ny = nv[1][b8 + j], nz = nv[2][b8 + j];
-          const float jp = __uint_as_float(v[0][j]);
-          F[0][j] = F[1][j] = F[2][j] = F[3][j] = 0.f;
-          if (q0 + j < NFQ) {
-            const float nn = nx * nx + ny * ny + nz * nz;
-            const float rJ = rsqrtf(nn);  // 1 / J^f (|n J^f| = J^f)
-            const float Jf = nn * rJ;
-            const float aun = __uint_as_float(v[1][j]) * nx + __uint_as_float(v[2][j]) * ny +
-                              __uint_as_float(v[3][j]) * nz;
-            const float jun = (__uint_as_float(v[4][j]) * nx + __uint_as_float(v[5][j]) * ny +
-                               __uint_as_float(v[6][j]) * nz) *
-                              rJ;
-            F[0][j] = -aun + 0.5f * p.tau_p * jp * Jf;
-            const float sc = -0.5f * (jp - p.tau_u * jun);
-            F[1][j] = sc * nx;
-            F[2][j] = sc * ny;
-            F[3][j] = sc * nz;
+          for (int j = 0; j < 4; ++j) {
+            const float nx = nv[0][b4 + j], ny = nv[1][b4 + j], nz = nv[2][b4 + j];
+            const float jp = __uint_as_float(v[0][j]);
+            F[0][j] = F[1][j] = F[2][j] = F[3][j] = 0.f;
+            if (q0 + b4 + j < NFQ) {
+              const float nn = nx * nx + ny * ny + nz * nz;
+              const float rJ = rsqrtf(nn);  // 1 / J^f (|n J^f| = J^f)
+              const float Jf = nn * rJ;
+              const float aun = __uint_as_float(v[1][j]) * nx + __uint_as_float(v[2][j]) * ny +
+                                __uint_as_float(v[3][j]) * nz;
+              const float jun = (__uint_as_float(v[4][j]) * nx + __uint_as_float(v[5][j]) * ny +
+                                 __uint_as_float(v[6][j]) * nz) *
+                                rJ;
+              F[0][j] = -aun + 0.5f * p.tau_p * jp * Jf;
+              const float sc = -0.5f * (jp - p.tau_u * jun);
+              F[1][j] = sc * nx;
+              F[2][j] = sc * ny;
+              F[3][j] = sc * nz;
+            }
           }
-        }
-        const uint32_t off = tc::kmajor_offset(mrow, q0, NFQ16);
+          const uint32_t off = tc::kmajor_offset(mrow, q0 + b4, NFQ16);
 #pragma unroll
-        for (int fld = 0; fld < 4; ++fld)
-          tc::split_store8(sFA + (2 * fld) * T::A_FQ + off, sFA + (2 * fld + 1) * T::A_FQ + off, F[fld]);
+          for (int fld = 0; fld < 4; ++fld)
+            tc::split_store4(sFA + (2 * fld) * T::A_FQ + off, sFA + (2 * fld + 1) * T::A_FQ + off, F[fld]);
+        }
       }
       sync_check();
       if (failed) break;
       if (issuer) {
         const uint32_t bl = ft + 2 * T::B_TRI;
-        if (warp < 4)
-          mma3_chain<NFQ16 / 16>(mk_mma3(tmem + T::TL + warp * NFP16, fa + (2 * warp) * T::A_FQ,
-                                         fa + (2 * warp + 1) * T::A_FQ, (NFQ16 / 8) * 128, bl, bl + T::B_TRI,
+        const int fld = warp - 8;
+        if (fld >= 0 && fld < 4)
+          mma3_chain<NFQ16 / 16>(mk_mma3(tmem + T::TL + fld * NFP16, fa + (2 * fld) * T::A_FQ,
+                                         fa + (2 * fld + 1) * T::A_FQ, (NFQ16 / 8) * 128, bl, bl + T::B_TRI,
                                          (NFQ16 / 8) * 128, tc::idesc_bf16(128, NFP16), false));
         tc::commit(bar(7));
       }
       wait_all(7, par_f);
       par_f ^= 1u;
-      // (iii) lifted values (owner's node order) -> this thread's scratch -> volume nodes
+      // (iii) lifted values of field grp (owner's node order) -> this thread's scratch -> volume nodes
       {
-        uint32_t L[2][NFP16 / 8][8];
+        uint32_t L[NFP16 / 8][8];
 #pragma unroll
-        for (int fi = 0; fi < 2; ++fi)
-#pragma unroll
-          for (int j8 = 0; j8 < NFP16 / 8; ++j8)
-            tc::tmem_ld8_nw(lane_base + T::TL + (2 * half + fi) * NFP16 + 8 * j8, L[fi][j8]);
+        for (int j8 = 0; j8 < NFP16 / 8; ++j8) tc::tmem_ld8_nw(lane_base + T::TL + grp * NFP16 + 8 * j8, L[j8]);
         tc::wait_ld();
 #pragma unroll
-        for (int fi = 0; fi < 2; ++fi)
+        for (int j8 = 0; j8 < NFP16 / 8; ++j8) tc::pin8(L[j8]);
 #pragma unroll
-          for (int j8 = 0; j8 < NFP16 / 8; ++j8) tc::pin8(L[fi][j8]);
-#pragma unroll
-        for (int fi = 0; fi < 2; ++fi)
-#pragma unroll
-          for (int j = 0; j < NFP; ++j)
-            sLS[((2 * half + fi) * NFP16 + j) * TILE + mrow] = __uint_as_float(L[fi][j >> 3][j & 7]);
+        for (int j = 0; j < NFP; ++j) sLS[(grp * NFP16 + j) * TILE + mrow] = __uint_as_float(L[j >> 3][j & 7]);
+        // add to this field's b accumulator (the first face initialises it)
         const int16_t* gi = sGI + (f * 6 + pio) * NP;
+        const uint32_t tb = lane_base + T::TB + KP * grp;
+        uint32_t acc[KP / 8][8];
+        if (f > 0) {
+#pragma unroll
+          for (int n8 = 0; n8 < KP / 8; ++n8) tc::tmem_ld8_nw(tb + 8 * n8, acc[n8]);
+          tc::wait_ld();
+#pragma unroll
+          for (int n8 = 0; n8 < KP / 8; ++n8) tc::pin8(acc[n8]);
+        } else {
+#pragma unroll
+          for (int n8 = 0; n8 < KP / 8; ++n8)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[n8][j] = 0u;
+        }
 #pragma unroll
         for (int n = 0; n < NP; ++n) {
           const int jj = gi[n];
-          if (jj >= 0) {
-#pragma unroll
-            for (int fi = 0; fi < 2; ++fi) bS[fi][n] += sLS[((2 * half + fi) * NFP16 + jj) * TILE + mrow];
-          }
+          if (jj >= 0)
+            acc[n >> 3][n & 7] =
+                __float_as_uint(__uint_as_float(acc[n >> 3][n & 7]) + sLS[(grp * NFP16 + jj) * TILE + mrow]);
         }
+#pragma unroll
+        for (int n8 = 0; n8 < KP / 8; ++n8) {
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(acc[n8][j]);
+          tc::tmem_st8(tb + 8 * n8, v);
+        }
+        tc::wait_st();
       }
     }
     if (failed) break;
 
-    // ---- surface (+ point source) -> b accumulators in TMEM; fields -> split A
-    // operands (over the lifted-value scratch: every thread has finished with it) ----
+    // ---- field grp -> split A operand (over the lifted-value scratch: every
+    // thread has finished with it) ----
     __syncthreads();
-    {
-      if (half == 0 && p.src_elem != nullptr && p.src_elem[sh] == (int32_t)km) {
 #pragma unroll
-        for (int n = 0; n < NP; ++n) bS[0][n] += p.src_amp * p.src_vec[sh * NP + n];
-      }
+    for (int n0 = 0; n0 < KP; n0 += 8) {
+      float x[8];
 #pragma unroll
-      for (int fi = 0; fi < 2; ++fi) {
-        const int f = 2 * half + fi;
-#pragma unroll
-        for (int n0 = 0; n0 < KP; n0 += 8) {
-          float v[8], x[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            v[j] = n0 + j < NP ? bS[fi][n0 + j] : 0.f;
-            x[j] = n0 + j < NP ? sQS[(f * TILE + mrow) * NPS + n0 + j] : 0.f;
-          }
-          tc::tmem_st8(lane_base + T::TB + KP * f + n0, v);
-          const uint32_t off = tc::kmajor_offset(mrow, n0, KP);
-          tc::split_store8(sAQ + (2 * f) * T::A_FIELD + off, sAQ + (2 * f + 1) * T::A_FIELD + off, x);
-        }
-      }
-      tc::wait_st();
+      for (int j = 0; j < 8; ++j) x[j] = n0 + j < NP ? sQS[(grp * TILE + mrow) * NPS + n0 + j] : 0.f;
+      const uint32_t off = tc::kmajor_offset(mrow, n0, KP);
+      tc::split_store8(sAQ + (2 * grp) * T::A_FIELD + off, sAQ + (2 * grp + 1) * T::A_FIELD + off, x);
     }
     sync_check();
     if (failed) break;
@@ -476,12 +492,13 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
       }
     }
     for (int c = 0; c < NCH; ++c) {
-      float G[9][8];
+      // geometric factors at this thread's 4 quadrature points
+      float G[9][4];
       {
         const float* gk = P.vgeo_il + (km >> 7) * 11 * NQ * 128 + (km & 127);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int q = c * QC + 8 * half + j;
+        for (int j = 0; j < 4; ++j) {
+          const int q = c * QC + 4 * grp + j;
 #pragma unroll
           for (int k = 0; k < 9; ++k) G[k][j] = q < NQ ? __ldg(gk + (size_t)(k * NQ + q) * 128) : 0.f;
         }
@@ -489,23 +506,23 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
       wait_all(4 + (c & 1), (par_t1 >> (c & 1)) & 1u);
       par_t1 ^= 1u << (c & 1);
       if (tid == 0 && c + 2 < NCH) load_slot(c & 1, vol_ops + (size_t)(c + 2) * T::SZ_OPV, T::SZ_VA);
-      float U[3][8], g[3][8];
+      float U[3][4], g[3][4];
       {
-        const uint32_t t = lane_base + (uint32_t)((c & 1) * T::T1) + 8 * half;
-        uint32_t u[3][8], d[3][8];
+        const uint32_t t = lane_base + (uint32_t)((c & 1) * T::T1) + 4 * grp;
+        uint32_t u[3][4], d[3][4];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          tc::tmem_ld8_nw(t + 16 * i, u[i]);
-          tc::tmem_ld8_nw(t + 48 + 16 * i, d[i]);
+          tc::tmem_ld4_nw(t + 16 * i, u[i]);
+          tc::tmem_ld4_nw(t + 48 + 16 * i, d[i]);
         }
         tc::wait_ld();
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          tc::pin8(u[i]);
-          tc::pin8(d[i]);
+          tc::pin4(u[i]);
+          tc::pin4(d[i]);
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 4; ++j) {
           const float u0 = __uint_as_float(u[0][j]), u1 = __uint_as_float(u[1][j]), u2 = __uint_as_float(u[2][j]);
           const float d0 = __uint_as_float(d[0][j]), d1 = __uint_as_float(d[1][j]), d2 = __uint_as_float(d[2][j]);
 #pragma unroll
@@ -521,11 +538,11 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
           load_slot(2 + ((c + 1) & 1), vol_ops + (size_t)(c + 1) * T::SZ_OPV + T::SZ_VA, T::SZ_VB);
       }
       {
-        const uint32_t off = tc::kmajor_offset(mrow, 8 * half, QC);
+        const uint32_t off = tc::kmajor_offset(mrow, 4 * grp, QC);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          tc::split_store8(sAX + (2 * a) * T::A_CH + off, sAX + (2 * a + 1) * T::A_CH + off, U[a]);
-          tc::split_store8(sAX + (2 * (3 + a)) * T::A_CH + off, sAX + (2 * (3 + a) + 1) * T::A_CH + off, g[a]);
+          tc::split_store4(sAX + (2 * a) * T::A_CH + off, sAX + (2 * a + 1) * T::A_CH + off, U[a]);
+          tc::split_store4(sAX + (2 * (3 + a)) * T::A_CH + off, sAX + (2 * (3 + a) + 1) * T::A_CH + off, g[a]);
         }
       }
       sync_check();
@@ -555,33 +572,29 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
       }
     }
 
-    // ---- b -> split A operand ----
-#pragma unroll
-    for (int fi = 0; fi < 2; ++fi) {
-      const int f = 2 * half + fi;
+    // ---- b of field grp (+ point source, Sec. 4.1 load vector) -> split A operand ----
+    {
+      const bool src = grp == 0 && p.src_elem != nullptr && p.src_elem[sh] == (int32_t)km;
 #pragma unroll
       for (int n0 = 0; n0 < KP; n0 += 8) {
         uint32_t v[8], v1[8], v2[8];
-        tc::tmem_ld8_nw(lane_base + T::TB + KP * f + n0, v);
-        if (f == 0) {  // b_p = sum over the three derivative directions
-          tc::tmem_ld8_nw(lane_base + T::TBX + n0, v1);
-          tc::tmem_ld8_nw(lane_base + T::TBX + KP + n0, v2);
-        }
+        tc::tmem_ld8_nw(lane_base + T::TB + KP * grp + n0, v);
+        tc::tmem_ld8_nw(lane_base + T::TBX + n0, v1);
+        tc::tmem_ld8_nw(lane_base + T::TBX + KP + n0, v2);
         tc::wait_ld();
         tc::pin8(v);
+        tc::pin8(v1);
+        tc::pin8(v2);
         float x[8];
-        if (f == 0) {
-          tc::pin8(v1);
-          tc::pin8(v2);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            x[j] = n0 + j < NP ? __uint_as_float(v[j]) + __uint_as_float(v1[j]) + __uint_as_float(v2[j]) : 0.f;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) x[j] = n0 + j < NP ? __uint_as_float(v[j]) : 0.f;
+        for (int j = 0; j < 8; ++j) {
+          // b_p = sum over the three derivative directions
+          float b = __uint_as_float(v[j]);
+          if (grp == 0) b += __uint_as_float(v1[j]) + __uint_as_float(v2[j]) + (src ? p.src_amp * p.src_vec[sh * NP + n0 + j] : 0.f);
+          x[j] = n0 + j < NP ? b : 0.f;
         }
         const uint32_t off = tc::kmajor_offset(mrow, n0, KP);
-        tc::split_store8(sAQ + (2 * f) * T::A_FIELD + off, sAQ + (2 * f + 1) * T::A_FIELD + off, x);
+        tc::split_store8(sAQ + (2 * grp) * T::A_FIELD + off, sAQ + (2 * grp + 1) * T::A_FIELD + off, x);
       }
     }
     sync_check();
@@ -601,37 +614,32 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
       }
     }
     for (int c = 0; c < NCH; ++c) {
-      float wt[2][16];
-#pragma unroll
-      for (int fi = 0; fi < 2; ++fi) {
-        const int f = 2 * half + fi;
-        const float* w = P.vgeo_il + ((km >> 7) * 11 + (f == 0 ? 9 : 10)) * NQ * 128 + (km & 127);
+      // weights of field grp (c^2/J for p, 1/J for u) at the 16 points of the chunk
+      float wt[16];
+      {
+        const float* w = P.vgeo_il + ((km >> 7) * 11 + (grp == 0 ? 9 : 10)) * NQ * 128 + (km & 127);
 #pragma unroll
         for (int ql = 0; ql < 16; ++ql) {
           const int q = c * QC + ql;
-          wt[fi][ql] = q < NQ ? __ldg(w + (size_t)q * 128) : 0.f;
+          wt[ql] = q < NQ ? __ldg(w + (size_t)q * 128) : 0.f;
         }
       }
       wait_all(4 + (c & 1), (par_t1 >> (c & 1)) & 1u);
       par_t1 ^= 1u << (c & 1);
       if (tid == 0 && c + 2 < NCH) load_slot(c & 1, upd_ops + (size_t)(c + 2) * T::SZ_OPU, T::SZ_UA);
-      float x[2][16];
+      float x[2][8];
       {
-        const uint32_t t = lane_base + (uint32_t)((c & 1) * T::T1);
-        uint32_t v[2][2][8];
-#pragma unroll
-        for (int fi = 0; fi < 2; ++fi) {
-          tc::tmem_ld8_nw(t + 16 * (2 * half + fi), v[fi][0]);
-          tc::tmem_ld8_nw(t + 16 * (2 * half + fi) + 8, v[fi][1]);
-        }
+        const uint32_t t = lane_base + (uint32_t)((c & 1) * T::T1) + 16 * grp;
+        uint32_t v[2][8];
+        tc::tmem_ld8_nw(t, v[0]);
+        tc::tmem_ld8_nw(t + 8, v[1]);
         tc::wait_ld();
+        tc::pin8(v[0]);
+        tc::pin8(v[1]);
 #pragma unroll
-        for (int fi = 0; fi < 2; ++fi) {
-          tc::pin8(v[fi][0]);
-          tc::pin8(v[fi][1]);
+        for (int h8 = 0; h8 < 2; ++h8)
 #pragma unroll
-          for (int ql = 0; ql < 16; ++ql) x[fi][ql] = __uint_as_float(v[fi][ql >> 3][ql & 7]) * wt[fi][ql];
-        }
+          for (int j = 0; j < 8; ++j) x[h8][j] = __uint_as_float(v[h8][j]) * wt[8 * h8 + j];
       }
       if (c > 0) {
         wait_all(6, par_m2);
@@ -640,16 +648,9 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
           load_slot(2 + ((c + 1) & 1), upd_ops + (size_t)(c + 1) * T::SZ_OPU + T::SZ_UA, T::SZ_UB);
       }
 #pragma unroll
-      for (int fi = 0; fi < 2; ++fi) {
-        const int f = 2 * half + fi;
-#pragma unroll
-        for (int h8 = 0; h8 < 2; ++h8) {
-          const uint32_t off = tc::kmajor_offset(mrow, 8 * h8, QC);
-          float y[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) y[j] = x[fi][8 * h8 + j];
-          tc::split_store8(sAX + (2 * f) * T::A_CH + off, sAX + (2 * f + 1) * T::A_CH + off, y);
-        }
+      for (int h8 = 0; h8 < 2; ++h8) {
+        const uint32_t off = tc::kmajor_offset(mrow, 8 * h8, QC);
+        tc::split_store8(sAX + (2 * grp) * T::A_CH + off, sAX + (2 * grp + 1) * T::A_CH + off, x[h8]);
       }
       sync_check();
       if (failed) break;
@@ -673,24 +674,20 @@ __global__ void __launch_bounds__(256, 1) stage_tc_kernel(const TcStageParams P)
 
     // ---- epilogue: r -> FP32 tile -> coalesced dQ/dt, or the LSRK update (Sec. 5.2) ----
 #pragma unroll
-    for (int fi = 0; fi < 2; ++fi) {
-      const int f = 2 * half + fi;
+    for (int n0 = 0; n0 < KP; n0 += 8) {
+      uint32_t v[8];
+      tc::tmem_ld8_nw(lane_base + T::TB + KP * grp + n0, v);
+      tc::wait_ld();
+      tc::pin8(v);
 #pragma unroll
-      for (int n0 = 0; n0 < KP; n0 += 8) {
-        uint32_t v[8];
-        tc::tmem_ld8_nw(lane_base + T::TB + KP * f + n0, v);
-        tc::wait_ld();
-        tc::pin8(v);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (n0 + j < NP) sTT[(f * TILE + mrow) * NPS + n0 + j] = __uint_as_float(v[j]);
-      }
+      for (int j = 0; j < 8; ++j)
+        if (n0 + j < NP) sTT[(grp * TILE + mrow) * NPS + n0 + j] = __uint_as_float(v[j]);
     }
     sync_check();
     {
       const int nval = ncol_t * NP;
 #pragma unroll 4
-      for (int i = tid; i < 4 * TILE * NP; i += 256) {
+      for (int i = tid; i < 4 * TILE * NP; i += kThreads) {
         const int f = i / (TILE * NP), r = i - f * (TILE * NP);
         if (r >= nval) continue;
         const int c = r / NP, n = r - c * NP;
@@ -749,12 +746,12 @@ cudaError_t launch_stage_tc_n(const TcStageParams& P, int mode, int grid, cudaSt
     auto kern = stage_tc_kernel<N, kRhs>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
     if (e != cudaSuccess) return e;
-    kern<<<g, 256, T::SMEM, stream>>>(P);
+    kern<<<g, kThreads, T::SMEM, stream>>>(P);
   } else {
     auto kern = stage_tc_kernel<N, kLsrk>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
     if (e != cudaSuccess) return e;
-    kern<<<g, 256, T::SMEM, stream>>>(P);
+    kern<<<g, kThreads, T::SMEM, stream>>>(P);
   }
   return cudaGetLastError();
 }
