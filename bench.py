@@ -8,10 +8,12 @@ time step = 5 fused stage launches (strong-weak volume + surface terms,
 weight-adjusted update, Runge-Kutta update).  DOF = 4 K Np S scalar unknowns;
 value = DOF * stages / second.
 
-The headline line is the FP32 path; the FP64 path is measured on the same
-mesh, data and dt and reported under "variants".  Inputs (1.1 GB of FP32
-geometric factors alone) are larger than the 129 MB L2, so no flush is
-needed between iterations.
+The headline line is the mixed-precision path (FP32 fields, the dense
+products on the tensor cores with split bf16 operands); the plain FP64 path
+and the FP32 CUDA-core path are measured on the same mesh, data and dt and
+reported under "variants", and "accuracy" gives the L2 error of each against
+the analytic solution.  Inputs (1.1 GB of FP32 geometric factors alone) are
+larger than the 129 MB L2, so no flush is needed between iterations.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -55,6 +57,38 @@ def peaks():
         return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
     except Exception:
         return 6800.0, "fallback", 2070.0
+
+
+TC_SOURCES = ("paper_1608_03836_gb300/csrc/stage_tc.cu", "paper_1608_03836_gb300/csrc/tc_ops.cuh")
+TC_PROFILE = "profiles/stage_tc_kernel_n20_full.md"
+
+
+def tc_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def tc_traffic_per_element():
+    """DRAM bytes per element and launch of the tensor-core stage from the
+    committed ncu summary (lines 'source_hash: ...' and
+    'dram_bytes_per_element: ...'), or None when the kernel source has changed
+    since the capture."""
+    try:
+        vals = {}
+        with open(os.path.join(ROOT, TC_PROFILE)) as f:
+            for ln in f:
+                if ":" in ln and ln.split(":")[0].strip() in ("source_hash", "dram_bytes_per_element"):
+                    k, v = ln.split(":", 1)
+                    vals[k.strip()] = v.strip().strip("`")
+        if vals.get("source_hash") != tc_source_hash():
+            return None
+        return float(vals["dram_bytes_per_element"])
+    except Exception:
+        return None
 
 
 class ClockSampler:
@@ -380,7 +414,6 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
@@ -404,7 +437,8 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    m, Q = build_case(W, "fp32", rank)
+    headline = "fp32_3xbf16"
+    m, Q = build_case(W, headline, rank)
     Np, K = m.Np, m.K
     dof = 4 * K * Np
     barrier()
@@ -412,21 +446,33 @@ def main():
     with ClockSampler(local) as clk:
         total_ms, stage_ms = time_steps(W, m, Q, args.steps, args.warmup)
     barrier()
+    W.wadg_device_status(m)
     total_ms = max_over_ranks(total_ms, ws)
     ms_per_step = total_ms / args.steps
     value = job_value(dof, 5, ms_per_step, ws)
     e2e_ms, nbytes = e2e_steps(W, m, Q, max(2, args.steps // 2))
     e2e_value = ws * dof * 5 / (e2e_ms * 1e-3)
-
     hbm, peak_kind, sm_max = peaks()
     B, F = algorithmic(WORKLOAD["N"], 1, 4)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, CUDA-core FMA
-    achieved_tf = F * K / (stage_ms * 1e-3) / 1e12
     achieved_gbs = B * K / (stage_ms * 1e-3) / 1e9
+    achieved_tf = F * K / (stage_ms * 1e-3) / 1e12
+    tpe = tc_traffic_per_element()
+    variants = {headline: {"value": value, "ms_per_step": ms_per_step, "stage_ms": stage_ms,
+                           "achieved_tflops": achieved_tf, "achieved_gbs": achieved_gbs,
+                           "dtype": "f32 fields, bf16x3 tensor products"}}
+    del Q, m
+    torch.cuda.empty_cache()
 
-    variants = {}
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, CUDA-core FMA
+    m32, Q32 = build_case(W, "fp32", rank)
+    t32, s32 = time_steps(W, m32, Q32, args.steps, 3)
+    variants["fp32"] = {"value": ws * dof * 5 / (t32 / args.steps * 1e-3), "ms_per_step": t32 / args.steps,
+                        "stage_ms": s32, "achieved_tflops": F * K / (s32 * 1e-3) / 1e12,
+                        "achieved_gbs": B * K / (s32 * 1e-3) / 1e9, "dtype": "f32",
+                        "alu_frac": F * K / (s32 * 1e-3) / 1e12 / fp32_peak}
+    del Q32, m32
+    torch.cuda.empty_cache()
     if not args.no_fp64:
-        del Q
         m64, Q64 = build_case(W, "fp64", rank)
         t64, s64 = time_steps(W, m64, Q64, max(1, args.steps // 5), 3)
         ms64 = t64 / max(1, args.steps // 5)
@@ -434,18 +480,9 @@ def main():
         variants["fp64"] = {"value": ws * dof * 5 / (ms64 * 1e-3), "ms_per_step": ms64, "stage_ms": s64,
                             "achieved_tflops": F * K / (s64 * 1e-3) / 1e12,
                             "achieved_gbs": B64 * K / (s64 * 1e-3) / 1e9, "dtype": "f64"}
+        variants["fp64"]["headline_speedup"] = value / variants["fp64"]["value"]
         del Q64, m64
-    variants["fp32"] = {"value": value, "ms_per_step": ms_per_step, "stage_ms": stage_ms,
-                        "achieved_tflops": achieved_tf, "achieved_gbs": achieved_gbs, "dtype": "f32"}
-    if not args.no_tc:
-        mtc, Qtc = build_case(W, "fp32_3xbf16", rank)
-        ttc, stc = time_steps(W, mtc, Qtc, args.steps, 3)
-        W.wadg_device_status(mtc)
-        mstc = ttc / args.steps
-        variants["fp32_3xbf16"] = {"value": ws * dof * 5 / (mstc * 1e-3), "ms_per_step": mstc, "stage_ms": stc,
-                                   "achieved_tflops": F * K / (stc * 1e-3) / 1e12,
-                                   "achieved_gbs": B * K / (stc * 1e-3) / 1e9, "dtype": "f32 (bf16x3 products)"}
-        del Qtc, mtc
+        torch.cuda.empty_cache()
 
     extras = {}
     if not args.no_extras:
@@ -458,18 +495,20 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16x3/f32", "data": "synthetic",
         "config": {"workload": f"warped Kuhn cube {WORKLOAD['n']}^3x6 = {K} curved tets, N=4 (Np=35), "
                                "heterogeneous c^2, 1 shot, LSRK(5,4) step = 5 fused stage launches",
-                   "elements": K, "N": WORKLOAD["N"], "shots": 1, "dof": dof,
+                   "elements": K, "N": WORKLOAD["N"], "shots": 1, "dof": dof, "precision": headline,
                    "l2": "inputs larger than L2 (1.1 GB FP32 geometric factors)",
                    "parallelism": f"replicas{ws}"},
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp32_peak, "traffic": None,
-                     "kernel": "stage_kernel<float,4,12> (one launch = one stage over all elements)",
-                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)",
-                     "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
-                             "peak_kind": peak_kind}},
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm,
+                     "traffic": None if tpe is None else tpe * K,
+                     "peak_kind": peak_kind,
+                     "kernel": "stage_tc_kernel<4,1> (one launch = one LSRK stage over all elements)",
+                     "algorithmic_bytes_per_element": B,
+                     "tensor": {"achieved_fp32_equiv_tflops": achieved_tf,
+                                "note": "flops counted once per product; each runs as three bf16 MMAs"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
