@@ -269,7 +269,7 @@ def accuracy(W):
         h = 2.0 / n
         dt_max = 0.5 * (h / 2) / (N + 1) ** 2
         case = {"workload": f"warped cube {n}^3x6, N={N}, c^2=1, standing wave to T={T}, dt_max={dt_max:.3e}"}
-        for prec in ("fp64", "fp32", "fp32_3xbf16"):
+        for prec in ("fp64", "fp32", "fp32_3xbf16", "fp32_tf32"):
             m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
             W.wadg_set_operators(m, prec, 1, 1.0, 1.0, None)
             xq = W.wadg_volume_points(m)
@@ -280,7 +280,7 @@ def accuracy(W):
             err = W.wadg_l2_error(m, Q, torch.from_numpy(standing_wave(xq, T)[:, :, None, :]).cuda(), 1)
             case[prec] = {"l2_error_p": err, "nsteps": nsteps}
         e64 = case["fp64"]["l2_error_p"]
-        for prec in ("fp32", "fp32_3xbf16"):
+        for prec in ("fp32", "fp32_3xbf16", "fp32_tf32"):
             case[prec]["ratio_to_fp64"] = case[prec]["l2_error_p"] / e64
             case[prec]["equal_l2_error"] = bool(case[prec]["l2_error_p"] <= 1.05 * e64)
         out[f"n{n}_N{N}"] = case
@@ -461,6 +461,15 @@ def main():
                            "achieved_tflops": achieved_tf, "achieved_gbs": achieved_gbs,
                            "dtype": "f32 fields, bf16x3 tensor products"}}
     del Q, m
+    torch.cuda.empty_cache()
+
+    mtf, Qtf = build_case(W, "fp32_tf32", rank)
+    ttf, stf = time_steps(W, mtf, Qtf, args.steps, 3)
+    W.wadg_device_status(mtf)
+    variants["fp32_tf32"] = {"value": ws * dof * 5 / (ttf / args.steps * 1e-3), "ms_per_step": ttf / args.steps,
+                             "stage_ms": stf, "achieved_gbs": B * K / (stf * 1e-3) / 1e9,
+                             "dtype": "f32 fields, tf32 tensor products"}
+    del Qtf, mtf
     torch.cuda.empty_cache()
 
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, CUDA-core FMA

@@ -15,6 +15,7 @@ from .api import (  # noqa: E402,F401
     WADG_FP32,
     WADG_FP64,
     WADG_FP32_3XBF16,
+    WADG_FP32_TF32,
     wadg_device_status,
     wadg_selftest_bounded_wait,
     BatchHandle,

@@ -13,8 +13,8 @@ import numpy as np
 
 from ._lib import WadgError, load
 
-WADG_FP64, WADG_FP32, WADG_FP32_3XBF16 = 0, 1, 3
-PRECISIONS = {"fp64": WADG_FP64, "fp32": WADG_FP32, "fp32_3xbf16": WADG_FP32_3XBF16}
+WADG_FP64, WADG_FP32, WADG_FP32_TF32, WADG_FP32_3XBF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": WADG_FP64, "fp32": WADG_FP32, "fp32_tf32": WADG_FP32_TF32, "fp32_3xbf16": WADG_FP32_3XBF16}
 
 
 def _check(status: int, where: str, mesh=None):

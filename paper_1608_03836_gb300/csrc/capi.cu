@@ -528,12 +528,13 @@ int wadg_volume_points(const wadg_mesh* m, double* xyz) {
 
 int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, double tau_u, const double* c2q) {
   if (!m) return WADG_EINVAL;
-  if (precision != WADG_FP64 && precision != WADG_FP32 && precision != WADG_FP32_3XBF16)
+  if (precision != WADG_FP64 && precision != WADG_FP32 && precision != WADG_FP32_TF32 &&
+      precision != WADG_FP32_3XBF16)
     return fail(m, WADG_EUNSUPPORTED, "precision %d is not built", precision);
-  if (precision == WADG_FP32_3XBF16 && m->N > 4)
-    return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 4");
+  const bool tensor = precision == WADG_FP32_3XBF16 || precision == WADG_FP32_TF32;
+  if (tensor && m->N > 4) return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 4");
   if (shots < 1 || shots > (1 << 20)) return fail(m, WADG_EINVAL, "shots=%d", shots);
-  if (precision == WADG_FP32_3XBF16 && (int64_t)m->K * shots * m->ref.Np >= ((int64_t)1 << 31))
+  if (tensor && (int64_t)m->K * shots * m->ref.Np >= ((int64_t)1 << 31))
     return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage needs K * shots * Np < 2^31 (31-bit gather offsets)");
   if (!(tau_p >= 0) || !(tau_u >= 0)) return fail(m, WADG_EINVAL, "penalties must be >= 0");
   DeviceGuard g(m->device);
@@ -568,12 +569,14 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
       int st = upload_ops<float>(m, m->ops32);
       if (st != WADG_OK) return st;
     }
-    if (precision == WADG_FP32_3XBF16) {
-      if (!m->d_tcops) {
+    if (tensor) {
+      const int fmt = precision == WADG_FP32_3XBF16 ? 0 : 1;
+      if (!m->d_tcops || m->tc_fmt != fmt) {
         std::vector<uint8_t> packed;
-        if (!pack_tc_ops(m->N, m->ref, packed)) return fail(m, WADG_EUNSUPPORTED, "tensor-core tables");
-        WADG_CUDA(m, cudaMalloc((void**)&m->d_tcops, packed.size()));
+        if (!pack_tc_ops(m->N, m->ref, fmt, packed)) return fail(m, WADG_EUNSUPPORTED, "tensor-core tables");
+        if (!m->d_tcops) WADG_CUDA(m, cudaMalloc((void**)&m->d_tcops, packed.size()));
         WADG_CUDA(m, cudaMemcpy(m->d_tcops, packed.data(), packed.size(), cudaMemcpyHostToDevice));
+        m->tc_fmt = fmt;
       }
       const int64_t Kt = (K + 127) / 128;
       if (!m->d_vgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_vgeo_il, (size_t)Kt * 128 * 11 * Nq * sizeof(float)));
@@ -634,21 +637,22 @@ StageParams<T> base_params(const wadg_mesh* m) {
 }
 
 // Stage launch for the mesh's precision: RHS and LSRK stages of
-// WADG_FP32_3XBF16 run on the tensor cores, everything else on CUDA cores.
+// WADG_FP32_3XBF16 and WADG_FP32_TF32 run on the tensor cores, everything
+// else on CUDA cores.
 template <typename T>
 cudaError_t stage_launch(const wadg_mesh* m, const StageParams<T>& p, int mode, cudaStream_t st) {
   return launch_stage<T>(m->N, p, mode, st);
 }
 template <>
 cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p, int mode, cudaStream_t st) {
-  if (m->precision == WADG_FP32_3XBF16 && (mode == 0 || mode == 1)) {
+  if ((m->precision == WADG_FP32_3XBF16 || m->precision == WADG_FP32_TF32) && (mode == 0 || mode == 1)) {
     TcStageParams P;
     P.s = p;
     P.ops = m->d_tcops;
     P.err = m->d_err;
     P.vgeo_il = m->d_vgeo_il;
     P.fgeo_il = m->d_fgeo_il;
-    return launch_stage_tc(m->N, P, mode, m->num_sms, st);
+    return launch_stage_tc(m->N, P, mode, m->tc_fmt, m->num_sms, st);
   }
   return launch_stage<float>(m->N, p, mode, st);
 }

@@ -125,10 +125,72 @@ __device__ __forceinline__ void mma3_chain(const Mma3& g) {
   }
 }
 
+// Operand formats.  A tile of R rows by K values takes R K 4 bytes in both:
+// format 0 holds the bf16 hi part at the tile base and the lo part `part`
+// bytes after it (three products per K step of 16); format 1 holds tf32
+// values (one product per K step of 8).  Both use the K-major no-swizzle
+// core-matrix layout (8 rows x 16 bytes per core matrix), and one
+// instruction's K step is 256 bytes (16 in the descriptor address) in both.
+template <int FMT>
+struct OpFmt;
+
+template <>
+struct OpFmt<0> {
+  __host__ __device__ static constexpr uint32_t sbo(int K) { return (uint32_t)(K / 8) * 128u; }
+  __host__ __device__ static constexpr uint32_t idesc(int M, int Nn) { return tc::idesc_bf16(M, Nn); }
+  __device__ static void st8(uint8_t* base, int part, int row, int k0, int K, const float (&x)[8]) {
+    const uint32_t o = tc::kmajor_offset(row, k0, K);
+    tc::split_store8(base + o, base + part + o, x);
+  }
+  __device__ static void st4(uint8_t* base, int part, int row, int k0, int K, const float (&x)[4]) {
+    const uint32_t o = tc::kmajor_offset(row, k0, K);
+    tc::split_store4(base + o, base + part + o, x);
+  }
+  __device__ static void st1(uint8_t* base, int part, int row, int k, int K, float x) {
+    const uint32_t o = tc::kmajor_offset(row, k, K);
+    __nv_bfloat16 h, l;
+    tc::split_bf16(x, h, l);
+    *reinterpret_cast<__nv_bfloat16*>(base + o) = h;
+    *reinterpret_cast<__nv_bfloat16*>(base + part + o) = l;
+  }
+  template <int KE>
+  __device__ static void chain(const Mma3& g) {
+    mma3_chain<KE / 16>(g);
+  }
+};
+
+template <>
+struct OpFmt<1> {
+  __host__ __device__ static constexpr uint32_t sbo(int K) { return (uint32_t)(K / 4) * 128u; }
+  __host__ __device__ static constexpr uint32_t idesc(int M, int Nn) { return tc::idesc_tf32(M, Nn); }
+  __device__ static void st8(uint8_t* base, int, int row, int k0, int K, const float (&x)[8]) {
+    uint8_t* d = base + tc::kmajor_offset4(row, k0, K);
+    *reinterpret_cast<uint4*>(d) = make_uint4(tc::to_tf32(x[0]), tc::to_tf32(x[1]), tc::to_tf32(x[2]), tc::to_tf32(x[3]));
+    *reinterpret_cast<uint4*>(d + 128) =
+        make_uint4(tc::to_tf32(x[4]), tc::to_tf32(x[5]), tc::to_tf32(x[6]), tc::to_tf32(x[7]));
+  }
+  __device__ static void st4(uint8_t* base, int, int row, int k0, int K, const float (&x)[4]) {
+    *reinterpret_cast<uint4*>(base + tc::kmajor_offset4(row, k0, K)) =
+        make_uint4(tc::to_tf32(x[0]), tc::to_tf32(x[1]), tc::to_tf32(x[2]), tc::to_tf32(x[3]));
+  }
+  __device__ static void st1(uint8_t* base, int, int row, int k, int K, float x) {
+    *reinterpret_cast<uint32_t*>(base + tc::kmajor_offset4(row, k, K)) = tc::to_tf32(x);
+  }
+  template <int KE>
+  __device__ static void chain(const Mma3& g) {
+#pragma unroll
+    for (int ks = 0; ks < KE / 8; ++ks) {
+      const uint64_t o = (uint64_t)(16 * ks);
+      tc::mma_tf32(g.d, g.ah + o, g.bh + o, g.idesc, (g.acc || ks > 0) ? 1u : 0u);
+    }
+  }
+};
+
 }  // namespace
 
-template <int N, int MODE>
+template <int N, int MODE, int FMT>
 __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStageParams P) {
+  using OF = OpFmt<FMT>;
   using T = TcDims<N>;
   constexpr int NP = T::NP, NQ = T::NQ, NFP = T::NFP, NFQ = T::NFQ, KP = T::KP, QC = T::QC, NPS = T::NPS;
   constexpr int TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16, NCH = T::NCH;
@@ -185,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   const uint32_t aq = tc::smem_addr(sAQ), ax = tc::smem_addr(sAX), fa = tc::smem_addr(sFA);
   const uint32_t ft = tc::smem_addr(sFT), slots = tc::smem_addr(smem + T::OFF_SLOT);
   auto slot_addr = [&](int s) { return slots + (uint32_t)(s * T::SZ_SLOT); };
-  const uint32_t sbo_KP = (KP / 8) * 128, sbo_16 = 2 * 128;
+  const uint32_t sbo_KP = OF::sbo(KP), sbo_16 = OF::sbo(16);
   const uint8_t* vol_ops = P.ops;
   const uint8_t* upd_ops = P.ops + (size_t)NCH * T::SZ_OPV;
 
@@ -228,36 +290,36 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1);
     const int i = w - 8;
     if (i >= 0 && i < 3)
-      mma3_chain<KP / 16>(mk_mma3(d + 16 * i, aq + (2 * (1 + i)) * T::A_FIELD, aq + (2 * (1 + i) + 1) * T::A_FIELD,
-                                  sbo_KP, sl, sl + T::B_V, sbo_KP, tc::idesc_bf16(128, 16), false));
+      OF::template chain<KP>(mk_mma3(d + 16 * i, aq + (2 * (1 + i)) * T::A_FIELD, aq + (2 * (1 + i) + 1) * T::A_FIELD,
+                                  sbo_KP, sl, sl + T::B_V, sbo_KP, OF::idesc(128, 16), false));
     else if (i == 3)
-      mma3_chain<KP / 16>(mk_mma3(d + 48, aq, aq + T::A_FIELD, sbo_KP, sl + 2 * T::B_V, sl + 5 * T::B_V, sbo_KP,
-                                  tc::idesc_bf16(128, 48), false));
+      OF::template chain<KP>(mk_mma3(d + 48, aq, aq + T::A_FIELD, sbo_KP, sl + 2 * T::B_V, sl + 5 * T::B_V, sbo_KP,
+                                  OF::idesc(128, 48), false));
   };
   // b_p += sum_a Dw_a U^a (one accumulator per a; a = r holds the surface
   // term), b_ui += Vw g_i (onto the surface terms)
   auto issue_DW = [&](int c, int i) {
     const uint32_t sl = slot_addr(2 + (c & 1)), bvw = sl + 6 * T::B_P;
     if (i < 3)
-      mma3_chain<1>(mk_mma3(tmem + (i == 0 ? T::TB : T::TBX + KP * (i - 1)), ax + (2 * i) * T::A_CH,
+      OF::template chain<16>(mk_mma3(tmem + (i == 0 ? T::TB : T::TBX + KP * (i - 1)), ax + (2 * i) * T::A_CH,
                             ax + (2 * i + 1) * T::A_CH, sbo_16, sl + 2 * i * T::B_P, sl + (2 * i + 1) * T::B_P, sbo_16,
-                            tc::idesc_bf16(128, KP), i == 0 || c > 0));
+                            OF::idesc(128, KP), i == 0 || c > 0));
     else if (i < 6)
-      mma3_chain<1>(mk_mma3(tmem + T::TB + KP * (i - 2), ax + (2 * i) * T::A_CH, ax + (2 * i + 1) * T::A_CH, sbo_16,
-                            bvw, bvw + T::B_P, sbo_16, tc::idesc_bf16(128, KP), true));
+      OF::template chain<16>(mk_mma3(tmem + T::TB + KP * (i - 2), ax + (2 * i) * T::A_CH, ax + (2 * i + 1) * T::A_CH, sbo_16,
+                            bvw, bvw + T::B_P, sbo_16, OF::idesc(128, KP), true));
   };
   auto issue_U1 = [&](int c, int w) {  // (V_q M^^{-1}) b per field (N = 16)
     const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1);
     const int f = w - 8;
     if (f >= 0 && f < 4)
-      mma3_chain<KP / 16>(mk_mma3(d + 16 * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP, sl,
-                                  sl + T::B_V, sbo_KP, tc::idesc_bf16(128, 16), false));
+      OF::template chain<KP>(mk_mma3(d + 16 * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP, sl,
+                                  sl + T::B_V, sbo_KP, OF::idesc(128, 16), false));
   };
   auto issue_U2 = [&](int c, int f) {  // r += P_q (W ...) per field (N = KP)
     const uint32_t sl = slot_addr(2 + (c & 1));
     if (f < 4)
-      mma3_chain<1>(mk_mma3(tmem + T::TB + KP * f, ax + (2 * f) * T::A_CH, ax + (2 * f + 1) * T::A_CH, sbo_16, sl,
-                            sl + T::B_P, sbo_16, tc::idesc_bf16(128, KP), c > 0));
+      OF::template chain<16>(mk_mma3(tmem + T::TB + KP * f, ax + (2 * f) * T::A_CH, ax + (2 * f + 1) * T::A_CH, sbo_16, sl,
+                            sl + T::B_P, sbo_16, OF::idesc(128, KP), c > 0));
   };
 
   if (tid == 0 && (int64_t)blockIdx.x < ntiles) prefetch_volume();
@@ -345,23 +407,17 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
             cv[1 + i] = on ? 0.5f * (up + qm[it][1 + i]) : 0.f;
             cv[4 + i] = on ? up - qm[it][1 + i] : 0.f;
           }
-          const uint32_t off = tc::kmajor_offset(r, j, NFP16);
 #pragma unroll
-          for (int c = 0; c < 7; ++c) {
-            __nv_bfloat16 h, l;
-            tc::split_bf16(cv[c], h, l);
-            *reinterpret_cast<__nv_bfloat16*>(sFA + (2 * c) * T::A_FN + off) = h;
-            *reinterpret_cast<__nv_bfloat16*>(sFA + (2 * c + 1) * T::A_FN + off) = l;
-          }
+          for (int c = 0; c < 7; ++c) OF::st1(sFA + (2 * c) * T::A_FN, T::A_FN, r, j, NFP16, cv[c]);
         }
       }
       sync_check();
       if (failed) break;
       if (issuer) {
         if (warp < 7)
-          mma3_chain<NFP16 / 16>(mk_mma3(tmem + T::TI + warp * NFQ16, fa + (2 * warp) * T::A_FN,
-                                         fa + (2 * warp + 1) * T::A_FN, (NFP16 / 8) * 128, ft, ft + T::B_TRI,
-                                         (NFP16 / 8) * 128, tc::idesc_bf16(128, NFQ16), false));
+          OF::template chain<NFP16>(mk_mma3(tmem + T::TI + warp * NFQ16, fa + (2 * warp) * T::A_FN,
+                                         fa + (2 * warp + 1) * T::A_FN, OF::sbo(NFP16), ft, ft + T::B_TRI,
+                                         OF::sbo(NFP16), OF::idesc(128, NFQ16), false));
         tc::commit(bar(7));
       }
       wait_all(7, par_f);
@@ -398,10 +454,8 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
               F[3][j] = sc * nz;
             }
           }
-          const uint32_t off = tc::kmajor_offset(mrow, q0 + b4, NFQ16);
 #pragma unroll
-          for (int fld = 0; fld < 4; ++fld)
-            tc::split_store4(sFA + (2 * fld) * T::A_FQ + off, sFA + (2 * fld + 1) * T::A_FQ + off, F[fld]);
+          for (int fld = 0; fld < 4; ++fld) OF::st4(sFA + (2 * fld) * T::A_FQ, T::A_FQ, mrow, q0 + b4, NFQ16, F[fld]);
         }
       }
       sync_check();
@@ -410,9 +464,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         const uint32_t bl = ft + 2 * T::B_TRI;
         const int fld = warp - 8;
         if (fld >= 0 && fld < 4)
-          mma3_chain<NFQ16 / 16>(mk_mma3(tmem + T::TL + fld * NFP16, fa + (2 * fld) * T::A_FQ,
-                                         fa + (2 * fld + 1) * T::A_FQ, (NFQ16 / 8) * 128, bl, bl + T::B_TRI,
-                                         (NFQ16 / 8) * 128, tc::idesc_bf16(128, NFP16), false));
+          OF::template chain<NFQ16>(mk_mma3(tmem + T::TL + fld * NFP16, fa + (2 * fld) * T::A_FQ,
+                                         fa + (2 * fld + 1) * T::A_FQ, OF::sbo(NFQ16), bl, bl + T::B_TRI,
+                                         OF::sbo(NFQ16), OF::idesc(128, NFP16), false));
         tc::commit(bar(7));
       }
       wait_all(7, par_f);
@@ -470,8 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       float x[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) x[j] = n0 + j < NP ? sQS[(grp * TILE + mrow) * NPS + n0 + j] : 0.f;
-      const uint32_t off = tc::kmajor_offset(mrow, n0, KP);
-      tc::split_store8(sAQ + (2 * grp) * T::A_FIELD + off, sAQ + (2 * grp + 1) * T::A_FIELD + off, x);
+      OF::st8(sAQ + (2 * grp) * T::A_FIELD, T::A_FIELD, mrow, n0, KP, x);
     }
     sync_check();
     if (failed) break;
@@ -538,11 +591,10 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
           load_slot(2 + ((c + 1) & 1), vol_ops + (size_t)(c + 1) * T::SZ_OPV + T::SZ_VA, T::SZ_VB);
       }
       {
-        const uint32_t off = tc::kmajor_offset(mrow, 4 * grp, QC);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          tc::split_store4(sAX + (2 * a) * T::A_CH + off, sAX + (2 * a + 1) * T::A_CH + off, U[a]);
-          tc::split_store4(sAX + (2 * (3 + a)) * T::A_CH + off, sAX + (2 * (3 + a) + 1) * T::A_CH + off, g[a]);
+          OF::st4(sAX + (2 * a) * T::A_CH, T::A_CH, mrow, 4 * grp, QC, U[a]);
+          OF::st4(sAX + (2 * (3 + a)) * T::A_CH, T::A_CH, mrow, 4 * grp, QC, g[a]);
         }
       }
       sync_check();
@@ -593,8 +645,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
           if (grp == 0) b += __uint_as_float(v1[j]) + __uint_as_float(v2[j]) + (src ? p.src_amp * p.src_vec[sh * NP + n0 + j] : 0.f);
           x[j] = n0 + j < NP ? b : 0.f;
         }
-        const uint32_t off = tc::kmajor_offset(mrow, n0, KP);
-        tc::split_store8(sAQ + (2 * grp) * T::A_FIELD + off, sAQ + (2 * grp + 1) * T::A_FIELD + off, x);
+        OF::st8(sAQ + (2 * grp) * T::A_FIELD, T::A_FIELD, mrow, n0, KP, x);
       }
     }
     sync_check();
@@ -649,8 +700,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       }
 #pragma unroll
       for (int h8 = 0; h8 < 2; ++h8) {
-        const uint32_t off = tc::kmajor_offset(mrow, 8 * h8, QC);
-        tc::split_store8(sAX + (2 * grp) * T::A_CH + off, sAX + (2 * grp + 1) * T::A_CH + off, x[h8]);
+        OF::st8(sAX + (2 * grp) * T::A_CH, T::A_CH, mrow, 8 * h8, QC, x[h8]);
       }
       sync_check();
       if (failed) break;
@@ -736,32 +786,32 @@ cudaError_t launch_bounded_wait_selftest(int* err, uint32_t max_iters, cudaStrea
   return cudaGetLastError();
 }
 
+template <int N, int MODE, int FMT>
+cudaError_t launch_one(const TcStageParams& P, int grid, cudaStream_t stream) {
+  using T = TcDims<N>;
+  auto kern = stage_tc_kernel<N, MODE, FMT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, T::SMEM, stream>>>(P);
+  return cudaGetLastError();
+}
+
 template <int N>
-cudaError_t launch_stage_tc_n(const TcStageParams& P, int mode, int grid, cudaStream_t stream) {
+cudaError_t launch_stage_tc_n(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream) {
   using T = TcDims<N>;
   const int64_t ntiles = (P.s.ncols + T::TILE - 1) / T::TILE;
   if (ntiles == 0) return cudaSuccess;
   const int g = (int)(ntiles < grid ? ntiles : grid);
-  if (mode == kRhs) {
-    auto kern = stage_tc_kernel<N, kRhs>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
-    if (e != cudaSuccess) return e;
-    kern<<<g, kThreads, T::SMEM, stream>>>(P);
-  } else {
-    auto kern = stage_tc_kernel<N, kLsrk>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
-    if (e != cudaSuccess) return e;
-    kern<<<g, kThreads, T::SMEM, stream>>>(P);
-  }
-  return cudaGetLastError();
+  if (mode == kRhs) return fmt == 0 ? launch_one<N, kRhs, 0>(P, g, stream) : launch_one<N, kRhs, 1>(P, g, stream);
+  return fmt == 0 ? launch_one<N, kLsrk, 0>(P, g, stream) : launch_one<N, kLsrk, 1>(P, g, stream);
 }
 
-cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int grid, cudaStream_t stream) {
+cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream) {
   switch (N) {
-    case 1: return launch_stage_tc_n<1>(P, mode, grid, stream);
-    case 2: return launch_stage_tc_n<2>(P, mode, grid, stream);
-    case 3: return launch_stage_tc_n<3>(P, mode, grid, stream);
-    case 4: return launch_stage_tc_n<4>(P, mode, grid, stream);
+    case 1: return launch_stage_tc_n<1>(P, mode, fmt, grid, stream);
+    case 2: return launch_stage_tc_n<2>(P, mode, fmt, grid, stream);
+    case 3: return launch_stage_tc_n<3>(P, mode, fmt, grid, stream);
+    case 4: return launch_stage_tc_n<4>(P, mode, fmt, grid, stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -802,51 +852,67 @@ size_t host_kmajor_offset(int row, int k, int K) {
   return (size_t)(((row >> 3) * (K >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// Writes a [R x K] split tile: hi part at dst, lo part at dst + part_bytes.
+// tf32 bits of x: round to nearest, ties away from zero, at bit 13.
+uint32_t tf32_bits_rna(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return u & 0xffffe000u;
+  return (u + 0x1000u) & 0xffffe000u;
+}
+
+// Writes a [R x K] operand tile of the given format: format 0, the split bf16
+// parts (hi at dst, lo at dst + part_bytes); format 1, tf32 values in the
+// 4-byte K-major layout (the same R K 4 bytes).
 template <typename F>
-void put_tile(uint8_t* dst, size_t part_bytes, int R, int K, F value) {
+void put_tile(int fmt, uint8_t* dst, size_t part_bytes, int R, int K, F value) {
   for (int r = 0; r < R; ++r)
     for (int k = 0; k < K; ++k) {
       const double x = value(r, k);
-      const uint16_t h = bf16_bits_rne((float)x);
-      const uint16_t l = bf16_bits_rne((float)(x - (double)bf16_bits_to_float(h)));
-      const size_t off = host_kmajor_offset(r, k, K);
-      std::memcpy(dst + off, &h, 2);
-      std::memcpy(dst + part_bytes + off, &l, 2);
+      if (fmt == 0) {
+        const uint16_t h = bf16_bits_rne((float)x);
+        const uint16_t l = bf16_bits_rne((float)(x - (double)bf16_bits_to_float(h)));
+        const size_t off = host_kmajor_offset(r, k, K);
+        std::memcpy(dst + off, &h, 2);
+        std::memcpy(dst + part_bytes + off, &l, 2);
+      } else {
+        const uint32_t t = tf32_bits_rna((float)x);
+        const size_t off = (size_t)(((r >> 3) * (K >> 2) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+        std::memcpy(dst + off, &t, 4);
+      }
     }
 }
 
 template <int N>
-void pack_n(const RefOps& o, std::vector<uint8_t>& out) {
+void pack_n(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
   using T = TcDims<N>;
   const int Np = o.Np, Nq = o.Nq, KP = T::KP, QC = T::QC;
   out.assign((size_t)T::NCH * (T::SZ_OPV + T::SZ_OPU) + T::SZ_FOPS, 0);
   for (int ch = 0; ch < T::NCH; ++ch) {
     uint8_t* v = out.data() + (size_t)ch * T::SZ_OPV;
     auto qn = [&](int r) { return ch * QC + r; };
-    put_tile(v, T::B_V, QC, KP, [&](int r, int n) {
+    put_tile(fmt, v, T::B_V, QC, KP, [&](int r, int n) {
       const int q = qn(r);
       return (q < Nq && n < Np) ? o.Vq[q * Np + n] : 0.0;
     });
-    put_tile(v + 2 * T::B_V, 3 * T::B_V, 3 * QC, KP, [&](int r, int n) {
+    put_tile(fmt, v + 2 * T::B_V, 3 * T::B_V, 3 * QC, KP, [&](int r, int n) {
       const int a = r / QC, q = qn(r % QC);
       return (q < Nq && n < Np) ? o.Vqa[(a * Nq + q) * Np + n] : 0.0;
     });
     for (int a = 0; a < 3; ++a)
-      put_tile(v + 8 * T::B_V + 2 * a * T::B_P, T::B_P, KP, QC, [&](int n, int k) {
+      put_tile(fmt, v + 8 * T::B_V + 2 * a * T::B_P, T::B_P, KP, QC, [&](int n, int k) {
         const int q = qn(k);
         return (q < Nq && n < Np) ? o.Dw[(a * Np + n) * Nq + q] : 0.0;
       });
-    put_tile(v + 8 * T::B_V + 6 * T::B_P, T::B_P, KP, QC, [&](int n, int k) {
+    put_tile(fmt, v + 8 * T::B_V + 6 * T::B_P, T::B_P, KP, QC, [&](int n, int k) {
       const int q = qn(k);
       return (q < Nq && n < Np) ? o.Vw[n * Nq + q] : 0.0;
     });
     uint8_t* u = out.data() + (size_t)T::NCH * T::SZ_OPV + (size_t)ch * T::SZ_OPU;
-    put_tile(u, T::B_V, QC, KP, [&](int r, int n) {
+    put_tile(fmt, u, T::B_V, QC, KP, [&](int r, int n) {
       const int q = qn(r);
       return (q < Nq && n < Np) ? o.Vtilde[q * Np + n] : 0.0;
     });
-    put_tile(u + 2 * T::B_V, T::B_P, KP, QC, [&](int n, int k) {
+    put_tile(fmt, u + 2 * T::B_V, T::B_P, KP, QC, [&](int n, int k) {
       const int q = qn(k);
       return (q < Nq && n < Np) ? o.Pq[n * Nq + q] : 0.0;
     });
@@ -855,22 +921,22 @@ void pack_n(const RefOps& o, std::vector<uint8_t>& out) {
   // V_tri^T diag(w_f) as [NFP16 rows (j) x NFQ16 (q)]
   const int Nfp = o.Nfp, Nfq = o.Nfq;
   uint8_t* fo = out.data() + (size_t)T::NCH * (T::SZ_OPV + T::SZ_OPU);
-  put_tile(fo, T::B_TRI, T::NFQ16, T::NFP16, [&](int q, int j) {
+  put_tile(fmt, fo, T::B_TRI, T::NFQ16, T::NFP16, [&](int q, int j) {
     return (q < Nfq && j < Nfp) ? o.Vtri[q * Nfp + j] : 0.0;
   });
-  put_tile(fo + 2 * T::B_TRI, T::B_TRI, T::NFP16, T::NFQ16, [&](int j, int q) {
+  put_tile(fmt, fo + 2 * T::B_TRI, T::B_TRI, T::NFP16, T::NFQ16, [&](int j, int q) {
     return (q < Nfq && j < Nfp) ? o.VtriTw[j * Nfq + q] : 0.0;
   });
 }
 
 }  // namespace
 
-bool pack_tc_ops(int N, const RefOps& o, std::vector<uint8_t>& out) {
+bool pack_tc_ops(int N, const RefOps& o, int fmt, std::vector<uint8_t>& out) {
   switch (N) {
-    case 1: pack_n<1>(o, out); return true;
-    case 2: pack_n<2>(o, out); return true;
-    case 3: pack_n<3>(o, out); return true;
-    case 4: pack_n<4>(o, out); return true;
+    case 1: pack_n<1>(o, fmt, out); return true;
+    case 2: pack_n<2>(o, fmt, out); return true;
+    case 3: pack_n<3>(o, fmt, out); return true;
+    case 4: pack_n<4>(o, fmt, out); return true;
     default: return false;
   }
 }

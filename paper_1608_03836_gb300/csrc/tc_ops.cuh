@@ -41,6 +41,34 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor for kind::tf32 (A, B tf32, FP32 accumulator, both
+// K-major): A/B format bits 7-9 and 10-12 = 2 (TF32).
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle tile of 4-byte
+// elements with K columns (a core matrix holds 8 rows x 4 elements).
+__device__ __forceinline__ uint32_t kmajor_offset4(int row, int k, int K) {
+  return (uint32_t)(((row >> 3) * (K >> 2) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// FP32 -> tf32 (round to nearest, ties away from zero), as a 32-bit pattern.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// D[tmem] (+)= A * B^T over one K step of 8 tf32 values (issued by one thread).
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
 // D[tmem] (+)= A * B^T over one K step of 16 (issued by one thread).
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {

@@ -92,8 +92,8 @@ struct TcStageParams {
   const float* vgeo_il = nullptr;  // column-interleaved geometric factors (see aux_kernels.cu)
   const float* fgeo_il = nullptr;
 };
-cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int grid, cudaStream_t stream);
-bool pack_tc_ops(int N, const RefOps& o, std::vector<uint8_t>& out);
+cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
+bool pack_tc_ops(int N, const RefOps& o, int fmt, std::vector<uint8_t>& out);
 cudaError_t launch_bounded_wait_selftest(int* err, uint32_t max_iters, cudaStream_t stream);
 
 // Batches of FP32 meshes (batch.cu).
@@ -143,7 +143,8 @@ struct wadg_mesh {
   void* d_fgeo = nullptr;
   wadg::DevOps<double> ops64;
   wadg::DevOps<float> ops32;
-  uint8_t* d_tcops = nullptr;  // split operators of the tensor-core stage
+  uint8_t* d_tcops = nullptr;  // operators of the tensor-core stage (split bf16 or tf32)
+  int tc_fmt = -1;             // format of d_tcops: 0 split bf16, 1 tf32
   float* d_vgeo_il = nullptr;  // column-interleaved geometry for the tensor-core stage
   float* d_fgeo_il = nullptr;
   int* d_err = nullptr;        // device error flag (bounded waits)

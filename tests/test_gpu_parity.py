@@ -40,10 +40,10 @@ def _gpu_rhs(W, m, Q):
     return out.double().cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16", "fp32_tf32"])
 @pytest.mark.parametrize("N,n", [(1, 3), (2, 2), (3, 2), (4, 2), (5, 2), (6, 1)])
 def test_rhs_matches_oracle(W, precision, N, n):
-    if precision == "fp32_3xbf16" and N > 4:
+    if precision in ("fp32_3xbf16", "fp32_tf32") and N > 4:
         pytest.skip("the tensor-core stage is built for N <= 4")
     VXYZ, EToV, geom = make_mesh_inputs(n, N)
     om = oracle_case(VXYZ, EToV, geom, N)
@@ -65,7 +65,7 @@ def test_volume_points_match_oracle_geometry(W):
     assert np.abs(xq - om.xq).max() < 1e-14
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16", "fp32_tf32"])
 def test_shots_and_ragged_tail(W, precision):
     """S = 3 shots of different data on one mesh; K*S = 162 is not a multiple of
     the block width, so the last block is ragged."""
@@ -82,7 +82,7 @@ def test_shots_and_ragged_tail(W, precision):
         assert l2 < TOL[precision] and mx < 10 * TOL[precision], (s, l2, mx)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_3xbf16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_3xbf16", "fp32_tf32"])
 def test_more_tiles_than_blocks(W, precision):
     """6,000 tets x 4 shots = 24,000 columns: more 128-column tiles (187.5)
     than resident blocks, so persistent blocks take several tiles, the last
@@ -122,7 +122,7 @@ def test_penalty_parameters(W, tau):
     assert l2 < TOL["fp64"]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16", "fp32_tf32"])
 def test_lsrk_steps_match_oracle(W, precision):
     import torch
     from oracle import wadg as OW
@@ -187,7 +187,7 @@ def test_bad_arguments_are_rejected(W):
     assert e.value.status == -8
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16", "fp32_tf32"])
 def test_sources_and_receivers_match_oracle(W, precision):
     """Two shots, each driven by a Ricker point source at its own seeded
     position, three receivers per shot, four LSRK steps from rest."""
