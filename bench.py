@@ -287,6 +287,54 @@ def accuracy(W):
     return out
 
 
+def c2_study(W):
+    """The precision configuration: warped cube 24^3 x 6 = 82,944 tets, N = 5,
+    c^2 = 1, standing wave to T = 0.5.  For each precision built at N = 5 (the
+    tensor-core stage is built for N <= 4), the L2 error of p against the
+    analytic solution, the relative L2 difference from the FP64 solution (the
+    FP64 path equals the oracle's discrete solution to 1e-11) and the stage
+    throughput."""
+    import torch
+    from synthetic import warped_cube, standing_wave
+    n, N, T = 24, 5, 0.5
+    VXYZ, EToV, geom = warped_cube(n, N, 0.1)
+    h = 2.0 / n
+    dt_max = 0.5 * (h / 2) / (N + 1) ** 2
+    out = {"workload": f"warped cube {n}^3x6 = {len(EToV)} tets, N={N}, c^2=1, standing wave to T={T}, "
+                       f"dt_max={dt_max:.3e}",
+           "not_built": {"fp32_3xbf16": "tensor-core stage built for N <= 4",
+                         "fp32_tf32": "tensor-core stage built for N <= 4"}}
+    ref = None
+    for prec in ("fp64", "fp32"):
+        m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
+        W.wadg_set_operators(m, prec, 1, 1.0, 1.0, None)
+        xq = W.wadg_volume_points(m)
+        Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
+        W.wadg_project(m, torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda(), Q)
+        R = torch.zeros_like(Q)
+        stream = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nsteps = W.wadg_solve(m, Q, R, 0.0, T, dt_max)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        err = W.wadg_l2_error(m, Q, torch.from_numpy(standing_wave(xq, T)[:, :, None, :]).cuda(), 1)
+        dof = 4 * m.K * m.Np
+        row = {"l2_error_p": err, "nsteps": nsteps, "solve_ms": ms,
+               "dof_stage_per_s": dof * 5 * nsteps / (ms * 1e-3)}
+        p = Q[0].double().cpu().numpy()
+        if ref is None:
+            ref = p
+        else:
+            row["rel_l2_diff_vs_fp64_nodal"] = float(np.linalg.norm(p - ref) / np.linalg.norm(ref))
+            row["ratio_to_fp64"] = err / out["fp64"]["l2_error_p"]
+        out[prec] = row
+        del Q, R, m
+        torch.cuda.empty_cache()
+    return out
+
+
 def e2e_steps(W, m, Q, steps):
     """Same metric end to end: pinned host Q, res -> device, one step, -> host."""
     import torch
@@ -415,6 +463,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--c2", action="store_true",
+                    help="run only the N = 5 precision study (82,944 tets, T = 0.5) and print its JSON")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
     args = ap.parse_args()
@@ -431,6 +481,10 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     import paper_1608_03836_gb300 as W
+    if args.c2:
+        if rank == 0:
+            print(json.dumps({"c2_precision_study": c2_study(W)}))
+        return
 
     def barrier():
         if ws > 1:
