@@ -652,6 +652,7 @@ cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p,
     P.err = m->d_err;
     P.vgeo_il = m->d_vgeo_il;
     P.fgeo_il = m->d_fgeo_il;
+    P.bulk_q = (p.ncols * m->ref.Np) % 4 == 0 && ((uintptr_t)p.Qin & 15) == 0;
     return launch_stage_tc(m->N, P, mode, m->tc_fmt, m->num_sms, st);
   }
   return launch_stage<float>(m->N, p, mode, st);

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   uint4* sNB = reinterpret_cast<uint4*>(smem + T::OFF_NB);                     // [128] neighbour offsets
   uint32_t* sC4 = reinterpret_cast<uint32_t*>(smem + T::OFF_NB + TILE * 16);   // [128] face codes
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + T::OFF_BAR);
-  // bars: 0-3 operator slots, 4-5 first products of a chunk, 6 second products, 7 faces, 8 drain
+  // bars: 0-3 operator slots, 4-5 first products of a chunk, 6 second products, 7 faces, 8 drain, 9 fields
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + T::OFF_BAR + 80);
   int* sflag = reinterpret_cast<int*>(smem + T::OFF_BAR + 84);
 
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   const int64_t ntiles = (ncols + TILE - 1) / TILE;
 
   if (tid == 0) {
-    for (int i = 0; i < 9; ++i) tc::mbar_init(tc::smem_addr(bars + i), i < 4 ? 1 : kIssuers);
+    for (int i = 0; i < 10; ++i) tc::mbar_init(tc::smem_addr(bars + i), i < 4 || i == 9 ? 1 : kIssuers);
     *sflag = 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), 512);
@@ -322,7 +322,23 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
                             sl + T::B_P, sbo_16, OF::idesc(128, KP), c > 0));
   };
 
-  if (tid == 0 && (int64_t)blockIdx.x < ntiles) prefetch_volume();
+  // fields of a tile by bulk copies (when the FP32 tile has the global row
+  // stride and the copies are 16-byte aligned), issued one tile ahead
+  const bool bulkq = NPS == NP && P.bulk_q != 0;
+  uint32_t par_q = 0;
+  auto load_q = [&](int64_t t) {  // thread 0
+    const int64_t c0 = t * TILE;
+    const uint32_t bytes = (uint32_t)((ncols - c0 < TILE ? ncols - c0 : TILE) * NP * 4);
+    tc::mbar_expect_tx(bar(9), 4 * bytes);
+    for (int f = 0; f < 4; ++f)
+      tc::bulk_g2s(tc::smem_addr(sQS + f * TILE * NPS), p.Qin + f * fs + c0 * NP, bytes, bar(9));
+    pend |= 16u;
+  };
+
+  if (tid == 0 && (int64_t)blockIdx.x < ntiles) {
+    prefetch_volume();
+    if (bulkq) load_q(blockIdx.x);
+  }
 
   for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int64_t col0 = tile * TILE;
@@ -341,8 +357,12 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       sC4[mrow] = code4;
     }
 
-    // ---- fields -> FP32 tile in shared memory (coalesced) ----
-    {
+    // ---- fields -> FP32 tile in shared memory (coalesced; or the bulk copies issued one tile ahead) ----
+    if (bulkq) {
+      wait_all(9, par_q);
+      par_q ^= 1u;
+      pend &= ~16u;
+    } else {
       const int nval = ncol_t * NP;
 #pragma unroll 5
       for (int i = tid; i < 4 * TILE * NP; i += kThreads) {
@@ -720,7 +740,10 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     if (failed) break;
     wait_all(6, par_m2);
     par_m2 ^= 1u;
-    if (tid == 0 && tile + gridDim.x < ntiles) prefetch_volume();
+    if (tid == 0 && tile + gridDim.x < ntiles) {
+      prefetch_volume();
+      if (bulkq) load_q(tile + gridDim.x);  // the FP32 tile area is free: the update's products are complete
+    }
 
     // ---- epilogue: r -> FP32 tile -> coalesced dQ/dt, or the LSRK update (Sec. 5.2) ----
 #pragma unroll
@@ -756,9 +779,11 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   }
 
   // drain: operator copies still in flight and every issued product
-  if (tid == 0)
+  if (tid == 0) {
     for (int s = 0; s < 4; ++s)
       if (pend & (1u << s)) tc::mbar_wait(bar(s), (par_ld >> s) & 1u, kWaitIters);
+    if (pend & 16u) tc::mbar_wait(bar(9), par_q, kWaitIters);
+  }
   if (issuer) {
     tc::commit(bar(8));
     tc::mbar_wait(bar(8), 0, kWaitIters);

@@ -91,6 +91,7 @@ struct TcStageParams {
   int* err = nullptr;            // set to 1 when a bounded wait expires
   const float* vgeo_il = nullptr;  // column-interleaved geometric factors (see aux_kernels.cu)
   const float* fgeo_il = nullptr;
+  int bulk_q = 0;  // fields may be loaded by bulk copies (16-byte aligned tiles, row stride = Np)
 };
 cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
 bool pack_tc_ops(int N, const RefOps& o, int fmt, std::vector<uint8_t>& out);
