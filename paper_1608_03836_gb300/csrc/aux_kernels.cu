@@ -124,28 +124,42 @@ __global__ void geo_pack_kernel(int64_t K, int Nq, int Nfq, const double* __rest
 }
 
 // Column-interleaved FP32 copies for the tensor-core stage, where one thread
-// owns one element and a warp owns 32 consecutive elements:
-//   vgeo_il[((k/128) * 11 + c) * Nq + q][k % 128],  fgeo_il[((k/128) * 3 + d) * 4 Nfq + qf][k % 128].
+// owns one element, a warp owns 32 consecutive elements and a thread reads
+// four consecutive points at once (one 16-byte load):
+//   vgeo_il[k/128][c][q/4][k % 128][q % 4]           (c < 11, q < 4 ceil(Nq/4)),
+//   fgeo_il[k/128][d * 4 + face][q/4][k % 128][q % 4] (q < 4 ceil(Nfq/4)),
+// zero in the padding (points beyond Nq or Nfq, elements beyond K).
 __global__ void geo_pack_il_kernel(int64_t K, int Nq, int Nfq, const double* __restrict__ J, const double* __restrict__ G,
                                    const double* __restrict__ c2, const double* __restrict__ nJ, float* __restrict__ vgeo,
                                    float* __restrict__ fgeo) {
-  const int64_t nv = K * 11 * Nq, nf = K * 12 * Nfq;
+  const int nq4 = (Nq + 3) / 4, nf4 = (Nfq + 3) / 4;
+  const int64_t Kt = (K + 127) / 128;
+  const int64_t nv = Kt * 11 * nq4 * 512, nf = Kt * 12 * nf4 * 512;
   for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nv + nf; it += (int64_t)gridDim.x * blockDim.x) {
-    if (it < nv) {
-      const int64_t k = it % K;
-      const int64_t r = it / K;  // c * Nq + q
-      const int c = (int)(r / Nq), q = (int)(r % Nq);
-      const double Jq = J[k * Nq + q];
-      double v;
-      if (c < 9) v = G[(k * 9 + c) * Nq + q];
-      else if (c == 9) v = (c2 ? c2[k * Nq + q] : 1.0) / Jq;
-      else v = 1.0 / Jq;
-      vgeo[(((k >> 7) * 11 * Nq) + r) * 128 + (k & 127)] = (float)v;
+    // it = (((kt * rows + row) * groups + g) * 128 + kl) * 4 + e
+    const bool vol = it < nv;
+    const int64_t j = vol ? it : it - nv;
+    const int e = (int)(j & 3), kl = (int)((j >> 2) & 127);
+    const int64_t rest = j >> 9;
+    const int groups = vol ? nq4 : nf4, rows = vol ? 11 : 12;
+    const int g = (int)(rest % groups);
+    const int row = (int)((rest / groups) % rows);
+    const int64_t kt = rest / groups / rows;
+    const int64_t k = kt * 128 + kl;
+    const int q = 4 * g + e;
+    float v = 0.f;  // padding: elements beyond K, points beyond Nq / Nfq
+    if (vol) {
+      if (k < K && q < Nq) {
+        const double Jq = J[k * Nq + q];
+        if (row < 9) v = (float)G[(k * 9 + row) * Nq + q];
+        else if (row == 9) v = (float)((c2 ? c2[k * Nq + q] : 1.0) / Jq);
+        else v = (float)(1.0 / Jq);
+      }
+      vgeo[j] = v;
     } else {
-      const int64_t j = it - nv;
-      const int64_t k = j % K;
-      const int64_t r = j / K;  // d * 4 Nfq + qf
-      fgeo[(((k >> 7) * 12 * Nfq) + r) * 128 + (k & 127)] = (float)nJ[k * 12 * Nfq + r];
+      // row = d * 4 + face
+      if (k < K && q < Nfq) v = (float)nJ[k * 12 * Nfq + row * Nfq + q];
+      fgeo[j] = v;
     }
   }
 }

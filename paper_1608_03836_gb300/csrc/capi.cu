@@ -579,8 +579,9 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
         m->tc_fmt = fmt;
       }
       const int64_t Kt = (K + 127) / 128;
-      if (!m->d_vgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_vgeo_il, (size_t)Kt * 128 * 11 * Nq * sizeof(float)));
-      if (!m->d_fgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_fgeo_il, (size_t)Kt * 128 * 12 * Nfq * sizeof(float)));
+      const int64_t nq4 = (Nq + 3) / 4, nf4 = (Nfq + 3) / 4;
+      if (!m->d_vgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_vgeo_il, (size_t)Kt * 128 * 11 * nq4 * 4 * sizeof(float)));
+      if (!m->d_fgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_fgeo_il, (size_t)Kt * 128 * 12 * nf4 * 4 * sizeof(float)));
       WADG_CUDA(m, launch_geo_pack_il(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, m->d_nJ, m->d_vgeo_il, m->d_fgeo_il, 0));
     }
   }

@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   using T = TcDims<N>;
   constexpr int NP = T::NP, NQ = T::NQ, NFP = T::NFP, NFQ = T::NFQ, KP = T::KP, QC = T::QC, NPS = T::NPS;
   constexpr int TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16, NCH = T::NCH;
+  constexpr int NQ4 = (NQ + 3) / 4, NF4 = (NFQ + 3) / 4;  // groups of four points in the interleaved geometry
   const StageParams<float>& p = P.s;
   const DevOps<float>& ops = p.ops;
 
@@ -378,17 +379,23 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     // accumulators in TMEM ----
     for (int f = 0; f < 4 && !failed; ++f) {
       const int pio = (int)((code4 >> (8 * f)) & 0xffu) % 6;
-      // normals x surface Jacobian at this thread's face points (8 per group), needed after the first products
+      // normals x surface Jacobian at this thread's face points (8 per group, two
+      // 16-byte loads per component), needed after the first products
       const int q0 = 8 * grp;
       float nv[3][8];
       {
-        const float* nfg = P.fgeo_il + ((km >> 7) * 12 * NFQ + f * NFQ) * 128 + (km & 127);
+        const float4* nfg = reinterpret_cast<const float4*>(P.fgeo_il) + (km >> 7) * 12 * NF4 * 128 + (km & 127);
 #pragma unroll
-        for (int qq = 0; qq < 8; ++qq) {
-          const int q = q0 + qq;
+        for (int dd = 0; dd < 3; ++dd)
 #pragma unroll
-          for (int dd = 0; dd < 3; ++dd) nv[dd][qq] = q < NFQ ? __ldg(nfg + (size_t)(dd * 4 * NFQ + q) * 128) : 0.f;
-        }
+          for (int h = 0; h < 2; ++h) {
+            const int g = 2 * grp + h;
+            const float4 v = g < NF4 ? __ldg(nfg + (size_t)((dd * 4 + f) * NF4 + g) * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
+            nv[dd][4 * h] = v.x;
+            nv[dd][4 * h + 1] = v.y;
+            nv[dd][4 * h + 2] = v.z;
+            nv[dd][4 * h + 3] = v.w;
+          }
       }
       // (i) [p], {u}, [u] at the face nodes, owner's node order -> split A
       // operands.  Sixteen lanes take the face nodes j of one column, so that
@@ -565,15 +572,18 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       }
     }
     for (int c = 0; c < NCH; ++c) {
-      // geometric factors at this thread's 4 quadrature points
+      // geometric factors at this thread's 4 quadrature points (one 16-byte load each)
       float G[9][4];
       {
-        const float* gk = P.vgeo_il + (km >> 7) * 11 * NQ * 128 + (km & 127);
+        const float4* gk = reinterpret_cast<const float4*>(P.vgeo_il) + (km >> 7) * 11 * NQ4 * 128 + (km & 127);
+        const int g = c * (QC / 4) + grp;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = c * QC + 4 * grp + j;
-#pragma unroll
-          for (int k = 0; k < 9; ++k) G[k][j] = q < NQ ? __ldg(gk + (size_t)(k * NQ + q) * 128) : 0.f;
+        for (int k = 0; k < 9; ++k) {
+          const float4 v = g < NQ4 ? __ldg(gk + (size_t)(k * NQ4 + g) * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
+          G[k][0] = v.x;
+          G[k][1] = v.y;
+          G[k][2] = v.z;
+          G[k][3] = v.w;
         }
       }
       wait_all(4 + (c & 1), (par_t1 >> (c & 1)) & 1u);
@@ -688,11 +698,16 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       // weights of field grp (c^2/J for p, 1/J for u) at the 16 points of the chunk
       float wt[16];
       {
-        const float* w = P.vgeo_il + ((km >> 7) * 11 + (grp == 0 ? 9 : 10)) * NQ * 128 + (km & 127);
+        const float4* w =
+            reinterpret_cast<const float4*>(P.vgeo_il) + ((km >> 7) * 11 + (grp == 0 ? 9 : 10)) * NQ4 * 128 + (km & 127);
 #pragma unroll
-        for (int ql = 0; ql < 16; ++ql) {
-          const int q = c * QC + ql;
-          wt[ql] = q < NQ ? __ldg(w + (size_t)q * 128) : 0.f;
+        for (int h = 0; h < 4; ++h) {
+          const int g = c * (QC / 4) + h;
+          const float4 v = g < NQ4 ? __ldg(w + (size_t)g * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
+          wt[4 * h] = v.x;
+          wt[4 * h + 1] = v.y;
+          wt[4 * h + 2] = v.z;
+          wt[4 * h + 3] = v.w;
         }
       }
       wait_all(4 + (c & 1), (par_t1 >> (c & 1)) & 1u);
