@@ -49,9 +49,17 @@ struct TcDims {
   static constexpr int B_P = KP * QC * 2;         // one part of a [KP x 16] operator chunk
   // packed operators per chunk: volume A part (V_q, V_q^a), volume B part
   // ((V_q^a)^T diag(w), V_q^T diag(w)), update A part (V_q M^^{-1}), update B part (P_q)
-  static constexpr int SZ_VA = 8 * B_V, SZ_VB = 8 * B_P, SZ_UA = 2 * B_V, SZ_UB = 2 * B_P;
+  // the update runs in chunks of 32 points (its four outputs per point fit
+  // twice in TMEM beside the r accumulators)
+  static constexpr int UQC = 32;
+  static constexpr int UNCH = (NQ + UQC - 1) / UQC;
+  static constexpr int A_UCH = TILE * UQC * 2;    // one part of a [128 x 32] update chunk array
+  static constexpr int B_UV = UQC * KP * 2;       // one part of a [32 x KP] operator chunk
+  static constexpr int B_UP = KP * UQC * 2;       // one part of a [KP x 32] operator chunk
+  static constexpr int SZ_VA = 8 * B_V, SZ_VB = 8 * B_P, SZ_UA = 2 * B_UV, SZ_UB = 2 * B_UP;
   static constexpr int SZ_OPV = SZ_VA + SZ_VB, SZ_OPU = SZ_UA + SZ_UB;
-  static constexpr int SZ_SLOT = SZ_VA > SZ_VB ? SZ_VA : SZ_VB;
+  static constexpr int SZ_OPS = NCH * SZ_OPV + UNCH * SZ_OPU;  // packed chunks before the face operators
+  static constexpr int SZ_SLOT = SZ_VA > SZ_VB ? (SZ_VA > SZ_UA ? SZ_VA : SZ_UA) : (SZ_VB > SZ_UA ? SZ_VB : SZ_UA);
   static constexpr int NFP16 = (NFP + 15) / 16 * 16, NFQ16 = (NFQ + 15) / 16 * 16;
   static constexpr int A_FN = TILE * NFP16 * 2;    // one part of a [128 x NFP16] face-node tile
   static constexpr int A_FQ = TILE * NFQ16 * 2;    // one part of a [128 x NFQ16] face-point tile
@@ -63,8 +71,9 @@ struct TcDims {
   static constexpr int OFF_SLOT = SZ_R0;
   static constexpr int OFF_AX = OFF_SLOT + 4 * SZ_SLOT;
   static constexpr int OFF_QS = OFF_AX;  // FP32 input tile: from the load to the split (before the volume)
-  static constexpr int END_AX = OFF_AX + SZ_AX, END_QS = OFF_QS + SZ_T32;
-  static constexpr int OFF_FT = ((END_AX > END_QS ? END_AX : END_QS) + 127) / 128 * 128;
+  static constexpr int END_AX = OFF_AX + SZ_AX, END_QS = OFF_QS + SZ_T32, END_UX = OFF_AX + 8 * A_UCH;
+  static constexpr int END_X = END_AX > END_QS ? (END_AX > END_UX ? END_AX : END_UX) : (END_QS > END_UX ? END_QS : END_UX);
+  static constexpr int OFF_FT = (END_X + 127) / 128 * 128;
   static constexpr int B_TRI = NFQ16 * NFP16 * 2;  // one part of V_tri [NFQ16 x NFP16] or of its lift
   static constexpr int SZ_FOPS = 4 * B_TRI;
   static constexpr int OFF_GI = OFF_FT + SZ_FOPS;
@@ -76,11 +85,13 @@ struct TcDims {
   static constexpr int OFF_BAR = OFF_NB + TILE * 20;
   static constexpr int SMEM = OFF_BAR + 128;
   // TMEM columns
-  static constexpr int T1 = 96;                    // chunk outputs, two buffers at 0 and T1
+  static constexpr int T1 = 96;                    // volume chunk outputs, two buffers at 0 and T1
+  static constexpr int T1U = 128;                  // update chunk outputs (4 x 32), two buffers at 0 and T1U
   static constexpr int TB = 320;                   // b accumulators b_p (a = r), b_u1..3 (4 x KP), then r
   static constexpr int TBX = 224;                  // b_p for a = s, t (2 x KP), summed into b_p
   static constexpr int TI = 0, TL = 7 * NFQ16;     // face interpolants (7 x NFQ16), lifted faces (4 x NFP16)
   static_assert(2 * T1 <= TBX && TBX + 2 * KP <= TB && TB + 4 * KP <= 512 && TL + 4 * NFP16 <= TB, "TMEM plan");
+  static_assert(2 * T1U <= TB && SZ_UA <= SZ_SLOT && SZ_UB <= SZ_SLOT, "update plan");
   static_assert(SMEM <= 232448, "shared memory");
 };
 
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     *sflag = 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), 512);
-  stage_copy(sFT, P.ops + (size_t)NCH * (T::SZ_OPV + T::SZ_OPU), T::SZ_FOPS);
+  stage_copy(sFT, P.ops + (size_t)T::SZ_OPS, T::SZ_FOPS);
   for (int i = tid; i < 4 * 6 * NP; i += kThreads) sGI[i] = ops.ginv[i];
   for (int i = tid; i < 4 * 6 * NFP; i += kThreads) sGX[i] = ops.gidx[i];
   tc::fence_before();
@@ -309,18 +320,18 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       OF::template chain<16>(mk_mma3(tmem + T::TB + KP * (i - 2), ax + (2 * i) * T::A_CH, ax + (2 * i + 1) * T::A_CH, sbo_16,
                             bvw, bvw + T::B_P, sbo_16, OF::idesc(128, KP), true));
   };
-  auto issue_U1 = [&](int c, int w) {  // (V_q M^^{-1}) b per field (N = 16)
-    const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1);
+  auto issue_U1 = [&](int c, int w) {  // (V_q M^^{-1}) b per field (N = 32)
+    const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1U);
     const int f = w - 8;
     if (f >= 0 && f < 4)
-      OF::template chain<KP>(mk_mma3(d + 16 * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP, sl,
-                                  sl + T::B_V, sbo_KP, OF::idesc(128, 16), false));
+      OF::template chain<KP>(mk_mma3(d + T::UQC * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP,
+                                     sl, sl + T::B_UV, sbo_KP, OF::idesc(128, T::UQC), false));
   };
-  auto issue_U2 = [&](int c, int f) {  // r += P_q (W ...) per field (N = KP)
-    const uint32_t sl = slot_addr(2 + (c & 1));
+  auto issue_U2 = [&](int c, int f) {  // r += P_q (W ...) per field (N = KP, K = 32)
+    const uint32_t sl = slot_addr(2 + (c & 1)), sbo_32 = OF::sbo(T::UQC);
     if (f < 4)
-      OF::template chain<16>(mk_mma3(tmem + T::TB + KP * f, ax + (2 * f) * T::A_CH, ax + (2 * f + 1) * T::A_CH, sbo_16, sl,
-                            sl + T::B_P, sbo_16, OF::idesc(128, KP), c > 0));
+      OF::template chain<T::UQC>(mk_mma3(tmem + T::TB + KP * f, ax + (2 * f) * T::A_UCH, ax + (2 * f + 1) * T::A_UCH,
+                                         sbo_32, sl, sl + T::B_UP, sbo_32, OF::idesc(128, KP), c > 0));
   };
 
   // fields of a tile by bulk copies (when the FP32 tile has the global row
@@ -648,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     if (tid == 0) {  // update operators of chunks 0 and 1
       load_slot(0, upd_ops, T::SZ_UA);
       load_slot(2, upd_ops + T::SZ_UA, T::SZ_UB);
-      if (NCH > 1) {
+      if (T::UNCH > 1) {
         load_slot(1, upd_ops + T::SZ_OPU, T::SZ_UA);
         load_slot(3, upd_ops + T::SZ_OPU + T::SZ_UA, T::SZ_UB);
       }
@@ -681,28 +692,30 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     sync_check();
     if (failed) break;
 
-    // ---- weight-adjusted update (Sec. 6.2, Eq. (matfree); Sec. 7), pipelined like the volume ----
+    // ---- weight-adjusted update (Sec. 6.2, Eq. (matfree); Sec. 7), pipelined
+    // like the volume, in chunks of 32 points ----
+    constexpr int UQC = T::UQC, UNCH = T::UNCH;
     wait_slot(0);
     if (issuer) {
       issue_U1(0, warp);
       tc::commit(bar(4));
     }
-    if (NCH > 1) {
+    if (UNCH > 1) {
       wait_slot(1);
       if (issuer) {
         issue_U1(1, warp);
         tc::commit(bar(5));
       }
     }
-    for (int c = 0; c < NCH; ++c) {
-      // weights of field grp (c^2/J for p, 1/J for u) at the 16 points of the chunk
-      float wt[16];
+    for (int c = 0; c < UNCH; ++c) {
+      // weights of field grp (c^2/J for p, 1/J for u) at the 32 points of the chunk
+      float wt[UQC];
       {
         const float4* w =
             reinterpret_cast<const float4*>(P.vgeo_il) + ((km >> 7) * 11 + (grp == 0 ? 9 : 10)) * NQ4 * 128 + (km & 127);
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int g = c * (QC / 4) + h;
+        for (int h = 0; h < UQC / 4; ++h) {
+          const int g = c * (UQC / 4) + h;
           const float4 v = g < NQ4 ? __ldg(w + (size_t)g * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
           wt[4 * h] = v.x;
           wt[4 * h + 1] = v.y;
@@ -712,31 +725,29 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       }
       wait_all(4 + (c & 1), (par_t1 >> (c & 1)) & 1u);
       par_t1 ^= 1u << (c & 1);
-      if (tid == 0 && c + 2 < NCH) load_slot(c & 1, upd_ops + (size_t)(c + 2) * T::SZ_OPU, T::SZ_UA);
-      float x[2][8];
+      if (tid == 0 && c + 2 < UNCH) load_slot(c & 1, upd_ops + (size_t)(c + 2) * T::SZ_OPU, T::SZ_UA);
+      float x[UQC / 8][8];
       {
-        const uint32_t t = lane_base + (uint32_t)((c & 1) * T::T1) + 16 * grp;
-        uint32_t v[2][8];
-        tc::tmem_ld8_nw(t, v[0]);
-        tc::tmem_ld8_nw(t + 8, v[1]);
-        tc::wait_ld();
-        tc::pin8(v[0]);
-        tc::pin8(v[1]);
+        const uint32_t t = lane_base + (uint32_t)((c & 1) * T::T1U) + UQC * grp;
+        uint32_t v[UQC / 8][8];
 #pragma unroll
-        for (int h8 = 0; h8 < 2; ++h8)
+        for (int h8 = 0; h8 < UQC / 8; ++h8) tc::tmem_ld8_nw(t + 8 * h8, v[h8]);
+        tc::wait_ld();
+#pragma unroll
+        for (int h8 = 0; h8 < UQC / 8; ++h8) {
+          tc::pin8(v[h8]);
 #pragma unroll
           for (int j = 0; j < 8; ++j) x[h8][j] = __uint_as_float(v[h8][j]) * wt[8 * h8 + j];
+        }
       }
       if (c > 0) {
         wait_all(6, par_m2);
         par_m2 ^= 1u;
-        if (tid == 0 && c + 1 < NCH)
+        if (tid == 0 && c + 1 < UNCH)
           load_slot(2 + ((c + 1) & 1), upd_ops + (size_t)(c + 1) * T::SZ_OPU + T::SZ_UA, T::SZ_UB);
       }
 #pragma unroll
-      for (int h8 = 0; h8 < 2; ++h8) {
-        OF::st8(sAX + (2 * grp) * T::A_CH, T::A_CH, mrow, 8 * h8, QC, x[h8]);
-      }
+      for (int h8 = 0; h8 < UQC / 8; ++h8) OF::st8(sAX + (2 * grp) * T::A_UCH, T::A_UCH, mrow, 8 * h8, UQC, x[h8]);
       sync_check();
       if (failed) break;
       wait_slot(2 + (c & 1));
@@ -744,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         issue_U2(c, warp);
         tc::commit(bar(6));
       }
-      if (c + 2 < NCH) {
+      if (c + 2 < UNCH) {
         wait_slot(c & 1);
         if (issuer) {
           issue_U1(c + 2, warp);
@@ -858,10 +869,10 @@ cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, in
 
 size_t tc_ops_bytes(int N) {
   switch (N) {
-    case 1: return (size_t)TcDims<1>::NCH * (TcDims<1>::SZ_OPV + TcDims<1>::SZ_OPU) + TcDims<1>::SZ_FOPS;
-    case 2: return (size_t)TcDims<2>::NCH * (TcDims<2>::SZ_OPV + TcDims<2>::SZ_OPU) + TcDims<2>::SZ_FOPS;
-    case 3: return (size_t)TcDims<3>::NCH * (TcDims<3>::SZ_OPV + TcDims<3>::SZ_OPU) + TcDims<3>::SZ_FOPS;
-    case 4: return (size_t)TcDims<4>::NCH * (TcDims<4>::SZ_OPV + TcDims<4>::SZ_OPU) + TcDims<4>::SZ_FOPS;
+    case 1: return (size_t)TcDims<1>::SZ_OPS + TcDims<1>::SZ_FOPS;
+    case 2: return (size_t)TcDims<2>::SZ_OPS + TcDims<2>::SZ_FOPS;
+    case 3: return (size_t)TcDims<3>::SZ_OPS + TcDims<3>::SZ_FOPS;
+    case 4: return (size_t)TcDims<4>::SZ_OPS + TcDims<4>::SZ_FOPS;
     default: return 0;
   }
 }
@@ -926,7 +937,7 @@ template <int N>
 void pack_n(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
   using T = TcDims<N>;
   const int Np = o.Np, Nq = o.Nq, KP = T::KP, QC = T::QC;
-  out.assign((size_t)T::NCH * (T::SZ_OPV + T::SZ_OPU) + T::SZ_FOPS, 0);
+  out.assign((size_t)T::SZ_OPS + T::SZ_FOPS, 0);
   for (int ch = 0; ch < T::NCH; ++ch) {
     uint8_t* v = out.data() + (size_t)ch * T::SZ_OPV;
     auto qn = [&](int r) { return ch * QC + r; };
@@ -947,12 +958,15 @@ void pack_n(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
       const int q = qn(k);
       return (q < Nq && n < Np) ? o.Vw[n * Nq + q] : 0.0;
     });
+  }
+  for (int ch = 0; ch < T::UNCH; ++ch) {
+    auto qn = [&](int r) { return ch * T::UQC + r; };
     uint8_t* u = out.data() + (size_t)T::NCH * T::SZ_OPV + (size_t)ch * T::SZ_OPU;
-    put_tile(fmt, u, T::B_V, QC, KP, [&](int r, int n) {
+    put_tile(fmt, u, T::B_UV, T::UQC, KP, [&](int r, int n) {
       const int q = qn(r);
       return (q < Nq && n < Np) ? o.Vtilde[q * Np + n] : 0.0;
     });
-    put_tile(fmt, u + 2 * T::B_V, T::B_P, KP, QC, [&](int n, int k) {
+    put_tile(fmt, u + 2 * T::B_UV, T::B_UP, KP, T::UQC, [&](int n, int k) {
       const int q = qn(k);
       return (q < Nq && n < Np) ? o.Pq[n * Nq + q] : 0.0;
     });
@@ -960,7 +974,7 @@ void pack_n(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
   // face operators: V_tri as [NFQ16 rows (q) x NFP16 (j)], the lift
   // V_tri^T diag(w_f) as [NFP16 rows (j) x NFQ16 (q)]
   const int Nfp = o.Nfp, Nfq = o.Nfq;
-  uint8_t* fo = out.data() + (size_t)T::NCH * (T::SZ_OPV + T::SZ_OPU);
+  uint8_t* fo = out.data() + (size_t)T::SZ_OPS;
   put_tile(fmt, fo, T::B_TRI, T::NFQ16, T::NFP16, [&](int q, int j) {
     return (q < Nfq && j < Nfp) ? o.Vtri[q * Nfp + j] : 0.0;
   });
