@@ -212,16 +212,19 @@ def batched_shots(W, steps):
     return out
 
 
-def uneven_batch(W, steps):
+def uneven_batch(W, steps, small=False):
     """12 meshes of uneven size and degree (n_i = 4 + round(12 i/11) hexes per
     side, N_i = 2 + (i mod 5)) stepped by one persistent launch per stage
-    (autotuned grid), against the same meshes stepped one after another."""
+    (autotuned grid), against the same meshes stepped one after another.
+    small=True: the same degrees on n_i = 2 + (i mod 4) (48 to 384 tets per
+    mesh), where the per-mesh launches dominate."""
     import torch
     from synthetic import warped_cube, random_fields
     ms, Qs, Rs = [], [], []
     dof = 0
     for i in range(12):
-        n, N = 4 + int(round(12 * i / 11)), 2 + (i % 5)
+        n = 2 + (i % 4) if small else 4 + int(round(12 * i / 11))
+        N = 2 + (i % 5)
         VXYZ, EToV, geom = warped_cube(n, N, 0.1)
         m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
         W.wadg_set_operators(m, "fp32", 1, 1.0, 1.0, None)
@@ -249,7 +252,8 @@ def uneven_batch(W, steps):
     torch.cuda.synchronize()
     t_seq = e0.elapsed_time(e1) / steps
     info = W.wadg_batch_info(b)
-    return {"workload": "12 warped cubes, n = 4..16, N = 2..6, FP32", "dof": dof, "items": info["items"],
+    return {"workload": "12 warped cubes, " + ("n = 2..5" if small else "n = 4..16") + ", N = 2..6, FP32",
+            "dof": dof, "items": info["items"],
             "grid": grid, "value": dof * 5 / (t_batch * 1e-3), "ms_per_step": t_batch,
             "sequential_ms_per_step": t_seq, "launches_per_step": 5, "sequential_launches_per_step": 60}
 
@@ -551,6 +555,7 @@ def main():
     if not args.no_extras:
         extras["batched_shots"] = batched_shots(W, max(2, args.steps // 3))
         extras["uneven_batch"] = uneven_batch(W, max(2, args.steps))
+        extras["uneven_batch_small"] = uneven_batch(W, max(2, args.steps), small=True)
         extras["accuracy"] = accuracy(W)
 
     if rank != 0:
