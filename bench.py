@@ -64,11 +64,17 @@ TC_PROFILE = "profiles/stage_tc_kernel_n20_full.md"
 
 
 def tc_source_hash() -> str:
+    """Hash of the kernel sources without their comments and blank lines (a
+    comment edit does not change the kernel the counters were taken on)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for rel in TC_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel)) as f:
+            for line in f:
+                code = re.sub(r"//.*$", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

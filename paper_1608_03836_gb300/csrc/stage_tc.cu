@@ -1,29 +1,33 @@
-// Fused WADG stage on the 5th-generation tensor cores (FP32 fields, products
-// in split bf16: x = hi + lo, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32
-// accumulation in TMEM).
+// Fused WADG stage on the 5th-generation tensor cores: FP32 fields, the dense
+// products as tcgen05.mma with FP32 accumulation in TMEM, operands either split
+// bf16 (x = hi + lo, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) or tf32.
 //
-// A persistent CTA (256 threads, one per SM) walks tiles of 128 columns
-// (element, shot).  A column is one MMA row (M = 128) and one TMEM lane; the
-// reference operators are the B operands (N = operator rows), streamed from
-// L2 in chunks of 16 volume quadrature points, pre-split and pre-laid-out in
-// the K-major no-swizzle core-matrix layout (see tc_ops.cuh).  Per tile:
-//   volume (Sec. 6.4): per chunk, u_i = V_q u_i and dp/dx^_a = V_q^a p (MMA),
-//     U^a = sum_i G_ai u_i and -(J grad p)_i (epilogue, one thread per column),
-//     b_p += sum_a (V_q^a)^T diag(w) U^a, b_ui -= V_q^T diag(w) (J grad p)_i
-//     (MMA, accumulated in TMEM over the chunks);
-//   surface (Sec. 6.4), face by face: the face-node combinations [p], {u},
-//     [u] are gathered in the owner's node order (CUDA cores), interpolated
-//     to the face points by V_tri (MMA), turned into the strong-weak flux with
-//     n J^f (epilogue), lifted by V_tri^T diag(w_f) (MMA) and added to a
-//     shared-memory accumulator at the volume nodes (epilogue);
-//   geometric factors are read from column-interleaved copies, so that the 32
-//   lanes of a warp (32 consecutive elements) read 128 contiguous bytes;
-//   update (Sec. 6.2, Eq. (matfree); Sec. 7): b is split into an A operand;
-//     per chunk, (V_q M^^{-1}) b (MMA), times W = c^2/J or 1/J (epilogue),
-//     P_q (...) accumulated in TMEM (MMA);
-//   epilogue: dQ/dt = r, or the LSRK update (Sec. 5.2).
-// Waits on the tensor cores are bounded; on expiry the CTA records an error
-// in p.err, frees its TMEM and returns.
+// A persistent CTA (512 threads, one per SM) walks tiles of 128 columns
+// (element, shot).  A column is one MMA row (M = 128) and one TMEM lane; four
+// threads share it (warps w, w + 4, w + 8, w + 12 own the lanes of quarter w),
+// each taking one field or a quarter of the points.  The reference operators
+// are the B operands (N = operator rows), packed on the host in the K-major
+// no-swizzle core-matrix layout (see tc_ops.cuh) and streamed from L2 into
+// four shared-memory slots by bulk asynchronous copies ahead of use.  Per tile:
+//   fields -> an FP32 tile (bulk copies issued during the previous tile);
+//   surface (Sec. 4.1, Sec. 6.4), face by face: 16 lanes gather the face nodes
+//     of one column ([p], {u}, [u] in the owner's node order), V_tri products
+//     to the face points, the strong-weak flux with n J^f on the CUDA cores,
+//     lift products, and the lifted values scattered to the volume nodes and
+//     summed in the b accumulators in TMEM;
+//   volume (Sec. 6.4), chunks of 16 points, software-pipelined: V_q u_i and
+//     V_q^a p of chunk c + 2 and the test products of chunk c run on the tensor
+//     cores while the CUDA cores form U^a = sum_i G_ai u_i and
+//     g_i = -sum_a G_ai dp/dx^_a of chunk c + 1;
+//   update (Sec. 6.2, Eq. (matfree); Sec. 7), chunks of 32 points: b -> V_q
+//     M^^{-1} b, times W = c^2/J or 1/J, P_q (...) accumulated in TMEM;
+//   epilogue: dQ/dt, or the LSRK update (Sec. 5.2), written coalesced.
+// Geometric factors come from copies interleaved over 128 elements in groups
+// of four points (one 16-byte load per four points).  Every tcgen05.mma holds
+// its issuing thread for 100-200 cycles, so lane 0 of every warp issues at
+// most one accumulator chain per step.  Waits on the tensor cores and the bulk
+// copies are bounded; on expiry the CTA records an error in P.err, drains its
+// copies and products, frees its TMEM and returns.
 #include <cstring>
 #include <vector>
 

@@ -21,7 +21,7 @@ def W():
     return lib
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16", "fp32_tf32"])
 def test_solve_graph_equals_steps(W, precision):
     """The captured graph replays exactly the launches of wadg_step: bitwise
     equal results, also on a second (replayed) call, with sources/receivers."""
