@@ -574,6 +574,23 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     // ---- volume terms (Sec. 6.4), chunks of 16 quadrature points, pipelined:
     // the products of chunk c + 2 and of chunk c run while the CUDA cores
     // work on chunk c + 1 ----
+    // geometric factors at this thread's 4 quadrature points of chunk c (one
+    // 16-byte load each), loaded before the products of the previous step are
+    // issued so that the issue time hides their latency
+    float G[9][4];
+    auto load_G = [&](int c) {
+      const float4* gk = reinterpret_cast<const float4*>(P.vgeo_il) + (km >> 7) * 11 * NQ4 * 128 + (km & 127);
+      const int g = c * (QC / 4) + grp;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const float4 v = g < NQ4 ? __ldg(gk + (size_t)(k * NQ4 + g) * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
+        G[k][0] = v.x;
+        G[k][1] = v.y;
+        G[k][2] = v.z;
+        G[k][3] = v.w;
+      }
+    };
+    load_G(0);
     wait_slot(0);
     if (issuer) {
       issue_V(0, warp);
@@ -587,20 +604,6 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       }
     }
     for (int c = 0; c < NCH; ++c) {
-      // geometric factors at this thread's 4 quadrature points (one 16-byte load each)
-      float G[9][4];
-      {
-        const float4* gk = reinterpret_cast<const float4*>(P.vgeo_il) + (km >> 7) * 11 * NQ4 * 128 + (km & 127);
-        const int g = c * (QC / 4) + grp;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          const float4 v = g < NQ4 ? __ldg(gk + (size_t)(k * NQ4 + g) * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
-          G[k][0] = v.x;
-          G[k][1] = v.y;
-          G[k][2] = v.z;
-          G[k][3] = v.w;
-        }
-      }
       wait_all(4 + (c & 1), (par_t1 >> (c & 1)) & 1u);
       par_t1 ^= 1u << (c & 1);
       if (tid == 0 && c + 2 < NCH) load_slot(c & 1, vol_ops + (size_t)(c + 2) * T::SZ_OPV, T::SZ_VA);
@@ -644,6 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       }
       sync_check();
       if (failed) break;
+      if (c + 1 < NCH) load_G(c + 1);
       wait_slot(2 + (c & 1));
       if (issuer) {
         issue_DW(c, warp);
@@ -699,6 +703,23 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     // ---- weight-adjusted update (Sec. 6.2, Eq. (matfree); Sec. 7), pipelined
     // like the volume, in chunks of 32 points ----
     constexpr int UQC = T::UQC, UNCH = T::UNCH;
+    // weights of field grp (c^2/J for p, 1/J for u) at the 32 points of chunk c,
+    // loaded ahead like the geometric factors of the volume
+    float wt[UQC];
+    auto load_W = [&](int c) {
+      const float4* w =
+          reinterpret_cast<const float4*>(P.vgeo_il) + ((km >> 7) * 11 + (grp == 0 ? 9 : 10)) * NQ4 * 128 + (km & 127);
+#pragma unroll
+      for (int h = 0; h < UQC / 4; ++h) {
+        const int g = c * (UQC / 4) + h;
+        const float4 v = g < NQ4 ? __ldg(w + (size_t)g * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
+        wt[4 * h] = v.x;
+        wt[4 * h + 1] = v.y;
+        wt[4 * h + 2] = v.z;
+        wt[4 * h + 3] = v.w;
+      }
+    };
+    load_W(0);
     wait_slot(0);
     if (issuer) {
       issue_U1(0, warp);
@@ -712,21 +733,6 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       }
     }
     for (int c = 0; c < UNCH; ++c) {
-      // weights of field grp (c^2/J for p, 1/J for u) at the 32 points of the chunk
-      float wt[UQC];
-      {
-        const float4* w =
-            reinterpret_cast<const float4*>(P.vgeo_il) + ((km >> 7) * 11 + (grp == 0 ? 9 : 10)) * NQ4 * 128 + (km & 127);
-#pragma unroll
-        for (int h = 0; h < UQC / 4; ++h) {
-          const int g = c * (UQC / 4) + h;
-          const float4 v = g < NQ4 ? __ldg(w + (size_t)g * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
-          wt[4 * h] = v.x;
-          wt[4 * h + 1] = v.y;
-          wt[4 * h + 2] = v.z;
-          wt[4 * h + 3] = v.w;
-        }
-      }
       wait_all(4 + (c & 1), (par_t1 >> (c & 1)) & 1u);
       par_t1 ^= 1u << (c & 1);
       if (tid == 0 && c + 2 < UNCH) load_slot(c & 1, upd_ops + (size_t)(c + 2) * T::SZ_OPU, T::SZ_UA);
@@ -754,6 +760,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       for (int h8 = 0; h8 < UQC / 8; ++h8) OF::st8(sAX + (2 * grp) * T::A_UCH, T::A_UCH, mrow, 8 * h8, UQC, x[h8]);
       sync_check();
       if (failed) break;
+      if (c + 1 < UNCH) load_W(c + 1);
       wait_slot(2 + (c & 1));
       if (issuer) {
         issue_U2(c, warp);
