@@ -392,26 +392,27 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     // ---- surface terms (Sec. 4.1, Sec. 6.4), face by face; the lifted terms
     // are gathered at this thread's volume nodes and summed in the b
     // accumulators in TMEM ----
+    // normals x surface Jacobian at this thread's face points of face f (8 per
+    // group, two 16-byte loads per component), loaded one face ahead
+    float nv[3][8];
+    auto load_nv = [&](int f) {
+      const float4* nfg = reinterpret_cast<const float4*>(P.fgeo_il) + (km >> 7) * 12 * NF4 * 128 + (km & 127);
+#pragma unroll
+      for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int g = 2 * grp + h;
+          const float4 v = g < NF4 ? __ldg(nfg + (size_t)((dd * 4 + f) * NF4 + g) * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
+          nv[dd][4 * h] = v.x;
+          nv[dd][4 * h + 1] = v.y;
+          nv[dd][4 * h + 2] = v.z;
+          nv[dd][4 * h + 3] = v.w;
+        }
+    };
+    load_nv(0);
     for (int f = 0; f < 4 && !failed; ++f) {
       const int pio = (int)((code4 >> (8 * f)) & 0xffu) % 6;
-      // normals x surface Jacobian at this thread's face points (8 per group, two
-      // 16-byte loads per component), needed after the first products
       const int q0 = 8 * grp;
-      float nv[3][8];
-      {
-        const float4* nfg = reinterpret_cast<const float4*>(P.fgeo_il) + (km >> 7) * 12 * NF4 * 128 + (km & 127);
-#pragma unroll
-        for (int dd = 0; dd < 3; ++dd)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int g = 2 * grp + h;
-            const float4 v = g < NF4 ? __ldg(nfg + (size_t)((dd * 4 + f) * NF4 + g) * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
-            nv[dd][4 * h] = v.x;
-            nv[dd][4 * h + 1] = v.y;
-            nv[dd][4 * h + 2] = v.z;
-            nv[dd][4 * h + 3] = v.w;
-          }
-      }
       // (i) [p], {u}, [u] at the face nodes, owner's node order -> split A
       // operands.  Sixteen lanes take the face nodes j of one column, so that
       // the neighbour's values come from a few sectors of its row.
@@ -502,6 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       }
       sync_check();
       if (failed) break;
+      if (f < 3) load_nv(f + 1);
       if (issuer) {
         const uint32_t bl = ft + 2 * T::B_TRI;
         const int fld = warp - 8;
