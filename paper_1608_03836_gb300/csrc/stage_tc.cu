@@ -409,9 +409,56 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
           nv[dd][4 * h + 3] = v.w;
         }
     };
+    // (iii) lifted values of field grp of face f (owner's node order) -> this
+    // thread's scratch -> volume nodes; run while the next face's first
+    // products execute (the lift outputs, the interpolants and the b
+    // accumulators occupy disjoint TMEM columns)
+    auto scatter = [&](int f) {
+      const int pio = (int)((code4 >> (8 * f)) & 0xffu) % 6;
+      {
+        uint32_t L[NFP16 / 8][8];
+#pragma unroll
+        for (int j8 = 0; j8 < NFP16 / 8; ++j8) tc::tmem_ld8_nw(lane_base + T::TL + grp * NFP16 + 8 * j8, L[j8]);
+        tc::wait_ld();
+#pragma unroll
+        for (int j8 = 0; j8 < NFP16 / 8; ++j8) tc::pin8(L[j8]);
+#pragma unroll
+        for (int j = 0; j < NFP; ++j) sLS[(grp * NFP16 + j) * TILE + mrow] = __uint_as_float(L[j >> 3][j & 7]);
+        // add to this field's b accumulator (the first face initialises it)
+        const int16_t* gi = sGI + (f * 6 + pio) * NP;
+        const uint32_t tb = lane_base + T::TB + KP * grp;
+        uint32_t acc[KP / 8][8];
+        if (f > 0) {
+#pragma unroll
+          for (int n8 = 0; n8 < KP / 8; ++n8) tc::tmem_ld8_nw(tb + 8 * n8, acc[n8]);
+          tc::wait_ld();
+#pragma unroll
+          for (int n8 = 0; n8 < KP / 8; ++n8) tc::pin8(acc[n8]);
+        } else {
+#pragma unroll
+          for (int n8 = 0; n8 < KP / 8; ++n8)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[n8][j] = 0u;
+        }
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          const int jj = gi[n];
+          if (jj >= 0)
+            acc[n >> 3][n & 7] =
+                __float_as_uint(__uint_as_float(acc[n >> 3][n & 7]) + sLS[(grp * NFP16 + jj) * TILE + mrow]);
+        }
+#pragma unroll
+        for (int n8 = 0; n8 < KP / 8; ++n8) {
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(acc[n8][j]);
+          tc::tmem_st8(tb + 8 * n8, v);
+        }
+        tc::wait_st();
+      }
+    };
     load_nv(0);
     for (int f = 0; f < 4 && !failed; ++f) {
-      const int pio = (int)((code4 >> (8 * f)) & 0xffu) % 6;
       const int q0 = 8 * grp;
       // (i) [p], {u}, [u] at the face nodes, owner's node order -> split A
       // operands.  Sixteen lanes take the face nodes j of one column, so that
@@ -463,6 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
                                          OF::sbo(NFP16), OF::idesc(128, NFQ16), false));
         tc::commit(bar(7));
       }
+      if (f > 0) scatter(f - 1);
       wait_all(7, par_f);
       par_f ^= 1u;
       // (ii) strong-weak flux (Sec. 4.1) at this thread's face points -> split A operands
@@ -515,50 +563,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       }
       wait_all(7, par_f);
       par_f ^= 1u;
-      // (iii) lifted values of field grp (owner's node order) -> this thread's scratch -> volume nodes
-      {
-        uint32_t L[NFP16 / 8][8];
-#pragma unroll
-        for (int j8 = 0; j8 < NFP16 / 8; ++j8) tc::tmem_ld8_nw(lane_base + T::TL + grp * NFP16 + 8 * j8, L[j8]);
-        tc::wait_ld();
-#pragma unroll
-        for (int j8 = 0; j8 < NFP16 / 8; ++j8) tc::pin8(L[j8]);
-#pragma unroll
-        for (int j = 0; j < NFP; ++j) sLS[(grp * NFP16 + j) * TILE + mrow] = __uint_as_float(L[j >> 3][j & 7]);
-        // add to this field's b accumulator (the first face initialises it)
-        const int16_t* gi = sGI + (f * 6 + pio) * NP;
-        const uint32_t tb = lane_base + T::TB + KP * grp;
-        uint32_t acc[KP / 8][8];
-        if (f > 0) {
-#pragma unroll
-          for (int n8 = 0; n8 < KP / 8; ++n8) tc::tmem_ld8_nw(tb + 8 * n8, acc[n8]);
-          tc::wait_ld();
-#pragma unroll
-          for (int n8 = 0; n8 < KP / 8; ++n8) tc::pin8(acc[n8]);
-        } else {
-#pragma unroll
-          for (int n8 = 0; n8 < KP / 8; ++n8)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[n8][j] = 0u;
-        }
-#pragma unroll
-        for (int n = 0; n < NP; ++n) {
-          const int jj = gi[n];
-          if (jj >= 0)
-            acc[n >> 3][n & 7] =
-                __float_as_uint(__uint_as_float(acc[n >> 3][n & 7]) + sLS[(grp * NFP16 + jj) * TILE + mrow]);
-        }
-#pragma unroll
-        for (int n8 = 0; n8 < KP / 8; ++n8) {
-          float v[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(acc[n8][j]);
-          tc::tmem_st8(tb + 8 * n8, v);
-        }
-        tc::wait_st();
-      }
     }
     if (failed) break;
+    scatter(3);
 
     // ---- field grp -> split A operand (over the lifted-value scratch: every
     // thread has finished with it) ----
