@@ -346,22 +346,20 @@ def c2_study(W):
 
 
 def e2e_steps(W, m, Q, steps):
-    """Same metric end to end: pinned host Q, res -> device, one step, -> host."""
+    """Same metric end to end through the C ABI with host buffers: every step
+    one wadg_step_host call (pinned host Q and res copied to the device, one
+    LSRK step, both copied back; the call returns when the copies are done)."""
     import torch
     Qh = Q.cpu().pin_memory()
     Rh = torch.zeros_like(Qh).pin_memory()
-    Qd, Rd = torch.empty_like(Q), torch.empty_like(Q)
     dt = dt_for(m)
     stream = torch.cuda.current_stream()
+    W.wadg_step_host(m, Qh, Rh, 0.0, dt, 1)  # warm-up (allocates the library's device copies)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(stream)
     for _ in range(steps):
-        Qd.copy_(Qh, non_blocking=True)
-        Rd.copy_(Rh, non_blocking=True)
-        W.wadg_step(m, Qd, Rd, 0.0, dt, 1)
-        Qh.copy_(Qd, non_blocking=True)
-        Rh.copy_(Rd, non_blocking=True)
+        W.wadg_step_host(m, Qh, Rh, 0.0, dt, 1)
     b.record(stream)
     torch.cuda.synchronize()
     nbytes = 2 * Q.numel() * Q.element_size()

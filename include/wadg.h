@@ -151,6 +151,12 @@ int wadg_rhs(wadg_mesh* mesh, const void* Q, void* dQdt, wadg_stream stream);
 int wadg_step(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nsteps, void* traces,
               wadg_stream stream);
 
+/* wadg_step on host fields: Q and res are HOST [4][K][S][Np] arrays in the
+ * mesh precision (pinned memory gives the fastest copies), copied to device
+ * buffers owned by the mesh, stepped nsteps times, and copied back before the
+ * call returns (the call waits for the stream).  No receiver traces. */
+int wadg_step_host(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nsteps, wadg_stream stream);
+
 /* Solve from t0 to t0 + T (Sec. 5.2 time stepping): nsteps = ceil(T/dt_max)
  * LSRK(5,4) steps of dt = T/nsteps, exactly the launches of wadg_step.  All
  * launches of the solve are captured once into a CUDA graph on a library

@@ -45,6 +45,7 @@ from .api import (  # noqa: E402,F401
     wadg_solve,
     wadg_status_string,
     wadg_step,
+    wadg_step_host,
     wadg_step_adjoint,
     wadg_step_record,
     wadg_version,

@@ -162,6 +162,18 @@ def wadg_step(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, trace
            "wadg_step", mesh)
 
 
+def wadg_step_host(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, stream=None):
+    """wadg_step on host tensors (CPU, contiguous, the mesh precision; pinned
+    memory gives the fastest copies): copied in, stepped, copied back."""
+    import torch
+    shape = tuple(mesh.field_shape())
+    for name, x in (("Q", Q), ("res", res)):
+        if x.is_cuda or x.dtype != mesh.dtype or tuple(x.shape) != shape or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU tensor {shape} of {mesh.dtype}")
+    _check(load().wadg_step_host(mesh.handle, ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(res.data_ptr()),
+                                 float(t0), float(dt), int(nsteps), _stream(stream)), "wadg_step_host", mesh)
+
+
 def wadg_solve(mesh: MeshHandle, Q, res, t0: float, T: float, dt_max: float, traces=None, stream=None) -> int:
     """Solve to t0 + T with a captured CUDA graph; returns the number of steps."""
     a = _check_field(mesh, Q, "Q")

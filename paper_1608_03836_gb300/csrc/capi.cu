@@ -314,6 +314,8 @@ void wadg_mesh_destroy(wadg_mesh* m) {
   dfree(m->d_red);
   dfree(m->d_tcops);
   dfree(m->d_vgeo_il);
+  dfree(m->d_hostQ);
+  dfree(m->d_hostR);
   dfree(m->d_fgeo_il);
   dfree(m->d_err);
   dfree(m->d_src_elem);
@@ -744,6 +746,33 @@ int wadg_step(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps
                                    : step_t<float>(m, Q, res, t0, dt, nsteps, traces, s);
 }
 
+int wadg_step_host(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!Q || !res || Q == res) return fail(m, WADG_EINVAL, "Q and res must be distinct host pointers");
+  if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "nsteps/dt/t0");
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)4 * m->K * m->S * m->ref.Np * tsize(m->precision);
+  if (bytes != m->host_io_bytes) {
+    dfree(m->d_hostQ);
+    dfree(m->d_hostR);
+    m->host_io_bytes = 0;
+    WADG_CUDA(m, cudaMalloc(&m->d_hostQ, bytes));
+    WADG_CUDA(m, cudaMalloc(&m->d_hostR, bytes));
+    m->host_io_bytes = bytes;
+  }
+  WADG_CUDA(m, cudaMemcpyAsync(m->d_hostQ, Q, bytes, cudaMemcpyHostToDevice, s));
+  WADG_CUDA(m, cudaMemcpyAsync(m->d_hostR, res, bytes, cudaMemcpyHostToDevice, s));
+  st = m->precision == WADG_FP64 ? step_t<double>(m, m->d_hostQ, m->d_hostR, t0, dt, nsteps, nullptr, s)
+                                 : step_t<float>(m, m->d_hostQ, m->d_hostR, t0, dt, nsteps, nullptr, s);
+  if (st != WADG_OK) return st;
+  WADG_CUDA(m, cudaMemcpyAsync(Q, m->d_hostQ, bytes, cudaMemcpyDeviceToHost, s));
+  WADG_CUDA(m, cudaMemcpyAsync(res, m->d_hostR, bytes, cudaMemcpyDeviceToHost, s));
+  WADG_CUDA(m, cudaStreamSynchronize(s));
+  return WADG_OK;
+}
+
 int wadg_project(wadg_mesh* m, const double* fq, void* Q, wadg_stream stream) {
   int st = check_ready(m);
   if (st != WADG_OK) return st;
@@ -1083,7 +1112,8 @@ extern "C" int wadg_device_status(wadg_mesh* m, wadg_stream stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "device status");
   if (flag) {
-    cudaMemset(m->d_err, 0, sizeof(int));
+    cudaMemsetAsync(m->d_err, 0, sizeof(int), (cudaStream_t)stream);
+    cudaStreamSynchronize((cudaStream_t)stream);
     return fail(m, WADG_ETIMEOUT, "a bounded wait in a tensor-core kernel expired");
   }
   return WADG_OK;

@@ -146,6 +146,9 @@ struct wadg_mesh {
   wadg::DevOps<float> ops32;
   uint8_t* d_tcops = nullptr;  // operators of the tensor-core stage (split bf16 or tf32)
   int tc_fmt = -1;             // format of d_tcops: 0 split bf16, 1 tf32
+  void* d_hostQ = nullptr;     // device copies for wadg_step_host
+  void* d_hostR = nullptr;
+  size_t host_io_bytes = 0;
   float* d_vgeo_il = nullptr;  // column-interleaved geometry for the tensor-core stage
   float* d_fgeo_il = nullptr;
   int* d_err = nullptr;        // device error flag (bounded waits)

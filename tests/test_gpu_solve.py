@@ -68,3 +68,18 @@ def test_c0_standing_wave_matches_oracle_solve(W, precision):
     want = g["wadg"]["l2_error_p_volume_rule"]
     tol = 1e-9 if precision == "fp64" else 0.05
     assert abs(err - want) < tol * want, (err, want)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
+def test_step_host_equals_step(W, precision):
+    """wadg_step_host on pinned host tensors gives exactly wadg_step's result."""
+    import torch
+    VXYZ, EToV, geom = make_mesh_inputs(2, 3)
+    m = library_mesh(VXYZ, EToV, geom, 3, precision, shots=2, c2="heterogeneous")
+    Q0 = to_torch(random_Q(m.K, 2, m.Np, 12), m.dtype)
+    Qd, Rd = Q0.clone(), torch.zeros_like(Q0)
+    W.wadg_step(m, Qd, Rd, 0.0, 0.003, 4)
+    Qh, Rh = Q0.cpu().pin_memory(), torch.zeros_like(Q0).cpu().pin_memory()
+    W.wadg_step_host(m, Qh, Rh, 0.0, 0.003, 4)
+    torch.cuda.synchronize()
+    assert torch.equal(Qh, Qd.cpu()) and torch.equal(Rh, Rd.cpu())
