@@ -100,6 +100,40 @@ def a_h(mesh: Mesh, c: np.ndarray, tau_p=1.0, tau_u=1.0) -> np.ndarray:
     return out
 
 
+def a_h_strong(mesh: Mesh, c: np.ndarray, tau_p=1.0, tau_u=1.0) -> np.ndarray:
+    """Strong right-hand side functional (Sec. 4.1, the strong DG form), modal
+    (4, K, Np): both equations integrated by parts twice,
+
+        p:  -int (div u) v - int_dD 1/2 ([u].n - tau_p [p]) v,
+        u:  -int grad p . tau - int_dD 1/2 ([p] - tau_u [u].n) tau.n,
+
+    with J div u = sum_{a,i} G_ai du_i/dx^_a at the volume points.  With rules
+    exact for the volume (degree 4N-3) and surface (4N-2) integrands it equals
+    the strong-weak functional a_h (discrete integration by parts)."""
+    ref = mesh.ref
+    w = ref.w_q
+    p, u = c[0], c[1:]
+    du = np.einsum("aqm,ikm->aikq", ref.Vq_a, u)               # (3 a, 3 i, K, Nq): du_i/dx^_a
+    dpq = np.einsum("aqm,km->akq", ref.Vq_a, p)
+    G = mesh.G                                                 # (K, Nq, a, i)
+    jdiv = np.einsum("kqai,aikq->kq", G, du)                   # J div u
+    gp = np.einsum("kqai,akq->ikq", G, dpq)                    # J grad p
+    out = np.zeros_like(c)
+    out[0] = -np.einsum("qm,kq->km", ref.Vq, w * jdiv)
+    out[1:] = -np.einsum("qm,ikq->ikm", ref.Vq, w * gp)
+    minus, plus = traces(mesh, c)
+    nJ = np.moveaxis(mesh.nJ, -1, 0)
+    jp = plus[0] - minus[0]
+    ju_nJ = np.sum((plus[1:] - minus[1:]) * nJ, axis=0)        # [u].n J^f
+    F = np.empty_like(minus)
+    F[0] = -0.5 * (ju_nJ - tau_p * jp * mesh.Jf)
+    F[1:] = -0.5 * (jp - tau_u * ju_nJ / mesh.Jf) * nJ
+    for (f, sig), ks in mesh.face_groups.items():
+        V = mesh.face_V[(f, sig)]
+        out[:, ks] += np.einsum("fkp,pm->fkm", F[:, ks, f] * ref.w_f, V)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Mass inverses.
 # ---------------------------------------------------------------------------
@@ -170,9 +204,12 @@ def exact_mass_inverse(mesh: Mesh, r: np.ndarray, c2fun=None, qpts=None) -> np.n
 
 
 def rhs(mesh: Mesh, c: np.ndarray, variant: str = "wadg", tau_p=1.0, tau_u=1.0,
-        c2q=None, c2fun=None) -> np.ndarray:
-    """dQ/dt = -M^{-1} A_h Q in modal coefficients (sign folded into a_h)."""
-    r = a_h(mesh, c, tau_p, tau_u)
+        c2q=None, c2fun=None, form: str = "strong_weak") -> np.ndarray:
+    """dQ/dt = -M^{-1} A_h Q in modal coefficients (sign folded into a_h);
+    form "strong_weak" (default) or "strong"."""
+    if form not in ("strong_weak", "strong"):
+        raise ValueError(form)
+    r = (a_h if form == "strong_weak" else a_h_strong)(mesh, c, tau_p, tau_u)
     if variant == "wadg":
         return wadg_apply(mesh, r, c2q)
     if variant == "exact":
