@@ -151,6 +151,17 @@ int wadg_rhs(wadg_mesh* mesh, const void* Q, void* dQdt, wadg_stream stream);
 int wadg_step(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nsteps, void* traces,
               wadg_stream stream);
 
+/* Formulation of the stage (Sec. 4.1): 0 = strong-weak (the default; the
+ * pressure equation integrated by parts once), 1 = strong (both equations
+ * integrated by parts twice: volume term -int (div u) v, surface term
+ * -int 1/2 ([u].n - tau_p [p]) v), evaluated with the same degree 2N+1 rules
+ * (under-integrated on curved elements, where it differs from the
+ * strong-weak form; with exact rules the two agree).  The strong form is
+ * built for the CUDA-core precisions and N <= 5, for wadg_rhs, wadg_step,
+ * wadg_step_host and wadg_solve; the adjoint and batches require form 0.
+ * WADG_EUNSUPPORTED otherwise. */
+int wadg_set_formulation(wadg_mesh* mesh, int form);
+
 /* wadg_step on host fields: Q and res are HOST [4][K][S][Np] arrays in the
  * mesh precision (pinned memory gives the fastest copies), copied to device
  * buffers owned by the mesh, stepped nsteps times, and copied back before the

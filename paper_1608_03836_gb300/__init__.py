@@ -46,6 +46,8 @@ from .api import (  # noqa: E402,F401
     wadg_status_string,
     wadg_step,
     wadg_step_host,
+    wadg_set_formulation,
+    FORMULATIONS,
     wadg_step_adjoint,
     wadg_step_record,
     wadg_version,

@@ -162,6 +162,14 @@ def wadg_step(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, trace
            "wadg_step", mesh)
 
 
+FORMULATIONS = {"strong_weak": 0, "strong": 1}
+
+
+def wadg_set_formulation(mesh: MeshHandle, form: str):
+    """'strong_weak' (default) or 'strong' (see include/wadg.h)."""
+    _check(load().wadg_set_formulation(mesh.handle, FORMULATIONS[form]), "wadg_set_formulation", mesh)
+
+
 def wadg_step_host(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, stream=None):
     """wadg_step on host tensors (CPU, contiguous, the mesh precision; pinned
     memory gives the fastest copies): copied in, stepped, copied back."""

@@ -155,7 +155,8 @@ int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
   if (!b) return WADG_ENOMEM;
   b->meshes.assign(meshes, meshes + count);
   for (int i = 0; i < count; ++i) {
-    if (!meshes[i] || meshes[i]->precision != WADG_FP32 || meshes[i]->device != meshes[0]->device) {
+    if (!meshes[i] || meshes[i]->precision != WADG_FP32 || meshes[i]->form != 0 ||
+        meshes[i]->device != meshes[0]->device) {
       delete b;
       return WADG_ESTATE;
     }

@@ -535,6 +535,8 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
     return fail(m, WADG_EUNSUPPORTED, "precision %d is not built", precision);
   const bool tensor = precision == WADG_FP32_3XBF16 || precision == WADG_FP32_TF32;
   if (tensor && m->N > 4) return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 4");
+  if (tensor && m->form != 0)
+    return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage is built for the strong-weak formulation");
   if (shots < 1 || shots > (1 << 20)) return fail(m, WADG_EINVAL, "shots=%d", shots);
   if (tensor && (int64_t)m->K * shots * m->ref.Np >= ((int64_t)1 << 31))
     return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage needs K * shots * Np < 2^31 (31-bit gather offsets)");
@@ -642,9 +644,15 @@ StageParams<T> base_params(const wadg_mesh* m) {
 // Stage launch for the mesh's precision: RHS and LSRK stages of
 // WADG_FP32_3XBF16 and WADG_FP32_TF32 run on the tensor cores, everything
 // else on CUDA cores.
+// The strong formulation runs the RHS and LSRK stages as their strong modes.
+inline int stage_mode(const wadg_mesh* m, int mode) {
+  if (m->form == 0) return mode;
+  return mode == kRhs ? kRhsStrong : (mode == kLsrk ? kLsrkStrong : -1);
+}
+
 template <typename T>
 cudaError_t stage_launch(const wadg_mesh* m, const StageParams<T>& p, int mode, cudaStream_t st) {
-  return launch_stage<T>(m->N, p, mode, st);
+  return launch_stage<T>(m->N, p, stage_mode(m, mode), st);
 }
 template <>
 cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p, int mode, cudaStream_t st) {
@@ -658,7 +666,7 @@ cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p,
     P.bulk_q = (p.ncols * m->ref.Np) % 4 == 0 && ((uintptr_t)p.Qin & 15) == 0;
     return launch_stage_tc(m->N, P, mode, m->tc_fmt, m->num_sms, st);
   }
-  return launch_stage<float>(m->N, p, mode, st);
+  return launch_stage<float>(m->N, p, stage_mode(m, mode), st);
 }
 
 int check_ready(wadg_mesh* m) {
@@ -744,6 +752,19 @@ int wadg_step(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps
   cudaStream_t s = (cudaStream_t)stream;
   return m->precision == WADG_FP64 ? step_t<double>(m, Q, res, t0, dt, nsteps, traces, s)
                                    : step_t<float>(m, Q, res, t0, dt, nsteps, traces, s);
+}
+
+int wadg_set_formulation(wadg_mesh* m, int form) {
+  if (!m) return WADG_EINVAL;
+  if (form != 0 && form != 1) return fail(m, WADG_EINVAL, "formulation %d (0 strong-weak, 1 strong)", form);
+  if (form == 1 && m->N > 5) return fail(m, WADG_EUNSUPPORTED, "the strong formulation is built for N <= 5");
+  if (form == 1 && (m->precision == WADG_FP32_3XBF16 || m->precision == WADG_FP32_TF32))
+    return fail(m, WADG_EUNSUPPORTED, "the strong formulation runs on the CUDA-core precisions (FP64, FP32)");
+  if (form != m->form) {
+    m->form = form;
+    ++m->generation;  // a captured solve graph holds the other formulation's kernels
+  }
+  return WADG_OK;
 }
 
 int wadg_step_host(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, wadg_stream stream) {
@@ -985,6 +1006,7 @@ extern "C" {
 int wadg_rhs_adjoint(wadg_mesh* m, const void* lam, void* out, wadg_stream stream) {
   int st = check_ready(m);
   if (st != WADG_OK) return st;
+  if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
   if (!lam || !out || lam == out || !aligned16(lam) || !aligned16(out))
     return fail(m, WADG_EINVAL, "lambda and out must be distinct 16-byte aligned device pointers");
   DeviceGuard g(m->device);
@@ -996,6 +1018,7 @@ int wadg_step_record(wadg_mesh* m, void* Q, void* res, double t0, double dt, voi
                      wadg_stream stream) {
   int st = check_ready(m);
   if (st != WADG_OK) return st;
+  if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
   if (!Q || !res || Q == res || !aligned16(Q) || !aligned16(res))
     return fail(m, WADG_EINVAL, "Q and res must be distinct 16-byte aligned device pointers");
   if (!std::isfinite(dt) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "dt/t0");
@@ -1009,6 +1032,7 @@ int wadg_step_adjoint(wadg_mesh* m, void* lamQ, void* lamR, double dt, const voi
                       wadg_stream stream) {
   int st = check_ready(m);
   if (st != WADG_OK) return st;
+  if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
   if (!lamQ || !lamR || lamQ == lamR || !aligned16(lamQ) || !aligned16(lamR))
     return fail(m, WADG_EINVAL, "lambda_Q and lambda_res must be distinct 16-byte aligned device pointers");
   if ((dc2 != nullptr) != (ystore != nullptr)) return fail(m, WADG_EINVAL, "ystore and dc2 go together");

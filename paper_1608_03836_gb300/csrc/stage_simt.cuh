@@ -71,7 +71,7 @@ constexpr int cols_per_block() {
 
 constexpr int kStageThreads = 256;
 
-enum StageMode { kRhs = 0, kLsrk = 1, kRecord = 2, kAdjLsrk = 3, kAdjRhs = 4 };
+// (StageMode: see wadg_internal.h)
 
 // Vector loads: R consecutive operator rows through the read-only path, and
 // 4 consecutive columns from shared memory.
@@ -138,6 +138,9 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
   constexpr int NQP = Dm::NQP, NPP = Dm::NPP, NFQP = Dm::NFQP, NFPP = Dm::NFPP;
   constexpr int NG = E / 4;
   constexpr int NT = kStageThreads;
+  constexpr bool ADJ = MODE == kAdjLsrk || MODE == kAdjRhs;
+  constexpr bool STRONG = MODE == kRhsStrong || MODE == kLsrkStrong;
+  constexpr bool RHS_OUT = MODE == kRhs || MODE == kRhsStrong;
 
   T* sQ = reinterpret_cast<T*>(smem_raw);  // [4][NP][E]
   T* sR = sQ + 4 * NP * E;                 // [4][NP][E]  load vector b (un-inverted)
@@ -164,6 +167,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
   }
   __syncthreads();
 
+  if constexpr (!STRONG) {
   // ---- 1a. volume: values at quadrature points (6 products, 4 rows x 4 cols) ----
   {
     constexpr int RG = NQP / 4;
@@ -221,7 +225,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
       tile_dot<T, E, 2, NPP, NQ>(A, sX + job * NQ * E + g * 4, m0, acc);
       T* out = job == 0 ? sR : (job < 3 ? sP + (job - 1) * NP * E : sR + (job - 2) * NP * E);
       T sgn = job < 3 ? T(1) : T(-1);
-      if (MODE >= kAdjLsrk) sgn = -sgn;  // the volume operator is skew
+      if (ADJ) sgn = -sgn;  // the volume operator is skew
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
 #pragma unroll
@@ -231,6 +235,73 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
     }
   }
   __syncthreads();
+  } else {
+    // ---- 1a-1b (strong form): J div u = sum_{a,i} G_ai du_i/dx^_a and J grad p
+    // at the quadrature points, one field u_i at a time (scratch arrays 0-2:
+    // du_i/dx^_a, 3-5: dp/dx^_a then J grad p, 6: -J div u) ----
+    static_assert(7 * NQ <= Dm::XS, "strong-form scratch");
+    for (int i = 0; i < 3; ++i) {
+      {
+        constexpr int RG = NQP / 4;
+        const int njobs = i == 0 ? 6 : 3;
+        for (int it = tid; it < njobs * RG * NG; it += NT) {
+          const int g = it % NG;
+          const int m0 = ((it / NG) % RG) * 4;
+          const int job = it / (RG * NG);  // 0-2: du_i/dx^_a, 3-5: dp/dx^_a
+          const T* A = ops.VaT + (job % 3) * NP * NQP;
+          const T* in = (job < 3 ? sQ + (1 + i) * NP * E : sQ) + g * 4;
+          T acc[4][4];
+          tile_dot<T, E, 4, NQP, NP>(A, in, m0, acc);
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (m0 + r < NQ) sts_cols(sX + (job * NQ + m0 + r) * E + g * 4, acc[r]);
+        }
+      }
+      __syncthreads();
+      for (int it = tid; it < NQ * E; it += NT) {
+        const int q = it % NQ;
+        const int e = it / NQ;
+        int64_t c = col0 + e;
+        c = c < ncols ? c : ncols - 1;
+        const int64_t k = c / S;
+        const T* gk = p.vgeo + k * 11 * NQ + q;
+        T sdiv = i == 0 ? T(0) : sX[(6 * NQ + q) * E + e];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sdiv -= __ldg(gk + (a * 3 + i) * NQ) * sX[(a * NQ + q) * E + e];
+        sX[(6 * NQ + q) * E + e] = sdiv;
+        if (i == 0) {
+          T G[9], d[3];
+#pragma unroll
+          for (int j = 0; j < 9; ++j) G[j] = __ldg(gk + j * NQ);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) d[j] = sX[((3 + j) * NQ + q) * E + e];
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            sX[((3 + j) * NQ + q) * E + e] = G[0 * 3 + j] * d[0] + G[1 * 3 + j] * d[1] + G[2 * 3 + j] * d[2];
+        }
+      }
+      __syncthreads();
+    }
+    // ---- 1c (strong form): b_p = V_q^T diag(w) (-J div u), b_ui = -V_q^T diag(w) (J grad p)_i ----
+    {
+      constexpr int RG = NPP / 2;
+      for (int it = tid; it < 4 * RG * NG; it += NT) {
+        const int g = it % NG;
+        const int m0 = ((it / NG) % RG) * 2;
+        const int job = it / (RG * NG);
+        T acc[2][4];
+        tile_dot<T, E, 2, NPP, NQ>(ops.VwT, sX + (job == 0 ? 6 : 2 + job) * NQ * E + g * 4, m0, acc);
+        const T sgn = job == 0 ? T(1) : T(-1);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[r][e] *= sgn;
+          if (m0 + r < NP) sts_cols(sR + (job * NP + m0 + r) * E + g * 4, acc[r]);
+        }
+      }
+    }
+    __syncthreads();
+  }
 
   // ---- 2a. face nodes: [p], {u}, [u] in the owner's node order ----
   for (int it = tid; it < 4 * NFP * E; it += NT) {
@@ -310,8 +381,10 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
     const T aun = a1 * nx + a2 * ny + a3 * nz;
     const T jun = (j1 * nx + j2 * ny + j3 * nz) / Jf;
     // central terms change sign in the transpose; penalty terms do not
-    const T cs = MODE >= kAdjLsrk ? T(1) : T(-1);
-    const T Fp = cs * aun + T(0.5) * p.tau_p * jp * Jf;
+    const T cs = ADJ ? T(1) : T(-1);
+    // strong form: F_p = -1/2 ([u].n J^f - tau_p [p] J^f)
+    const T Fp = STRONG ? T(-0.5) * (j1 * nx + j2 * ny + j3 * nz) + T(0.5) * p.tau_p * jp * Jf
+                        : cs * aun + T(0.5) * p.tau_p * jp * Jf;
     const T s = T(0.5) * (cs * jp + p.tau_u * jun);
     sFQ[(0 * 4 * NFQ + qf) * E + e] = Fp;
     sFQ[(1 * 4 * NFQ + qf) * E + e] = s * nx;
@@ -345,7 +418,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
     c = c < ncols ? c : ncols - 1;
     const int64_t k = c / S;
     T acc = sR[(fld * NP + n) * E + e];
-    if (fld == 0) acc += sP[n * E + e] + sP[(NP + n) * E + e];
+    if (!STRONG && fld == 0) acc += sP[n * E + e] + sP[(NP + n) * E + e];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const int pio = p.fcode[k * 4 + f] % 6;
@@ -358,7 +431,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
     }
     sR[(fld * NP + n) * E + e] = acc;
   }
-  if (MODE >= kAdjLsrk) {
+  if (ADJ) {
     // ---- adjoint epilogue: A^T beta is complete in sR ----
     __syncthreads();
     for (int it = tid; it < 4 * NP * E; it += NT) {
@@ -423,7 +496,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
           const int m = m0 + r;
           if (m >= NP) continue;
           const int64_t idx = fld * fs + c * NP + m;
-          if (MODE == kRhs) {
+          if (RHS_OUT) {
             p.out[idx] = acc[r][e];
           } else {
             const T rr = p.rk_a * p.res[idx] + p.dt * acc[r][e];
@@ -463,6 +536,12 @@ cudaError_t launch_stage_n(const StageParams<T>& p, int mode, cudaStream_t strea
     case kRecord: return launch_stage_mode<T, N, kRecord>(p, stream);
     case kAdjLsrk: return launch_stage_mode<T, N, kAdjLsrk>(p, stream);
     case kAdjRhs: return launch_stage_mode<T, N, kAdjRhs>(p, stream);
+    case kRhsStrong:
+      if constexpr (N <= 5) return launch_stage_mode<T, N, kRhsStrong>(p, stream);
+      return cudaErrorInvalidValue;
+    case kLsrkStrong:
+      if constexpr (N <= 5) return launch_stage_mode<T, N, kLsrkStrong>(p, stream);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

@@ -44,6 +44,11 @@ struct DevOps {
   void* base = nullptr;       // single allocation holding all of the above
 };
 
+// Stage kernel modes.  kRhsStrong, kLsrkStrong: the strong formulation
+// (Sec. 4.1) with the same degree 2N+1 rules (under-integrated on curved
+// elements), N <= 5.
+enum StageMode { kRhs = 0, kLsrk = 1, kRecord = 2, kAdjLsrk = 3, kAdjRhs = 4, kRhsStrong = 5, kLsrkStrong = 6 };
+
 // Parameters of one fused stage launch (RHS + weight-adjusted update, and in
 // LSRK mode the Runge-Kutta update).
 template <typename T>
@@ -146,6 +151,7 @@ struct wadg_mesh {
   wadg::DevOps<float> ops32;
   uint8_t* d_tcops = nullptr;  // operators of the tensor-core stage (split bf16 or tf32)
   int tc_fmt = -1;             // format of d_tcops: 0 split bf16, 1 tf32
+  int form = 0;                // 0 strong-weak, 1 strong formulation (Sec. 4.1)
   void* d_hostQ = nullptr;     // device copies for wadg_step_host
   void* d_hostR = nullptr;
   size_t host_io_bytes = 0;
