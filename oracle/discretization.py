@@ -63,14 +63,18 @@ FACE_ORIENT = np.array([-1.0, 1.0, 1.0, -1.0])
 class RefTet:
     """Modal reference operators for degree N (M^ = I in this basis)."""
 
-    def __init__(self, N: int, qdeg_pts: int | None = None):
+    def __init__(self, N: int, qdeg_pts: int | None = None, face_pts: int | None = None):
+        """Collapsed rules with qdeg_pts points per direction on the volume
+        and face_pts on the faces (defaults: N+1, exact to degree 2N+1;
+        face_pts defaults to qdeg_pts)."""
         self.N = N
         self.Np = (N + 1) * (N + 2) * (N + 3) // 6
         self.Nfp = (N + 1) * (N + 2) // 2
         nq = N + 1 if qdeg_pts is None else qdeg_pts
-        self.rst_q, self.w_q = P.tet_rule(nq)               # degree 2N+1 volume rule
+        nf = nq if face_pts is None else face_pts
+        self.rst_q, self.w_q = P.tet_rule(nq)               # degree 2 nq - 1 volume rule
         self.Nq = len(self.w_q)
-        self.rs_f, self.w_f = P.tri_rule(nq)                # degree 2N+1 face rule
+        self.rs_f, self.w_f = P.tri_rule(nf)                # degree 2 nf - 1 face rule
         self.Nfq = len(self.w_f)
         self.lattice = own_lattice(N)
         self.Vn = P.dubiner_tet(N, *self.lattice.T)         # nodal <- modal
@@ -102,6 +106,7 @@ class Mesh:
         self.EToV = np.asarray(EToV, dtype=np.int64)
         self.K = len(self.EToV)
         X = np.asarray(geom_xyz, dtype=np.float64)           # (K, Np, 3) at the lattice
+        self.geom_xyz = X
         self.Xmodal = np.einsum("mn,knd->kmd", ref.Vn_inv, X)  # modal coefficients of x_h
         self._connect()
         self._geometry()

@@ -100,6 +100,26 @@ def a_h(mesh: Mesh, c: np.ndarray, tau_p=1.0, tau_u=1.0) -> np.ndarray:
     return out
 
 
+def strong_rule_points(N: int) -> tuple[int, int]:
+    """Points per direction of the collapsed volume and face rules of the
+    energy-stable strong form (Sec. 4.1): the volume integrands (J div u) v
+    have degree 2(N-1) + (N-1) + N = 4N-3 and the surface integrands
+    [u].nJ^f v degree (2N-2) + 2N = 4N-2 for an isoparametric map; an n-point
+    collapsed rule is exact to degree 2n-1.  The volume count never drops
+    below the N+1 of the degree 2N+1 rule."""
+    return max(N + 1, 2 * N - 1), 2 * N
+
+
+def strong_mesh(mesh: Mesh) -> Mesh:
+    """The same mesh and geometry with the strong form's rules (cached)."""
+    sm = getattr(mesh, "_strong_mesh", None)
+    if sm is None:
+        nv, nf = strong_rule_points(mesh.ref.N)
+        sm = Mesh(RefTet(mesh.ref.N, nv, nf), mesh.VXYZ, mesh.EToV, mesh.geom_xyz)
+        mesh._strong_mesh = sm
+    return sm
+
+
 def a_h_strong(mesh: Mesh, c: np.ndarray, tau_p=1.0, tau_u=1.0) -> np.ndarray:
     """Strong right-hand side functional (Sec. 4.1, the strong DG form), modal
     (4, K, Np): both equations integrated by parts twice,
@@ -205,11 +225,22 @@ def exact_mass_inverse(mesh: Mesh, r: np.ndarray, c2fun=None, qpts=None) -> np.n
 
 def rhs(mesh: Mesh, c: np.ndarray, variant: str = "wadg", tau_p=1.0, tau_u=1.0,
         c2q=None, c2fun=None, form: str = "strong_weak") -> np.ndarray:
-    """dQ/dt = -M^{-1} A_h Q in modal coefficients (sign folded into a_h);
-    form "strong_weak" (default) or "strong"."""
-    if form not in ("strong_weak", "strong"):
+    """dQ/dt = -M^{-1} A_h Q in modal coefficients (sign folded into a_h).
+
+    form: "strong_weak" (default, the mesh's degree 2N+1 rules); "strong",
+    the strong form with its volume and surface terms on the degree 4N-3 /
+    4N-2 rules of strong_mesh (Sec. 4.1, energy stable); or
+    "strong_underintegrated", the strong form on the mesh's degree 2N+1 rules
+    (Sec. 6.5: faster, stability not guaranteed).  The mass inverse always
+    uses the mesh's degree 2N+1 volume rule (Sec. 6.2)."""
+    if form == "strong_weak":
+        r = a_h(mesh, c, tau_p, tau_u)
+    elif form == "strong":
+        r = a_h_strong(strong_mesh(mesh), c, tau_p, tau_u)
+    elif form == "strong_underintegrated":
+        r = a_h_strong(mesh, c, tau_p, tau_u)
+    else:
         raise ValueError(form)
-    r = (a_h if form == "strong_weak" else a_h_strong)(mesh, c, tau_p, tau_u)
     if variant == "wadg":
         return wadg_apply(mesh, r, c2q)
     if variant == "exact":

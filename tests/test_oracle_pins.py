@@ -552,3 +552,68 @@ def test_strong_differs_from_strong_weak_when_under_integrated():
     c = random_fields((4, m.K, m.ref.Np), 19)
     a, b = OW.a_h(m, c), OW.a_h_strong(m, c)
     assert np.linalg.norm(a - b) > 1e-6 * np.linalg.norm(a)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_strong_rules_are_exact_and_minimal(N):
+    """Sec. 4.1: the strong form equals the strong-weak form (on the same face
+    rule, so that the non-polynomial penalty terms coincide) once the rules
+    integrate the degree 4N-3 volume and 4N-2 surface integrands exactly; the
+    strong form's rules (2N-1 volume, 2N face points per direction) do, and one
+    point fewer in either direction does not (curved mesh, tau = (1, 0.5))."""
+    from oracle import wadg as OW
+    from oracle.discretization import Mesh, RefTet
+    from synthetic import random_fields, warped_cube
+    nv, nf = OW.strong_rule_points(N)
+    assert (nv, nf) == (max(N + 1, 2 * N - 1), 2 * N)
+    VXYZ, EToV, geom = warped_cube(2, N, 0.1)
+    c = random_fields((4, len(EToV), (N + 1) * (N + 2) * (N + 3) // 6), 40 + N)
+
+    def gap(v, f):
+        m = Mesh(RefTet(N, v, f), VXYZ, EToV, geom)
+        a, b = OW.a_h(m, c, 1.0, 0.5), OW.a_h_strong(m, c, 1.0, 0.5)
+        return np.linalg.norm(a - b) / np.linalg.norm(a)
+
+    assert gap(nv, nf) < 1e-12
+    assert gap(nv - 1, nf) > 1e-7
+    assert gap(nv, nf - 1) > 1e-7
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_strong_form_energy_identity(N):
+    """The strong form on its exact rules satisfies the strong-weak discrete
+    energy identity Q^T a_h(Q) = dissipation (Sec. 4.1: energy stable), for
+    tau = 0 (conservative) and tau > 0; the same form on the degree 2N+1
+    rules does not (curved mesh)."""
+    from oracle.discretization import Mesh, RefTet
+    from synthetic import warped_cube
+    VXYZ, EToV, geom = warped_cube(2, N, 0.1)
+    mesh = Mesh(RefTet(N), VXYZ, EToV, geom)
+    sm = W.strong_mesh(mesh)
+    assert sm.ref.Nq == W.strong_rule_points(N)[0] ** 3 and sm.ref.Nfq == (2 * N) ** 2
+    rng = np.random.default_rng(7 + N)
+    c = rng.standard_normal((4, mesh.K, mesh.ref.Np))
+    scale = float(np.sum(c * c))
+    for tau in (0.0, 1.0):
+        lhs = float(np.sum(W.a_h_strong(sm, c, tau, tau) * c))
+        assert abs(lhs - W.dissipation(sm, c, tau, tau)) < 1e-12 * scale
+    under = float(np.sum(W.a_h_strong(mesh, c, 0.0, 0.0) * c))
+    assert abs(under) > 1e-8 * scale
+
+
+def test_strong_rhs_forms_select_rules():
+    """rhs(form=...) routes the strong form to the strong rules and the
+    under-integrated variant to the mesh's own rules; the mass inverse uses
+    the degree 2N+1 rule in both (the results equal the direct compositions)."""
+    from oracle.discretization import Mesh, RefTet
+    from synthetic import warped_cube
+    VXYZ, EToV, geom = warped_cube(2, 3, 0.1)
+    mesh = Mesh(RefTet(3), VXYZ, EToV, geom)
+    c = np.random.default_rng(3).standard_normal((4, mesh.K, mesh.ref.Np))
+    full = W.rhs(mesh, c, form="strong")
+    under = W.rhs(mesh, c, form="strong_underintegrated")
+    assert np.allclose(full, W.wadg_apply(mesh, W.a_h_strong(W.strong_mesh(mesh), c)), rtol=0, atol=1e-12)
+    assert np.allclose(under, W.wadg_apply(mesh, W.a_h_strong(mesh, c)), rtol=0, atol=1e-12)
+    assert np.linalg.norm(full - under) > 1e-6 * np.linalg.norm(full)
+    with pytest.raises(ValueError):
+        W.rhs(mesh, c, form="weak")
