@@ -152,14 +152,22 @@ int wadg_step(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nst
               wadg_stream stream);
 
 /* Formulation of the stage (Sec. 4.1): 0 = strong-weak (the default; the
- * pressure equation integrated by parts once), 1 = strong (both equations
+ * pressure equation integrated by parts once); 1 = strong (both equations
  * integrated by parts twice: volume term -int (div u) v, surface term
- * -int 1/2 ([u].n - tau_p [p]) v), evaluated with the same degree 2N+1 rules
- * (under-integrated on curved elements, where it differs from the
- * strong-weak form; with exact rules the two agree).  The strong form is
- * built for the CUDA-core precisions and N <= 5, for wadg_rhs, wadg_step,
- * wadg_step_host and wadg_solve; the adjoint and batches require form 0.
- * WADG_EUNSUPPORTED otherwise. */
+ * -int 1/2 ([u].n - tau_p [p]) v), with its volume and surface terms on
+ * collapsed rules of max(N+1, 2N-1) and 2N points per direction, exact for
+ * the degree 4N-3 volume and 4N-2 surface integrands of an isoparametric map,
+ * so that it is energy stable (Sec. 4.1, Sec. 6.3); 2 = the strong form on
+ * the degree 2N+1 rules of the strong-weak form (under-integrated on curved
+ * elements; faster, stability not guaranteed, Sec. 6.5).  The weight-adjusted
+ * update always uses the degree 2N+1 volume rule.  Form 1 computes and keeps
+ * the geometric factors at its rules' points (9 values per volume point, 3
+ * per face point, in the mesh precision); it returns WADG_EGEOM if J <= 0 at
+ * one of them.  The strong forms are built for the CUDA-core precisions and
+ * N <= 5, for wadg_rhs, wadg_step, wadg_step_host and wadg_solve; the adjoint
+ * and batches require form 0.  WADG_EUNSUPPORTED otherwise.  May be called
+ * before or after wadg_set_operators; on failure the previous formulation
+ * stays in effect. */
 int wadg_set_formulation(wadg_mesh* mesh, int form);
 
 /* wadg_step on host fields: Q and res are HOST [4][K][S][Np] arrays in the

@@ -162,11 +162,12 @@ def wadg_step(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, trace
            "wadg_step", mesh)
 
 
-FORMULATIONS = {"strong_weak": 0, "strong": 1}
+FORMULATIONS = {"strong_weak": 0, "strong": 1, "strong_underintegrated": 2}
 
 
 def wadg_set_formulation(mesh: MeshHandle, form: str):
-    """'strong_weak' (default) or 'strong' (see include/wadg.h)."""
+    """'strong_weak' (default), 'strong' (energy-stable rules) or
+    'strong_underintegrated' (the degree 2N+1 rules); see include/wadg.h."""
     _check(load().wadg_set_formulation(mesh.handle, FORMULATIONS[form]), "wadg_set_formulation", mesh)
 
 

@@ -164,6 +164,21 @@ __global__ void geo_pack_il_kernel(int64_t K, int Nq, int Nfq, const double* __r
   }
 }
 
+template <typename T>
+__global__ void to_precision_kernel(int64_t n, const double* __restrict__ in, T* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (T)in[i];
+}
+
+template <typename T>
+cudaError_t launch_to_precision(int64_t n, const double* in, T* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  to_precision_kernel<T><<<2048, 256, 0, st>>>(n, in, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_to_precision<float>(int64_t, const double*, float*, cudaStream_t);
+template cudaError_t launch_to_precision<double>(int64_t, const double*, double*, cudaStream_t);
+
 cudaError_t launch_geo_pack_il(int64_t K, int Nq, int Nfq, const double* J, const double* G, const double* c2,
                                const double* nJ, float* vgeo_il, float* fgeo_il, cudaStream_t st) {
   geo_pack_il_kernel<<<2048, 256, 0, st>>>(K, Nq, Nfq, J, G, c2, nJ, vgeo_il, fgeo_il);

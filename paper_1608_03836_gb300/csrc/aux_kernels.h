@@ -15,6 +15,9 @@ cudaError_t launch_geo_pack(int64_t K, int Nq, int Nfq, const double* J, const d
                             const double* nJ, T* vgeo, T* fgeo, cudaStream_t st);
 cudaError_t launch_geo_pack_il(int64_t K, int Nq, int Nfq, const double* J, const double* G, const double* c2,
                                const double* nJ, float* vgeo_il, float* fgeo_il, cudaStream_t st);
+// out[i] = (T) in[i], i < n.
+template <typename T>
+cudaError_t launch_to_precision(int64_t n, const double* in, T* out, cudaStream_t st);
 template <typename T>
 cudaError_t launch_project(int64_t ncols, int S, int Np, int Nq, const double* fq, const double* J, const double* Vq,
                            const double* Pq, T* Q, cudaStream_t st);

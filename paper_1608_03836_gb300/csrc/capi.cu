@@ -159,6 +159,171 @@ int upload_ops(wadg_mesh* m, DevOps<T>& ops) {
   return WADG_OK;
 }
 
+// Sizes of the strong-form stage tables for a runtime (N, form).
+struct StrongSizes {
+  int nqs = 0, nfqs = 0, nqsc = 0, nfqsp = 0;
+};
+template <int N, int F>
+StrongSizes strong_sizes_t() {
+  using D = StrongDims<N, F>;
+  return {D::NQS, D::NFQS, D::NQSC, D::NFQSP};
+}
+template <int F>
+StrongSizes strong_sizes_f(int N) {
+  switch (N) {
+    case 1: return strong_sizes_t<1, F>();
+    case 2: return strong_sizes_t<2, F>();
+    case 3: return strong_sizes_t<3, F>();
+    case 4: return strong_sizes_t<4, F>();
+    case 5: return strong_sizes_t<5, F>();
+    default: return StrongSizes();
+  }
+}
+StrongSizes strong_sizes(int N, int form) { return form == 1 ? strong_sizes_f<1>(N) : strong_sizes_f<2>(N); }
+
+void free_strong(wadg_mesh* m) {
+  dfree(m->d_sgeo);
+  dfree(m->d_sfgeo);
+  if (m->sops64.base) cudaFree(m->sops64.base);
+  if (m->sops32.base) cudaFree(m->sops32.base);
+  m->sops64 = StrongOps<double>();
+  m->sops32 = StrongOps<float>();
+  m->strong_form = 0;
+  m->strong_precision = -1;
+}
+
+// Tables of the rules R in precision T, k-major and zero padded to the row
+// counts of the strong-form stage (StrongDims).
+template <typename T>
+int upload_strong_ops(wadg_mesh* m, const RuleOps& R, const StrongSizes& z, StrongOps<T>& so) {
+  const int Np = m->ref.Np, Nfp = m->ref.Nfp;
+  const int NPP = (Np + 3) / 4 * 4, NFPP = (Nfp + 3) / 4 * 4;
+  if (R.Nq != z.nqs || R.Nfq != z.nfqs) return fail(m, WADG_EUNSUPPORTED, "strong-form rule sizes");
+  std::vector<T> h;
+  auto push = [&](size_t n) {
+    size_t off = h.size();
+    h.resize(off + ((n + 31) / 32) * 32, T(0));
+    return off;
+  };
+  const size_t oVa = push((size_t)3 * Np * z.nqsc), oVw = push((size_t)z.nqsc * NPP),
+               oVtri = push((size_t)Nfp * z.nfqsp), oVtriTw = push((size_t)z.nfqs * NFPP);
+  for (int n = 0; n < Np; ++n)
+    for (int q = 0; q < R.Nq; ++q) {
+      for (int a = 0; a < 3; ++a)
+        h[oVa + ((size_t)a * Np + n) * z.nqsc + q] = (T)R.Vqa[((size_t)a * R.Nq + q) * Np + n];
+      h[oVw + (size_t)q * NPP + n] = (T)(R.Vq[(size_t)q * Np + n] * R.wq[q]);
+    }
+  for (int j = 0; j < Nfp; ++j)
+    for (int q = 0; q < R.Nfq; ++q) {
+      h[oVtri + (size_t)j * z.nfqsp + q] = (T)R.Vtri[(size_t)q * Nfp + j];
+      h[oVtriTw + (size_t)q * NFPP + j] = (T)R.VtriTw[(size_t)j * R.Nfq + q];
+    }
+  void* base = nullptr;
+  WADG_CUDA(m, cudaMalloc(&base, h.size() * sizeof(T)));
+  cudaError_t e = cudaMemcpy(base, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    return cuda_fail(m, e, "strong-form tables");
+  }
+  T* b = (T*)base;
+  so.base = base;
+  so.VaT = b + oVa;
+  so.VwT = b + oVw;
+  so.VtriT = b + oVtri;
+  so.VtriTwT = b + oVtriTw;
+  return WADG_OK;
+}
+
+// Geometric factors G_ai at the volume points and n J^f at the (owner) face
+// points of the rules R, by the same FP64 kernels as the mesh's own rules,
+// stored in precision T as d_sgeo [K][9][Nq_R] and d_sfgeo [K][3][4 Nfq_R].
+template <typename T>
+int strong_geometry(wadg_mesh* m, const RuleOps& R) {
+  const int64_t K = m->K;
+  const int Np = m->ref.Np;
+  const size_t nVq = R.Vq.size(), nVqa = R.Vqa.size(), nVfa = R.Vfa.size();
+  const size_t nG = (size_t)K * 9 * R.Nq, nF = (size_t)K * 12 * R.Nfq;
+  std::vector<double> tab(nVq + nVqa + nVfa);
+  std::copy(R.Vq.begin(), R.Vq.end(), tab.begin());
+  std::copy(R.Vqa.begin(), R.Vqa.end(), tab.begin() + nVq);
+  std::copy(R.Vfa.begin(), R.Vfa.end(), tab.begin() + nVq + nVqa);
+  std::vector<int32_t> EToF32(m->EToF.begin(), m->EToF.end());
+  double *dTab = nullptr, *dJ = nullptr, *dG = nullptr, *dxq = nullptr, *dnJ = nullptr;
+  int32_t* dEToF = nullptr;
+  int* dbad = nullptr;
+  int nbad = 0;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = cudaMalloc((void**)&dTab, tab.size() * 8)) != cudaSuccess) break;
+    if ((e = cudaMalloc((void**)&dJ, (size_t)K * R.Nq * 8)) != cudaSuccess) break;
+    if ((e = cudaMalloc((void**)&dG, nG * 8)) != cudaSuccess) break;
+    if ((e = cudaMalloc((void**)&dxq, (size_t)K * R.Nq * 3 * 8)) != cudaSuccess) break;
+    if ((e = cudaMalloc((void**)&dnJ, nF * 8)) != cudaSuccess) break;
+    if ((e = cudaMalloc((void**)&dEToF, (size_t)K * 4 * 4)) != cudaSuccess) break;
+    if ((e = cudaMalloc((void**)&dbad, sizeof(int))) != cudaSuccess) break;
+    if ((e = cudaMemcpy(dTab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if ((e = cudaMemcpy(dEToF, EToF32.data(), (size_t)K * 16, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if ((e = cudaMemset(dbad, 0, sizeof(int))) != cudaSuccess) break;
+    if ((e = launch_geo_volume(K, Np, R.Nq, m->d_X, dTab, dTab + nVq, dJ, dG, dxq, dbad, 0)) != cudaSuccess) break;
+    if ((e = launch_geo_face(K, Np, R.Nfq, m->d_X, dTab + nVq + nVqa, m->d_owner, m->d_EToE, dEToF, dnJ, 0)) !=
+        cudaSuccess)
+      break;
+    if ((e = cudaMemcpy(&nbad, dbad, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+    if (nbad == 0) {
+      if (sizeof(T) == sizeof(double)) {
+        m->d_sgeo = dG;
+        m->d_sfgeo = dnJ;
+        dG = dnJ = nullptr;
+      } else {
+        if ((e = cudaMalloc(&m->d_sgeo, nG * sizeof(T))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&m->d_sfgeo, nF * sizeof(T))) != cudaSuccess) break;
+        if ((e = launch_to_precision<T>((int64_t)nG, dG, (T*)m->d_sgeo, 0)) != cudaSuccess) break;
+        if ((e = launch_to_precision<T>((int64_t)nF, dnJ, (T*)m->d_sfgeo, 0)) != cudaSuccess) break;
+        e = cudaDeviceSynchronize();
+      }
+    }
+  } while (0);
+  cudaFree(dTab);
+  cudaFree(dJ);
+  cudaFree(dG);
+  cudaFree(dxq);
+  cudaFree(dnJ);
+  cudaFree(dEToF);
+  cudaFree(dbad);
+  if (e != cudaSuccess) return cuda_fail(m, e, "strong-form geometry");
+  if (nbad > 0)
+    return fail(m, WADG_EGEOM, "J <= 0 at %d points of the strong form's volume rule (%d points per direction)", nbad,
+                R.nv);
+  return WADG_OK;
+}
+
+// Brings the strong-form state to the mesh's formulation and precision: the
+// tables of its rules and, for form 1, the geometric factors at their points.
+int prepare_strong(wadg_mesh* m) {
+  if (m->form == 0 || m->precision < 0) {
+    free_strong(m);
+    return WADG_OK;
+  }
+  if (m->strong_form == m->form && m->strong_precision == m->precision) return WADG_OK;
+  free_strong(m);
+  int nv = 0, nf = 0;
+  strong_rule_points(m->N, m->form, &nv, &nf);
+  RuleOps R;
+  char err[256];
+  if (!build_rule_ops(m->ref, nv, nf, R, err, sizeof(err))) return fail(m, WADG_EUNSUPPORTED, "%s", err);
+  const StrongSizes z = strong_sizes(m->N, m->form);
+  const bool f64 = m->precision == WADG_FP64;
+  int st = f64 ? upload_strong_ops<double>(m, R, z, m->sops64) : upload_strong_ops<float>(m, R, z, m->sops32);
+  if (st == WADG_OK && m->form == 1) st = f64 ? strong_geometry<double>(m, R) : strong_geometry<float>(m, R);
+  if (st != WADG_OK) {
+    free_strong(m);
+    return st;
+  }
+  m->strong_form = m->form;
+  m->strong_precision = m->precision;
+  return WADG_OK;
+}
+
 // Locate a physical point: element index and reference coordinates.  Among
 // the elements whose node bounding box holds the point, Newton's method on
 // x_h(x^) = x; the element where the point is most interior wins.
@@ -310,6 +475,7 @@ void wadg_mesh_destroy(wadg_mesh* m) {
   dfree(m->d_fgeo);
   if (m->ops64.base) cudaFree(m->ops64.base);
   if (m->ops32.base) cudaFree(m->ops32.base);
+  free_strong(m);
   dfree(m->d_Qtmp);
   dfree(m->d_red);
   dfree(m->d_tcops);
@@ -616,7 +782,7 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
   m->tau_u = tau_u;
   ++m->generation;
   WADG_CUDA(m, cudaDeviceSynchronize());
-  return WADG_OK;
+  return prepare_strong(m);
 }
 
 }  // extern "C"
@@ -625,6 +791,8 @@ namespace {
 
 inline const DevOps<double>& ops_of(const wadg_mesh* m, double) { return m->ops64; }
 inline const DevOps<float>& ops_of(const wadg_mesh* m, float) { return m->ops32; }
+inline const StrongOps<double>& sops_of(const wadg_mesh* m, double) { return m->sops64; }
+inline const StrongOps<float>& sops_of(const wadg_mesh* m, float) { return m->sops32; }
 
 template <typename T>
 StageParams<T> base_params(const wadg_mesh* m) {
@@ -634,6 +802,9 @@ StageParams<T> base_params(const wadg_mesh* m) {
   p.EToE = m->d_EToE;
   p.fcode = m->d_fcode;
   p.ops = ops_of(m, T());
+  p.sgeo = (const T*)m->d_sgeo;
+  p.sfgeo = (const T*)m->d_sfgeo;
+  p.sops = sops_of(m, T());
   p.ncols = m->K * m->S;
   p.S = m->S;
   p.tau_p = (T)m->tau_p;
@@ -644,10 +815,13 @@ StageParams<T> base_params(const wadg_mesh* m) {
 // Stage launch for the mesh's precision: RHS and LSRK stages of
 // WADG_FP32_3XBF16 and WADG_FP32_TF32 run on the tensor cores, everything
 // else on CUDA cores.
-// The strong formulation runs the RHS and LSRK stages as their strong modes.
+// The strong formulations run the RHS and LSRK stages as their strong modes.
 inline int stage_mode(const wadg_mesh* m, int mode) {
   if (m->form == 0) return mode;
-  return mode == kRhs ? kRhsStrong : (mode == kLsrk ? kLsrkStrong : -1);
+  const bool full = m->form == 1;
+  if (mode == kRhs) return full ? kRhsStrong : kRhsStrongU;
+  if (mode == kLsrk) return full ? kLsrkStrong : kLsrkStrongU;
+  return -1;
 }
 
 template <typename T>
@@ -672,6 +846,8 @@ cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p,
 int check_ready(wadg_mesh* m) {
   if (!m) return WADG_EINVAL;
   if (m->precision < 0) return fail(m, WADG_ESTATE, "wadg_set_operators has not been called");
+  if (m->form != 0 && (m->strong_form != m->form || m->strong_precision != m->precision))
+    return fail(m, WADG_ESTATE, "the strong-form tables are not built (an earlier call failed)");
   return WADG_OK;
 }
 
@@ -756,14 +932,23 @@ int wadg_step(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps
 
 int wadg_set_formulation(wadg_mesh* m, int form) {
   if (!m) return WADG_EINVAL;
-  if (form != 0 && form != 1) return fail(m, WADG_EINVAL, "formulation %d (0 strong-weak, 1 strong)", form);
-  if (form == 1 && m->N > 5) return fail(m, WADG_EUNSUPPORTED, "the strong formulation is built for N <= 5");
-  if (form == 1 && (m->precision == WADG_FP32_3XBF16 || m->precision == WADG_FP32_TF32))
+  if (form < 0 || form > 2)
+    return fail(m, WADG_EINVAL, "formulation %d (0 strong-weak, 1 strong, 2 strong on the 2N+1 rules)", form);
+  if (form != 0 && m->N > 5) return fail(m, WADG_EUNSUPPORTED, "the strong formulation is built for N <= 5");
+  if (form != 0 && (m->precision == WADG_FP32_3XBF16 || m->precision == WADG_FP32_TF32))
     return fail(m, WADG_EUNSUPPORTED, "the strong formulation runs on the CUDA-core precisions (FP64, FP32)");
-  if (form != m->form) {
-    m->form = form;
-    ++m->generation;  // a captured solve graph holds the other formulation's kernels
+  DeviceGuard g(m->device);
+  const int prev = m->form;
+  m->form = form;
+  const int st = prepare_strong(m);
+  if (st != WADG_OK) {
+    const std::string msg = m->last_error;
+    m->form = prev;
+    prepare_strong(m);
+    m->last_error = msg;
+    return st;
   }
+  if (form != prev) ++m->generation;  // a captured solve graph holds the other formulation's kernels
   return WADG_OK;
 }
 

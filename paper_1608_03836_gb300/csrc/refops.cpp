@@ -203,6 +203,117 @@ void lattice_basis(const RefOps& ops, int npts, const double* r, const double* s
   eval_nodal(ops.N, ops.Np, ops.VnInv, npts, r, s, t, vals, grads);
 }
 
+// Collapsed Gauss-Jacobi rule with n points per direction on the reference
+// tetrahedron (exact to degree 2n-1); point (ia, ib, ic) at ia + n (ib + n ic).
+static void tet_rule(int n, std::vector<double>& r, std::vector<double>& s, std::vector<double>& t,
+                     std::vector<double>& w) {
+  std::vector<double> xa(n), wa(n), xb(n), wb(n), xc(n), wc(n);
+  gauss_jacobi(n, 0.0, 0.0, xa.data(), wa.data());
+  gauss_jacobi(n, 1.0, 0.0, xb.data(), wb.data());
+  gauss_jacobi(n, 2.0, 0.0, xc.data(), wc.data());
+  const int nq = n * n * n;
+  r.resize(nq);
+  s.resize(nq);
+  t.resize(nq);
+  w.resize(nq);
+  for (int ic = 0; ic < n; ++ic)
+    for (int ib = 0; ib < n; ++ib)
+      for (int ia = 0; ia < n; ++ia) {
+        int q = ia + n * (ib + n * ic);
+        double a = xa[ia], b = xb[ib], c = xc[ic];
+        r[q] = 0.25 * (1 + a) * (1 - b) * (1 - c) - 1.0;
+        s[q] = 0.5 * (1 + b) * (1 - c) - 1.0;
+        t[q] = c;
+        w[q] = wa[ia] * wb[ib] * wc[ic] / 8.0;
+      }
+}
+
+// Collapsed rule with n points per direction on the reference triangle.
+static void tri_rule(int n, std::vector<double>& r, std::vector<double>& s, std::vector<double>& w) {
+  std::vector<double> xa(n), wa(n), xb(n), wb(n);
+  gauss_jacobi(n, 0.0, 0.0, xa.data(), wa.data());
+  gauss_jacobi(n, 1.0, 0.0, xb.data(), wb.data());
+  r.resize(n * n);
+  s.resize(n * n);
+  w.resize(n * n);
+  for (int ib = 0; ib < n; ++ib)
+    for (int ia = 0; ia < n; ++ia) {
+      int q = ia + n * ib;
+      r[q] = 0.5 * (1 + xa[ia]) * (1 - xb[ib]) - 1.0;
+      s[q] = xb[ib];
+      w[q] = wa[ia] * wb[ib] / 2.0;
+    }
+}
+
+// Triangle Lagrange basis of the degree-N lattice at npts points: out [npts][Nfp].
+static void tri_lagrange(int N, int Nfp, const std::vector<double>& VtInv, int npts, const double* r, const double* s,
+                         double* out) {
+  std::vector<double> vt(Nfp);
+  for (int q = 0; q < npts; ++q) {
+    tri_modal(N, r[q], s[q], vt.data());
+    for (int j = 0; j < Nfp; ++j) {
+      double acc = 0.0;
+      for (int m = 0; m < Nfp; ++m) acc += vt[m] * VtInv[m * Nfp + j];
+      out[q * Nfp + j] = acc;
+    }
+  }
+}
+
+// Basis values Vf [4][npts][Np] (nullable) and derivatives Vfa [4][3][npts][Np]
+// at the images of the triangle points (rf, sf) on each face.
+static void face_ops(int N, int Np, const std::vector<double>& VnInv, int npts, const double* rf, const double* sf,
+                     double* Vf, double* Vfa) {
+  std::vector<double> fr(npts), fs(npts), ft(npts), vals((size_t)npts * Np);
+  for (int f = 0; f < 4; ++f) {
+    const double* A = kRefV[kFaceV[f][0]];
+    const double* B = kRefV[kFaceV[f][1]];
+    const double* C = kRefV[kFaceV[f][2]];
+    for (int q = 0; q < npts; ++q) {
+      double la = -0.5 * (rf[q] + sf[q]), lb = 0.5 * (1 + rf[q]), lc = 0.5 * (1 + sf[q]);
+      fr[q] = la * A[0] + lb * B[0] + lc * C[0];
+      fs[q] = la * A[1] + lb * B[1] + lc * C[1];
+      ft[q] = la * A[2] + lb * B[2] + lc * C[2];
+    }
+    eval_nodal(N, Np, VnInv, npts, fr.data(), fs.data(), ft.data(), Vf ? &Vf[(size_t)f * npts * Np] : vals.data(),
+               &Vfa[(size_t)f * 3 * npts * Np]);
+  }
+}
+
+void strong_rule_points(int N, int form, int* nv, int* nf) {
+  if (form == 1) {
+    *nv = std::max(N + 1, 2 * N - 1);
+    *nf = 2 * N;
+  } else {
+    *nv = N + 1;
+    *nf = N + 1;
+  }
+}
+
+bool build_rule_ops(const RefOps& o, int nv, int nf, RuleOps& out, char* err, int errlen) {
+  if (o.N < 1 || nv < 1 || nf < 1 || nv > 16 || nf > 16 || (int)o.VtInv.size() != o.Nfp * o.Nfp) {
+    std::snprintf(err, errlen, "rules (%d, %d) for N=%d", nv, nf, o.N);
+    return false;
+  }
+  const int N = o.N, Np = o.Np, Nfp = o.Nfp;
+  out.nv = nv;
+  out.nf = nf;
+  tet_rule(nv, out.rq, out.sq, out.tq, out.wq);
+  tri_rule(nf, out.rf, out.sf, out.wf);
+  out.Nq = nv * nv * nv;
+  out.Nfq = nf * nf;
+  out.Vq.assign((size_t)out.Nq * Np, 0.0);
+  out.Vqa.assign((size_t)3 * out.Nq * Np, 0.0);
+  eval_nodal(N, Np, o.VnInv, out.Nq, out.rq.data(), out.sq.data(), out.tq.data(), out.Vq.data(), out.Vqa.data());
+  out.Vtri.assign((size_t)out.Nfq * Nfp, 0.0);
+  tri_lagrange(N, Nfp, o.VtInv, out.Nfq, out.rf.data(), out.sf.data(), out.Vtri.data());
+  out.VtriTw.assign((size_t)Nfp * out.Nfq, 0.0);
+  for (int j = 0; j < Nfp; ++j)
+    for (int q = 0; q < out.Nfq; ++q) out.VtriTw[j * out.Nfq + q] = out.Vtri[q * Nfp + j] * out.wf[q];
+  out.Vfa.assign((size_t)4 * 3 * out.Nfq * Np, 0.0);
+  face_ops(N, Np, o.VnInv, out.Nfq, out.rf.data(), out.sf.data(), nullptr, out.Vfa.data());
+  return true;
+}
+
 bool build_refops(int N, RefOps& o, char* err, int errlen) {
   if (N < 1 || N > 6) {
     std::snprintf(err, errlen, "degree N=%d outside 1..6", N);
@@ -229,34 +340,8 @@ bool build_refops(int N, RefOps& o, char* err, int errlen) {
       }
 
   // rules
-  std::vector<double> xa(n1), wa(n1), xb(n1), wb(n1), xc(n1), wc(n1);
-  gauss_jacobi(n1, 0.0, 0.0, xa.data(), wa.data());
-  gauss_jacobi(n1, 1.0, 0.0, xb.data(), wb.data());
-  gauss_jacobi(n1, 2.0, 0.0, xc.data(), wc.data());
-  o.rq.resize(Nq);
-  o.sq.resize(Nq);
-  o.tq.resize(Nq);
-  o.wq.resize(Nq);
-  for (int ic = 0; ic < n1; ++ic)
-    for (int ib = 0; ib < n1; ++ib)
-      for (int ia = 0; ia < n1; ++ia) {
-        int q = ia + n1 * (ib + n1 * ic);
-        double a = xa[ia], b = xb[ib], c = xc[ic];
-        o.rq[q] = 0.25 * (1 + a) * (1 - b) * (1 - c) - 1.0;
-        o.sq[q] = 0.5 * (1 + b) * (1 - c) - 1.0;
-        o.tq[q] = c;
-        o.wq[q] = wa[ia] * wb[ib] * wc[ic] / 8.0;
-      }
-  o.rf.resize(Nfq);
-  o.sf.resize(Nfq);
-  o.wf.resize(Nfq);
-  for (int ib = 0; ib < n1; ++ib)
-    for (int ia = 0; ia < n1; ++ia) {
-      int q = ia + n1 * ib;
-      o.rf[q] = 0.5 * (1 + xa[ia]) * (1 - xb[ib]) - 1.0;
-      o.sf[q] = xb[ib];
-      o.wf[q] = wa[ia] * wb[ib] / 2.0;
-    }
+  tet_rule(n1, o.rq, o.sq, o.tq, o.wq);
+  tri_rule(n1, o.rf, o.sf, o.wf);
 
   // Vandermonde at the lattice and its inverse
   std::vector<double> Vn(Np * Np), VnInv, tmp(3 * Np);
@@ -314,7 +399,7 @@ bool build_refops(int N, RefOps& o, char* err, int errlen) {
   }
 
   // face operators: triangle Lagrange basis of the face lattice at face points
-  std::vector<double> Vt(Nfp * Nfp), VtInv, vt(Nfp);
+  std::vector<double> Vt(Nfp * Nfp), VtInv;
   for (int j = 0; j <= N; ++j)
     for (int i = 0; i <= N - j; ++i) {
       int id = tri_lattice_index(N, i, j);
@@ -324,15 +409,9 @@ bool build_refops(int N, RefOps& o, char* err, int errlen) {
     std::snprintf(err, errlen, "singular triangle Vandermonde (N=%d)", N);
     return false;
   }
+  o.VtInv = VtInv;
   o.Vtri.assign(Nfq * Nfp, 0.0);
-  for (int q = 0; q < Nfq; ++q) {
-    tri_modal(N, o.rf[q], o.sf[q], vt.data());
-    for (int j = 0; j < Nfp; ++j) {
-      double acc = 0.0;
-      for (int m = 0; m < Nfp; ++m) acc += vt[m] * VtInv[m * Nfp + j];
-      o.Vtri[q * Nfp + j] = acc;
-    }
-  }
+  tri_lagrange(N, Nfp, VtInv, Nfq, o.rf.data(), o.sf.data(), o.Vtri.data());
   o.VtriTw.assign(Nfp * Nfq, 0.0);
   for (int j = 0; j < Nfp; ++j)
     for (int q = 0; q < Nfq; ++q) o.VtriTw[j * Nfq + q] = o.Vtri[q * Nfp + j] * o.wf[q];
@@ -340,20 +419,7 @@ bool build_refops(int N, RefOps& o, char* err, int errlen) {
   // face points, basis and derivatives there
   o.Vf.assign(4 * Nfq * Np, 0.0);
   o.Vfa.assign(4 * 3 * Nfq * Np, 0.0);
-  std::vector<double> fr(Nfq), fs(Nfq), ft(Nfq);
-  for (int f = 0; f < 4; ++f) {
-    const double* A = kRefV[kFaceV[f][0]];
-    const double* B = kRefV[kFaceV[f][1]];
-    const double* C = kRefV[kFaceV[f][2]];
-    for (int q = 0; q < Nfq; ++q) {
-      double la = -0.5 * (o.rf[q] + o.sf[q]), lb = 0.5 * (1 + o.rf[q]), lc = 0.5 * (1 + o.sf[q]);
-      fr[q] = la * A[0] + lb * B[0] + lc * C[0];
-      fs[q] = la * A[1] + lb * B[1] + lc * C[1];
-      ft[q] = la * A[2] + lb * B[2] + lc * C[2];
-    }
-    eval_nodal(N, Np, VnInv, Nfq, fr.data(), fs.data(), ft.data(), &o.Vf[(size_t)f * Nfq * Np],
-               &o.Vfa[(size_t)f * 3 * Nfq * Np]);
-  }
+  face_ops(N, Np, VnInv, Nfq, o.rf.data(), o.sf.data(), o.Vf.data(), o.Vfa.data());
 
   // Fmask: face-lattice node (i,j) of face f -> volume node
   o.Fmask.assign(4 * Nfp, -1);

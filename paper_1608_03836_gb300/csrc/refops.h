@@ -33,7 +33,31 @@ struct RefOps {
   std::vector<int> gidx;       // [4][6][Nfp] volume node at owner-order position j
   std::vector<int> ginv;       // [4][6][Np] owner-order position of node n (-1: not on face)
   std::vector<double> VnInv;   // [Np][Np] modal coefficients of the Lagrange basis
+  std::vector<double> VtInv;   // [Nfp][Nfp] same for the triangle lattice
 };
+
+// A second pair of rules on the same element: collapsed rules with nv points
+// per direction on the volume (exact to degree 2 nv - 1) and nf on each face,
+// with the operators that the strong form's volume and surface terms use.
+struct RuleOps {
+  int nv = 0, nf = 0, Nq = 0, Nfq = 0;
+  std::vector<double> rq, sq, tq, wq;  // [Nq]
+  std::vector<double> rf, sf, wf;      // [Nfq] on the reference triangle
+  std::vector<double> Vqa;     // [3][Nq][Np]  dl_n/dx^_a (x_q)
+  std::vector<double> Vq;      // [Nq][Np]     l_n(x_q)
+  std::vector<double> Vtri;    // [Nfq][Nfp]   triangle Lagrange basis at the face points
+  std::vector<double> VtriTw;  // [Nfp][Nfq]   V_tri^T diag(w_f)
+  std::vector<double> Vfa;     // [4][3][Nfq][Np] dl_n/dx^_a at face-f points
+};
+
+// Points per direction of the strong form's rules (Sec. 4.1).  form 1: the
+// energy-stable rules, exact for the degree 4N-3 volume and 4N-2 surface
+// integrands of an isoparametric map (max(N+1, 2N-1) and 2N points); form 2:
+// the degree 2N+1 rules of the strong-weak form (N+1 and N+1 points).
+void strong_rule_points(int N, int form, int* nv, int* nf);
+
+// Builds the operators of the rules (nv, nf) for the element of o.
+bool build_rule_ops(const RefOps& o, int nv, int nf, RuleOps& out, char* err, int errlen);
 
 // The six vertex permutations sigma of a triangle, lexicographic.
 extern const int kPerm[6][3];

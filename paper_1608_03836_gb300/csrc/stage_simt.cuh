@@ -56,9 +56,9 @@ struct Dims {
 // 76 KB of shared memory (3 blocks per SM), 112 KB for N >= 5.
 // FP64 is bound by the FP64 pipe, not by shared memory: it keeps ~96 KB
 // blocks with E a multiple of 4.
-template <typename T, int N>
-constexpr int cols_per_block() {
-  constexpr int per = Dims<N>::PER_COL * (int)sizeof(T);
+template <typename T, int N, int PER>
+constexpr int cols_for() {
+  constexpr int per = PER * (int)sizeof(T);
   if (sizeof(T) == 8) {
     constexpr int e8 = (98304 / per) / 4 * 4;
     return e8 < 4 ? 4 : (e8 > 32 ? 32 : e8);
@@ -67,6 +67,21 @@ constexpr int cols_per_block() {
   constexpr int fit = budget / per;
   constexpr int e = fit >= 28 ? 28 : (fit >= 20 ? 20 : (fit >= 12 ? 12 : 4));
   return e;
+}
+template <typename T, int N>
+constexpr int cols_per_block() {
+  return cols_for<T, N, Dims<N>::PER_COL>();
+}
+
+constexpr bool strong_mode(int mode) {
+  return mode == kRhsStrong || mode == kLsrkStrong || mode == kRhsStrongU || mode == kLsrkStrongU;
+}
+// Shared values per column of a mode: the strong modes use their own layout.
+template <int N, int MODE>
+constexpr int mode_per_col() {
+  if constexpr (MODE == kRhsStrong || MODE == kLsrkStrong) return StrongDims<N, 1>::PER_COL;
+  if constexpr (MODE == kRhsStrongU || MODE == kLsrkStrongU) return StrongDims<N, 2>::PER_COL;
+  return Dims<N>::PER_COL;
 }
 
 constexpr int kStageThreads = 256;
@@ -139,15 +154,21 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
   constexpr int NG = E / 4;
   constexpr int NT = kStageThreads;
   constexpr bool ADJ = MODE == kAdjLsrk || MODE == kAdjRhs;
-  constexpr bool STRONG = MODE == kRhsStrong || MODE == kLsrkStrong;
-  constexpr bool RHS_OUT = MODE == kRhs || MODE == kRhsStrong;
+  constexpr bool STRONG = strong_mode(MODE);
+  constexpr bool SFULL = MODE == kRhsStrong || MODE == kLsrkStrong;
+  constexpr bool RHS_OUT = MODE == kRhs || MODE == kRhsStrong || MODE == kRhsStrongU;
+  using SD = StrongDims<N, SFULL ? 1 : 2>;
+  // face phase: jump/average combinations at the face nodes and points
+  constexpr int NCMB = STRONG ? 4 : 7;
+  constexpr int FQ = STRONG ? SD::NFQS : NFQ;
+  constexpr int FQP = STRONG ? SD::NFQSP : NFQP;
 
   T* sQ = reinterpret_cast<T*>(smem_raw);  // [4][NP][E]
   T* sR = sQ + 4 * NP * E;                 // [4][NP][E]  load vector b (un-inverted)
-  T* sP = sR + 4 * NP * E;                 // [2][NP][E]  partial pressure volume terms
-  T* sX = sP + 2 * NP * E;                 // [XS][E]     scratch
-  T* sFN = sX;                             // [7][4 NFP][E] face-node combos
-  T* sFQ = sX + 7 * 4 * NFP * E;           // [7][4 NFQ][E] face-point values
+  T* sP = sR + 4 * NP * E;                 // [2][NP][E]  partial pressure volume terms (strong-weak)
+  T* sX = STRONG ? sP : sP + 2 * NP * E;   // [XS][E]     scratch
+  T* sFN = sX;                             // [NCMB][4 NFP][E] face-node combos
+  T* sFQ = sX + NCMB * 4 * NFP * E;        // [NCMB][4 FQ][E]  face-point values
 
   const int tid = threadIdx.x;
   const int64_t col0 = blk * E;
@@ -236,71 +257,82 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
   }
   __syncthreads();
   } else {
-    // ---- 1a-1b (strong form): J div u = sum_{a,i} G_ai du_i/dx^_a and J grad p
-    // at the quadrature points, one field u_i at a time (scratch arrays 0-2:
-    // du_i/dx^_a, 3-5: dp/dx^_a then J grad p, 6: -J div u) ----
-    static_assert(7 * NQ <= Dm::XS, "strong-form scratch");
-    for (int i = 0; i < 3; ++i) {
+    // ---- 1 (strong form, Sec. 6.3): at the rule's NQS volume points, QC at
+    // a time, the 12 reference derivatives d(p, u_i)/dx^_a; then pointwise
+    // J div u = sum_{a,i} G_ai du_i/dx^_a and J grad p = sum_a G_ai dp/dx^_a;
+    // then b_p = -V_q^T diag(w) (J div u), b_ui = -V_q^T diag(w) (J grad p)_i,
+    // accumulated over the chunks by the thread that owns each output ----
+    constexpr int NQS = SD::NQS, QC = SD::QC, NQSC = SD::NQSC;
+    static_assert(12 * QC <= SD::XS && 4 * NQ <= SD::XS, "strong-form scratch");
+    const T* sg = SFULL ? p.sgeo : p.vgeo;
+    constexpr int64_t GST = SFULL ? 9 * NQS : 11 * NQ;  // element stride of G_ai
+    for (int q0 = 0; q0 < NQSC; q0 += QC) {
       {
-        constexpr int RG = NQP / 4;
-        const int njobs = i == 0 ? 6 : 3;
-        for (int it = tid; it < njobs * RG * NG; it += NT) {
+        constexpr int RG = QC / 4;
+        for (int it = tid; it < 12 * RG * NG; it += NT) {
           const int g = it % NG;
           const int m0 = ((it / NG) % RG) * 4;
-          const int job = it / (RG * NG);  // 0-2: du_i/dx^_a, 3-5: dp/dx^_a
-          const T* A = ops.VaT + (job % 3) * NP * NQP;
-          const T* in = (job < 3 ? sQ + (1 + i) * NP * E : sQ) + g * 4;
+          const int job = it / (RG * NG);  // 3 field + a
+          const int fld = job / 3, a = job % 3;
           T acc[4][4];
-          tile_dot<T, E, 4, NQP, NP>(A, in, m0, acc);
+          tile_dot<T, E, 4, NQSC, NP>(p.sops.VaT + a * NP * NQSC + q0, sQ + fld * NP * E + g * 4, m0, acc);
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
-            if (m0 + r < NQ) sts_cols(sX + (job * NQ + m0 + r) * E + g * 4, acc[r]);
+          for (int r = 0; r < 4; ++r) sts_cols(sX + (job * QC + m0 + r) * E + g * 4, acc[r]);
         }
       }
       __syncthreads();
-      for (int it = tid; it < NQ * E; it += NT) {
-        const int q = it % NQ;
-        const int e = it / NQ;
-        int64_t c = col0 + e;
-        c = c < ncols ? c : ncols - 1;
-        const int64_t k = c / S;
-        const T* gk = p.vgeo + k * 11 * NQ + q;
-        T sdiv = i == 0 ? T(0) : sX[(6 * NQ + q) * E + e];
+      for (int it = tid; it < QC * E; it += NT) {
+        const int q = it % QC;
+        const int e = it / QC;
+        T v[12];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) sdiv -= __ldg(gk + (a * 3 + i) * NQ) * sX[(a * NQ + q) * E + e];
-        sX[(6 * NQ + q) * E + e] = sdiv;
-        if (i == 0) {
-          T G[9], d[3];
+        for (int j = 0; j < 12; ++j) v[j] = sX[(j * QC + q) * E + e];
+        T jdiv = T(0), gp[3] = {T(0), T(0), T(0)};
+        if (q0 + q < NQS) {  // padded points carry no geometry
+          int64_t c = col0 + e;
+          c = c < ncols ? c : ncols - 1;
+          const T* gk = sg + (c / S) * GST + q0 + q;
 #pragma unroll
-          for (int j = 0; j < 9; ++j) G[j] = __ldg(gk + j * NQ);
+          for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int j = 0; j < 3; ++j) d[j] = sX[((3 + j) * NQ + q) * E + e];
+            for (int i = 0; i < 3; ++i) {
+              const T G = __ldg(gk + (a * 3 + i) * NQS);
+              jdiv += G * v[3 * (1 + i) + a];
+              gp[i] += G * v[a];
+            }
+        }
+        sX[q * E + e] = jdiv;
 #pragma unroll
-          for (int j = 0; j < 3; ++j)
-            sX[((3 + j) * NQ + q) * E + e] = G[0 * 3 + j] * d[0] + G[1 * 3 + j] * d[1] + G[2 * 3 + j] * d[2];
+        for (int i = 0; i < 3; ++i) sX[((1 + i) * QC + q) * E + e] = gp[i];
+      }
+      __syncthreads();
+      {
+        constexpr int RG = NPP / 2;
+        for (int it = tid; it < 4 * RG * NG; it += NT) {
+          const int g = it % NG;
+          const int m0 = ((it / NG) % RG) * 2;
+          const int job = it / (RG * NG);
+          T acc[2][4];
+          tile_dot<T, E, 2, NPP, QC>(p.sops.VwT + q0 * NPP, sX + job * QC * E + g * 4, m0, acc);
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            if (m0 + r >= NP) continue;
+            T* o = sR + (job * NP + m0 + r) * E + g * 4;
+            T cur[4];
+            if (q0 == 0) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) cur[e] = -acc[r][e];
+            } else {
+              lds_cols(o, cur);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) cur[e] -= acc[r][e];
+            }
+            sts_cols(o, cur);
+          }
         }
       }
       __syncthreads();
     }
-    // ---- 1c (strong form): b_p = V_q^T diag(w) (-J div u), b_ui = -V_q^T diag(w) (J grad p)_i ----
-    {
-      constexpr int RG = NPP / 2;
-      for (int it = tid; it < 4 * RG * NG; it += NT) {
-        const int g = it % NG;
-        const int m0 = ((it / NG) % RG) * 2;
-        const int job = it / (RG * NG);
-        T acc[2][4];
-        tile_dot<T, E, 2, NPP, NQ>(ops.VwT, sX + (job == 0 ? 6 : 2 + job) * NQ * E + g * 4, m0, acc);
-        const T sgn = job == 0 ? T(1) : T(-1);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[r][e] *= sgn;
-          if (m0 + r < NP) sts_cols(sR + (job * NP + m0 + r) * E + g * 4, acc[r]);
-        }
-      }
-    }
-    __syncthreads();
   }
 
   // ---- 2a. face nodes: [p], {u}, [u] in the owner's node order ----
@@ -336,60 +368,78 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
     }
     const int row = f * NFP + j;
     sFN[(0 * 4 * NFP + row) * E + e] = pp - pm;
-    sFN[(1 * 4 * NFP + row) * E + e] = T(0.5) * (u1p + u1m);
-    sFN[(2 * 4 * NFP + row) * E + e] = T(0.5) * (u2p + u2m);
-    sFN[(3 * 4 * NFP + row) * E + e] = T(0.5) * (u3p + u3m);
-    sFN[(4 * 4 * NFP + row) * E + e] = u1p - u1m;
-    sFN[(5 * 4 * NFP + row) * E + e] = u2p - u2m;
-    sFN[(6 * 4 * NFP + row) * E + e] = u3p - u3m;
-  }
-  __syncthreads();
-
-  // ---- 2b. interpolate the 7 combinations to the face points ----
-  {
-    constexpr int RG = NFQP / 4;
-    for (int it = tid; it < 28 * RG * NG; it += NT) {
-      const int g = it % NG;
-      const int m0 = ((it / NG) % RG) * 4;
-      const int job = it / (RG * NG);  // combo * 4 + face
-      T acc[4][4];
-      tile_dot<T, E, 4, NFQP, NFP>(ops.VtriT, sFN + job * NFP * E + g * 4, m0, acc);
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        if (m0 + r < NFQ) sts_cols(sFQ + (job * NFQ + m0 + r) * E + g * 4, acc[r]);
+    if constexpr (STRONG) {  // [p], [u]
+      sFN[(1 * 4 * NFP + row) * E + e] = u1p - u1m;
+      sFN[(2 * 4 * NFP + row) * E + e] = u2p - u2m;
+      sFN[(3 * 4 * NFP + row) * E + e] = u3p - u3m;
+    } else {  // [p], {u}, [u]
+      sFN[(1 * 4 * NFP + row) * E + e] = T(0.5) * (u1p + u1m);
+      sFN[(2 * 4 * NFP + row) * E + e] = T(0.5) * (u2p + u2m);
+      sFN[(3 * 4 * NFP + row) * E + e] = T(0.5) * (u3p + u3m);
+      sFN[(4 * 4 * NFP + row) * E + e] = u1p - u1m;
+      sFN[(5 * 4 * NFP + row) * E + e] = u2p - u2m;
+      sFN[(6 * 4 * NFP + row) * E + e] = u3p - u3m;
     }
   }
   __syncthreads();
 
-  // ---- 2c. strong-weak flux (Sec. 4.1) ----
-  for (int it = tid; it < 4 * NFQ * E; it += NT) {
-    const int qf = it % (4 * NFQ);
-    const int e = it / (4 * NFQ);
+  // ---- 2b. interpolate the combinations to the face points ----
+  {
+    constexpr int RG = FQP / 4;
+    const T* Vtri = STRONG ? p.sops.VtriT : ops.VtriT;
+    for (int it = tid; it < NCMB * 4 * RG * NG; it += NT) {
+      const int g = it % NG;
+      const int m0 = ((it / NG) % RG) * 4;
+      const int job = it / (RG * NG);  // combo * 4 + face
+      T acc[4][4];
+      tile_dot<T, E, 4, FQP, NFP>(Vtri, sFN + job * NFP * E + g * 4, m0, acc);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (m0 + r < FQ) sts_cols(sFQ + (job * FQ + m0 + r) * E + g * 4, acc[r]);
+    }
+  }
+  __syncthreads();
+
+  // ---- 2c. fluxes (Sec. 4.1) ----
+  for (int it = tid; it < 4 * FQ * E; it += NT) {
+    const int qf = it % (4 * FQ);
+    const int e = it / (4 * FQ);
     int64_t c = col0 + e;
     c = c < ncols ? c : ncols - 1;
     const int64_t k = c / S;
-    const T* fg = p.fgeo + k * 3 * 4 * NFQ + qf;
-    const T nx = __ldg(fg), ny = __ldg(fg + 4 * NFQ), nz = __ldg(fg + 8 * NFQ);
+    const T* fg = (SFULL ? p.sfgeo : p.fgeo) + k * 3 * 4 * FQ + qf;
+    const T nx = __ldg(fg), ny = __ldg(fg + 4 * FQ), nz = __ldg(fg + 8 * FQ);
     const T Jf = sqrt(nx * nx + ny * ny + nz * nz);
-    const T jp = sFQ[(0 * 4 * NFQ + qf) * E + e];
-    const T a1 = sFQ[(1 * 4 * NFQ + qf) * E + e];
-    const T a2 = sFQ[(2 * 4 * NFQ + qf) * E + e];
-    const T a3 = sFQ[(3 * 4 * NFQ + qf) * E + e];
-    const T j1 = sFQ[(4 * 4 * NFQ + qf) * E + e];
-    const T j2 = sFQ[(5 * 4 * NFQ + qf) * E + e];
-    const T j3 = sFQ[(6 * 4 * NFQ + qf) * E + e];
-    const T aun = a1 * nx + a2 * ny + a3 * nz;
-    const T jun = (j1 * nx + j2 * ny + j3 * nz) / Jf;
-    // central terms change sign in the transpose; penalty terms do not
-    const T cs = ADJ ? T(1) : T(-1);
-    // strong form: F_p = -1/2 ([u].n J^f - tau_p [p] J^f)
-    const T Fp = STRONG ? T(-0.5) * (j1 * nx + j2 * ny + j3 * nz) + T(0.5) * p.tau_p * jp * Jf
-                        : cs * aun + T(0.5) * p.tau_p * jp * Jf;
-    const T s = T(0.5) * (cs * jp + p.tau_u * jun);
-    sFQ[(0 * 4 * NFQ + qf) * E + e] = Fp;
-    sFQ[(1 * 4 * NFQ + qf) * E + e] = s * nx;
-    sFQ[(2 * 4 * NFQ + qf) * E + e] = s * ny;
-    sFQ[(3 * 4 * NFQ + qf) * E + e] = s * nz;
+    const T jp = sFQ[(0 * 4 * FQ + qf) * E + e];
+    if constexpr (STRONG) {
+      // F_p = -1/2 ([u].n J^f - tau_p [p] J^f), F_u = -1/2 ([p] - tau_u [u].n) n J^f
+      const T j1 = sFQ[(1 * 4 * FQ + qf) * E + e];
+      const T j2 = sFQ[(2 * 4 * FQ + qf) * E + e];
+      const T j3 = sFQ[(3 * 4 * FQ + qf) * E + e];
+      const T junJ = j1 * nx + j2 * ny + j3 * nz;
+      const T s = T(0.5) * (-jp + p.tau_u * junJ / Jf);
+      sFQ[(0 * 4 * FQ + qf) * E + e] = T(-0.5) * junJ + T(0.5) * p.tau_p * jp * Jf;
+      sFQ[(1 * 4 * FQ + qf) * E + e] = s * nx;
+      sFQ[(2 * 4 * FQ + qf) * E + e] = s * ny;
+      sFQ[(3 * 4 * FQ + qf) * E + e] = s * nz;
+    } else {
+      // F_p = -1/2 (2 {u}.n J^f - tau_p [p] J^f), F_u = -1/2 ([p] - tau_u [u].n) n J^f
+      const T a1 = sFQ[(1 * 4 * FQ + qf) * E + e];
+      const T a2 = sFQ[(2 * 4 * FQ + qf) * E + e];
+      const T a3 = sFQ[(3 * 4 * FQ + qf) * E + e];
+      const T j1 = sFQ[(4 * 4 * FQ + qf) * E + e];
+      const T j2 = sFQ[(5 * 4 * FQ + qf) * E + e];
+      const T j3 = sFQ[(6 * 4 * FQ + qf) * E + e];
+      const T aun = a1 * nx + a2 * ny + a3 * nz;
+      const T jun = (j1 * nx + j2 * ny + j3 * nz) / Jf;
+      // central terms change sign in the transpose; penalty terms do not
+      const T cs = ADJ ? T(1) : T(-1);
+      const T s = T(0.5) * (cs * jp + p.tau_u * jun);
+      sFQ[(0 * 4 * FQ + qf) * E + e] = cs * aun + T(0.5) * p.tau_p * jp * Jf;
+      sFQ[(1 * 4 * FQ + qf) * E + e] = s * nx;
+      sFQ[(2 * 4 * FQ + qf) * E + e] = s * ny;
+      sFQ[(3 * 4 * FQ + qf) * E + e] = s * nz;
+    }
   }
   __syncthreads();
 
@@ -401,7 +451,7 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
       const int m0 = ((it / NG) % RG) * 2;
       const int job = it / (RG * NG);  // field * 4 + face
       T acc[2][4];
-      tile_dot<T, E, 2, NFPP, NFQ>(ops.VtriTwT, sFQ + job * NFQ * E + g * 4, m0, acc);
+      tile_dot<T, E, 2, NFPP, FQ>(STRONG ? p.sops.VtriTwT : ops.VtriTwT, sFQ + job * FQ * E + g * 4, m0, acc);
 #pragma unroll
       for (int r = 0; r < 2; ++r)
         if (m0 + r < NFP) sts_cols(sFN + (job * NFP + m0 + r) * E + g * 4, acc[r]);
@@ -517,8 +567,9 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<
 
 template <typename T, int N, int MODE>
 cudaError_t launch_stage_mode(const StageParams<T>& p, cudaStream_t stream) {
-  constexpr int E = cols_per_block<T, N>();
-  const size_t smem = (size_t)Dims<N>::PER_COL * E * sizeof(T);
+  constexpr int PER = mode_per_col<N, MODE>();
+  constexpr int E = cols_for<T, N, PER>();
+  const size_t smem = (size_t)PER * E * sizeof(T);
   const int64_t blocks = (p.ncols + E - 1) / E;
   if (blocks == 0) return cudaSuccess;
   auto kern = stage_kernel<T, N, E, MODE>;
@@ -541,6 +592,12 @@ cudaError_t launch_stage_n(const StageParams<T>& p, int mode, cudaStream_t strea
       return cudaErrorInvalidValue;
     case kLsrkStrong:
       if constexpr (N <= 5) return launch_stage_mode<T, N, kLsrkStrong>(p, stream);
+      return cudaErrorInvalidValue;
+    case kRhsStrongU:
+      if constexpr (N <= 5) return launch_stage_mode<T, N, kRhsStrongU>(p, stream);
+      return cudaErrorInvalidValue;
+    case kLsrkStrongU:
+      if constexpr (N <= 5) return launch_stage_mode<T, N, kLsrkStrongU>(p, stream);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

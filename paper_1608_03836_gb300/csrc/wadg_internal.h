@@ -45,9 +45,49 @@ struct DevOps {
 };
 
 // Stage kernel modes.  kRhsStrong, kLsrkStrong: the strong formulation
-// (Sec. 4.1) with the same degree 2N+1 rules (under-integrated on curved
-// elements), N <= 5.
-enum StageMode { kRhs = 0, kLsrk = 1, kRecord = 2, kAdjLsrk = 3, kAdjRhs = 4, kRhsStrong = 5, kLsrkStrong = 6 };
+// (Sec. 4.1) with its volume and surface terms on the energy-stable rules
+// (degree 4N-3 / 4N-2); kRhsStrongU, kLsrkStrongU: the strong formulation on
+// the degree 2N+1 rules (under-integrated on curved elements).  N <= 5.
+enum StageMode {
+  kRhs = 0, kLsrk = 1, kRecord = 2, kAdjLsrk = 3, kAdjRhs = 4,
+  kRhsStrong = 5, kLsrkStrong = 6, kRhsStrongU = 7, kLsrkStrongU = 8
+};
+
+// Sizes of the strong-form stage for degree N and formulation FORM (1: the
+// energy-stable rules, 2: the degree 2N+1 rules).  The volume terms walk the
+// NQS points in NCH chunks of QC points (a multiple of 4; the operator tables
+// are padded with zero rows to NQSC = NCH QC); a chunk's 12 derivative values
+// per point share the per-column scratch with the face phase (4 jump
+// combinations at 4 Nfp face nodes and 4 NFQS face points) and the update
+// (4 Nq values).
+template <int N, int FORM>
+struct StrongDims {
+  static constexpr int NP = (N + 1) * (N + 2) * (N + 3) / 6;
+  static constexpr int NFP = (N + 1) * (N + 2) / 2;
+  static constexpr int NQ = (N + 1) * (N + 1) * (N + 1);
+  static constexpr int NV = FORM == 1 ? (2 * N - 1 > N + 1 ? 2 * N - 1 : N + 1) : N + 1;
+  static constexpr int NF = FORM == 1 ? 2 * N : N + 1;
+  static constexpr int NQS = NV * NV * NV;
+  static constexpr int NFQS = NF * NF;
+  static constexpr int NFQSP = (NFQS + 3) / 4 * 4;
+  static constexpr int XF = 4 * 4 * NFP + 4 * 4 * NFQS;
+  static constexpr int NCH = (12 * NQS + XF - 1) / XF;
+  static constexpr int QC = ((NQS + NCH - 1) / NCH + 3) / 4 * 4;
+  static constexpr int NQSC = NCH * QC;
+  static constexpr int XS0 = XF > 12 * QC ? XF : 12 * QC;
+  static constexpr int XS = XS0 > 4 * NQ ? XS0 : 4 * NQ;
+  static constexpr int PER_COL = 8 * NP + XS;  // sQ, sR, scratch
+};
+
+// Device tables of the strong form's rules, k-major as in DevOps.
+template <typename T>
+struct StrongOps {
+  const T* VaT = nullptr;      // [3][Np][NQSC]  dl_n/dx^_a at the volume points
+  const T* VwT = nullptr;      // [NQSC][NPP]    V_q^T diag(w)
+  const T* VtriT = nullptr;    // [Nfp][NFQSP]   face interpolation
+  const T* VtriTwT = nullptr;  // [NFQS][NFPP]   V_tri^T diag(w_f)
+  void* base = nullptr;
+};
 
 // Parameters of one fused stage launch (RHS + weight-adjusted update, and in
 // LSRK mode the Runge-Kutta update).
@@ -71,6 +111,10 @@ struct StageParams {
   const T* src_vec = nullptr;         // [S][Np] l_n(x^_s)
   T src_amp = 0;
   T* yrec = nullptr;                  // record mode: [ncols][Nq]
+  // strong form on its own rules (kRhsStrong, kLsrkStrong)
+  const T* sgeo = nullptr;   // [K][9][NQS]: G_ai at the strong volume points
+  const T* sfgeo = nullptr;  // [K][3][4 NFQS]: n J^f at the strong face points (owner order)
+  StrongOps<T> sops;         // tables of the current strong formulation (1 or 2)
 };
 
 // Parameters of the adjoint weight-adjusted update beta = U^T mu (local).
@@ -151,7 +195,14 @@ struct wadg_mesh {
   wadg::DevOps<float> ops32;
   uint8_t* d_tcops = nullptr;  // operators of the tensor-core stage (split bf16 or tf32)
   int tc_fmt = -1;             // format of d_tcops: 0 split bf16, 1 tf32
-  int form = 0;                // 0 strong-weak, 1 strong formulation (Sec. 4.1)
+  int form = 0;                // 0 strong-weak, 1 strong, 2 strong on the 2N+1 rules (Sec. 4.1)
+  // strong-form state for (strong_form, strong_precision): tables, and for
+  // form 1 the geometric factors at its rules' points
+  int strong_form = 0, strong_precision = -1;
+  void* d_sgeo = nullptr;      // [K][9][NQS] in the mesh precision
+  void* d_sfgeo = nullptr;     // [K][3][4 NFQS]
+  wadg::StrongOps<double> sops64;
+  wadg::StrongOps<float> sops32;
   void* d_hostQ = nullptr;     // device copies for wadg_step_host
   void* d_hostR = nullptr;
   size_t host_io_bytes = 0;
