@@ -297,6 +297,50 @@ def accuracy(W):
     return out
 
 
+def algorithmic_form(N: int, S: int, s: int, form: str) -> int:
+    """Algorithmic bytes per element and stage of a formulation: the strong
+    form reads its 9 geometric factors at (max(N+1, 2N-1))^3 volume points and
+    its normals at (2N)^2 points per face, the update's two weights at the
+    degree 2N+1 points; the others read the strong-weak set (algorithmic())."""
+    if form != "strong":
+        return algorithmic(N, S, s)[0]
+    Np = (N + 1) * (N + 2) * (N + 3) // 6
+    nv, nf = max(N + 1, 2 * N - 1), 2 * N
+    return s * (16 * Np * S + 9 * nv ** 3 + 2 * (N + 1) ** 3 + 12 * nf ** 2) + 32
+
+
+def formulations(W, steps):
+    """The three formulations on the headline mesh (warped cube, N = 4,
+    heterogeneous c^2) on the CUDA-core stage, FP32 and FP64: LSRK step time,
+    one RHS launch, and that launch's algorithmic bytes against the measured
+    HBM copy bandwidth."""
+    import torch
+    hbm, _, _ = peaks()
+    out = {}
+    for prec, nsteps in (("fp32", max(2, steps // 2)), ("fp64", max(2, steps // 5))):
+        m, Q = build_case(W, prec, 0)
+        s = 4 if prec == "fp32" else 8
+        dof = 4 * m.K * m.Np
+        rows = {}
+        for form in ("strong_weak", "strong", "strong_underintegrated"):
+            W.wadg_set_formulation(m, form)
+            tot, st = time_steps(W, m, Q, nsteps, 3)
+            B = algorithmic_form(WORKLOAD["N"], 1, s, form)
+            rows[form] = {"value": dof * 5 / (tot / nsteps * 1e-3), "ms_per_step": tot / nsteps, "stage_ms": st,
+                          "algorithmic_bytes_per_element": B,
+                          "achieved_gbs": B * m.K / (st * 1e-3) / 1e9,
+                          "hbm_frac": B * m.K / (st * 1e-3) / 1e9 / hbm}
+        W.wadg_device_status(m)
+        for form in ("strong", "strong_underintegrated"):
+            rows[form]["time_vs_strong_weak"] = rows[form]["ms_per_step"] / rows["strong_weak"]["ms_per_step"]
+        out[prec] = rows
+        del Q, m
+        torch.cuda.empty_cache()
+    out["workload"] = (f"warped cube {WORKLOAD['n']}^3x6, N=4, heterogeneous c^2, CUDA-core stage; strong: "
+                       "7^3 volume and 8^2 face points per element for its volume and surface terms")
+    return out
+
+
 def c2_study(W):
     """The precision configuration: warped cube 24^3 x 6 = 82,944 tets, N = 5,
     c^2 = 1, standing wave to T = 0.5.  For each precision built at N = 5 (the
@@ -473,6 +517,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--c2", action="store_true",
                     help="run only the N = 5 precision study (82,944 tets, T = 0.5) and print its JSON")
+    ap.add_argument("--forms", action="store_true",
+                    help="run only the formulation comparison on the headline mesh and print its JSON")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
     args = ap.parse_args()
@@ -492,6 +538,10 @@ def main():
     if args.c2:
         if rank == 0:
             print(json.dumps({"c2_precision_study": c2_study(W)}))
+        return
+    if args.forms:
+        if rank == 0:
+            print(json.dumps({"formulations": formulations(W, args.steps)}))
         return
 
     def barrier():
@@ -561,6 +611,7 @@ def main():
         extras["uneven_batch"] = uneven_batch(W, max(2, args.steps))
         extras["uneven_batch_small"] = uneven_batch(W, max(2, args.steps), small=True)
         extras["accuracy"] = accuracy(W)
+        extras["formulations"] = formulations(W, args.steps)
 
     if rank != 0:
         return
