@@ -158,15 +158,40 @@ def a_h_strong(mesh: Mesh, c: np.ndarray, tau_p=1.0, tau_u=1.0) -> np.ndarray:
 # Mass inverses.
 # ---------------------------------------------------------------------------
 
-def wadg_apply(mesh: Mesh, r: np.ndarray, c2q=None) -> np.ndarray:
+def wadg_weights(mesh: Mesh, c2q=None, conservative: bool = False):
+    """Weights (W_p, W_u) at the volume points of the weight-adjusted update.
+
+    Default (Sec. 6.2, Sec. 7): W_p = c^2_q / J_q, W_u = 1 / J_q, i.e. the
+    reciprocals of the mass weights w_p = J/c^2 and w_u = J.
+    conservative=True (Sec. 3, after the moment estimate): local conservation
+    is restored by replacing each mass weight w by its projection Pi_N w onto
+    P^N within the weight-adjusted inner product: W = 1 / (Pi_N w)(x_q), the
+    projection taken with the volume rule (Pi_N w = V_q P_q w_q).  Then for a
+    load b the update r = P_q diag(W) V_q b has zeroth moment
+    sum_q w_q (w r)_q = b(1) exactly (mass weight w at the points).
+    """
+    ref = mesh.ref
+    wu = mesh.J
+    wp = wu if c2q is None else mesh.J / c2q
+    if conservative:
+        def proj(f):
+            coef = np.einsum("qm,kq->km", ref.Vq, f * ref.w_q)      # modal, M^ = I
+            return np.einsum("qm,km->kq", ref.Vq, coef)
+        wu, wp = proj(wu), proj(wp)
+        if np.any(wu <= 0) or np.any(wp <= 0):
+            raise ValueError("projected mass weight is not positive at a volume point")
+    return 1.0 / wp, 1.0 / wu
+
+
+def wadg_apply(mesh: Mesh, r: np.ndarray, c2q=None, conservative: bool = False) -> np.ndarray:
     """Weight-adjusted inverse, matrix free: P_q diag(W_q) V_q r (Sec. 6.2, Sec. 7).
 
-    W_q = c^2_q / J_q for the pressure row, 1 / J_q for the velocity rows.
+    W_q = c^2_q / J_q for the pressure row, 1 / J_q for the velocity rows
+    (or their locally conservative variants, see wadg_weights).
     In the orthonormal basis P_q = V_q^T diag(w_q).
     """
     ref = mesh.ref
-    Wu = 1.0 / mesh.J
-    Wp = Wu if c2q is None else c2q / mesh.J
+    Wp, Wu = wadg_weights(mesh, c2q, conservative)
     rq = np.einsum("qm,fkm->fkq", ref.Vq, r)
     rq[0] *= Wp
     rq[1:] *= Wu
@@ -224,7 +249,7 @@ def exact_mass_inverse(mesh: Mesh, r: np.ndarray, c2fun=None, qpts=None) -> np.n
 
 
 def rhs(mesh: Mesh, c: np.ndarray, variant: str = "wadg", tau_p=1.0, tau_u=1.0,
-        c2q=None, c2fun=None, form: str = "strong_weak") -> np.ndarray:
+        c2q=None, c2fun=None, form: str = "strong_weak", conservative: bool = False) -> np.ndarray:
     """dQ/dt = -M^{-1} A_h Q in modal coefficients (sign folded into a_h).
 
     form: "strong_weak" (default, the mesh's degree 2N+1 rules); "strong",
@@ -232,7 +257,8 @@ def rhs(mesh: Mesh, c: np.ndarray, variant: str = "wadg", tau_p=1.0, tau_u=1.0,
     4N-2 rules of strong_mesh (Sec. 4.1, energy stable); or
     "strong_underintegrated", the strong form on the mesh's degree 2N+1 rules
     (Sec. 6.5: faster, stability not guaranteed).  The mass inverse always
-    uses the mesh's degree 2N+1 volume rule (Sec. 6.2)."""
+    uses the mesh's degree 2N+1 volume rule (Sec. 6.2); conservative selects
+    the locally conservative weights of wadg_weights (variant "wadg")."""
     if form == "strong_weak":
         r = a_h(mesh, c, tau_p, tau_u)
     elif form == "strong":
@@ -242,7 +268,7 @@ def rhs(mesh: Mesh, c: np.ndarray, variant: str = "wadg", tau_p=1.0, tau_u=1.0,
     else:
         raise ValueError(form)
     if variant == "wadg":
-        return wadg_apply(mesh, r, c2q)
+        return wadg_apply(mesh, r, c2q, conservative)
     if variant == "exact":
         return exact_mass_inverse(mesh, r, c2fun)
     raise ValueError(variant)

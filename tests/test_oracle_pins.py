@@ -617,3 +617,82 @@ def test_strong_rhs_forms_select_rules():
     assert np.linalg.norm(full - under) > 1e-6 * np.linalg.norm(full)
     with pytest.raises(ValueError):
         W.rhs(mesh, c, form="weak")
+
+
+# ----------------------------------------------------------------------------
+# Local conservation (Sec. 3, after the moment estimate)
+# ----------------------------------------------------------------------------
+
+def _moments(mesh, r, c2q):
+    """Per element and field, sum_q w_q w(x_q) r(x_q) with the mass weights
+    w = J/c^2 (pressure) and J (velocity) at the volume points."""
+    ref = mesh.ref
+    vals = np.einsum("qm,fkm->fkq", ref.Vq, r)
+    w = np.broadcast_to(mesh.J, vals.shape).copy()
+    w[0] = mesh.J / c2q
+    return np.einsum("q,fkq->fk", ref.w_q, w * vals)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_conservative_weights_restore_local_conservation(N):
+    """With the mass weights projected onto P^N the update conserves every
+    element's zeroth moment exactly: sum_q w_q w_q r_q = b(1) for any load b
+    (curved mesh, heterogeneous c^2); with the pointwise weights it does not
+    (the moment error of the weight-adjusted inner product)."""
+    from synthetic import c2_heterogeneous
+    ref, mesh = _mesh(2, N)
+    c2q = c2_heterogeneous(mesh.xq)
+    b = np.random.default_rng(50 + N).standard_normal((4, mesh.K, ref.Np))
+    one = np.einsum("qm,q->m", ref.Vq, ref.w_q)           # modal coefficients of 1
+    want = np.einsum("fkm,m->fk", b, one)                  # b(1)
+    scale = np.abs(want).max()
+    got = _moments(mesh, W.wadg_apply(mesh, b, c2q, conservative=True), c2q)
+    assert np.abs(got - want).max() < 1e-12 * scale
+    plain = _moments(mesh, W.wadg_apply(mesh, b, c2q), c2q)
+    assert np.abs(plain - want).max() > 1e-8 * scale
+
+
+def test_conservative_weights_equal_pointwise_for_polynomial_jacobian():
+    """A global quadratic map has J of degree 3, in P^N for N = 3, so its
+    projection is J itself (the degree 7 rule integrates J phi exactly) and
+    the two weight sets coincide (c^2 = 1); a curved warp separates them."""
+    N = 3
+    VXYZ, EToV = kuhn_cube(2)
+    X = geometry_nodes(VXYZ, EToV, N, 0.0)
+    x, y, z = X[..., 0], X[..., 1], X[..., 2]
+    Xq = np.stack([x + 0.05 * y * y, y + 0.04 * z * z, z + 0.03 * x * x], -1)
+    mesh = Mesh(RefTet(N), VXYZ, EToV, Xq)
+    a, b = W.wadg_weights(mesh), W.wadg_weights(mesh, conservative=True)
+    assert np.abs(a[1] - b[1]).max() < 1e-12 * np.abs(a[1]).max()
+    assert np.abs(a[0] - b[0]).max() < 1e-12 * np.abs(a[0]).max()
+    _, curved = _mesh(2, N)
+    a, b = W.wadg_weights(curved), W.wadg_weights(curved, conservative=True)
+    assert np.abs(a[1] - b[1]).max() > 1e-6 * np.abs(a[1]).max()
+
+
+def test_point_source_zeroth_moment_on_curved_elements_with_conservative_weights():
+    """int J p_t = f(t) for a point source on curved elements holds to round-off
+    with the conservative weights, and only to the moment error otherwise."""
+    from oracle import sources as OS
+    ref, mesh = _mesh(2, 3)
+    src = OS.PointSet(mesh, [[0.13, -0.41, 0.27]])
+    amp = 0.7
+    b = OS.source_load(mesh, src, amp, 0)
+
+    def total(dq):
+        vals = np.einsum("qm,km->kq", ref.Vq, dq[0])
+        return float(np.sum(ref.w_q * mesh.J * vals))
+
+    assert abs(total(W.wadg_apply(mesh, b, conservative=True)) - amp) < 1e-13
+    assert abs(total(W.wadg_apply(mesh, b)) - amp) > 1e-9
+
+
+def test_rhs_conservative_flag_reaches_the_update():
+    """rhs(conservative=True) equals the conservative update of the same
+    functional, for both formulations it is offered with."""
+    ref, mesh = _mesh(2, 3)
+    c = np.random.default_rng(4).standard_normal((4, mesh.K, ref.Np))
+    for form, a_h in (("strong_weak", W.a_h), ("strong", lambda m, q, tp, tu: W.a_h_strong(W.strong_mesh(m), q, tp, tu))):
+        got = W.rhs(mesh, c, form=form, conservative=True)
+        want = W.wadg_apply(mesh, a_h(mesh, c, 1.0, 1.0), conservative=True)
+        assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
