@@ -170,6 +170,21 @@ int wadg_step(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nst
  * stays in effect. */
 int wadg_set_formulation(wadg_mesh* mesh, int form);
 
+/* Update weights (Sec. 3, the remark after the moment estimate): 0 = the
+ * pointwise weights W_p = c^2/J, W_u = 1/J at the volume points (the default,
+ * Sec. 6.2, Sec. 7); 1 = locally conservative weights W_p = 1 / Pi_N(J/c^2),
+ * W_u = 1 / Pi_N(J), the mass weights projected onto P^N with the volume rule
+ * (FP64, once), so that every element's update conserves its zeroth moment:
+ * sum_q w_q (J/c^2)_q dp/dt(x_q) equals the load functional at v = 1 (and
+ * likewise for u with J).  Applies to every precision and formulation
+ * (tensor cores included: the weights are part of the geometric factors).
+ * May be called before or after wadg_set_operators (which recomputes the
+ * weights when c^2 changes).  WADG_EGEOM if a projected weight is not
+ * positive at a volume point (the previous setting stays in effect).  The c^2
+ * gradient of the adjoint (wadg_step_record / wadg_step_adjoint with ystore)
+ * is built for the pointwise weights: WADG_EUNSUPPORTED under 1. */
+int wadg_set_conservation(wadg_mesh* mesh, int on);
+
 /* wadg_step on host fields: Q and res are HOST [4][K][S][Np] arrays in the
  * mesh precision (pinned memory gives the fastest copies), copied to device
  * buffers owned by the mesh, stepped nsteps times, and copied back before the

@@ -47,6 +47,7 @@ from .api import (  # noqa: E402,F401
     wadg_step,
     wadg_step_host,
     wadg_set_formulation,
+    wadg_set_conservation,
     FORMULATIONS,
     wadg_step_adjoint,
     wadg_step_record,

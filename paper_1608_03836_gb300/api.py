@@ -171,6 +171,12 @@ def wadg_set_formulation(mesh: MeshHandle, form: str):
     _check(load().wadg_set_formulation(mesh.handle, FORMULATIONS[form]), "wadg_set_formulation", mesh)
 
 
+def wadg_set_conservation(mesh: MeshHandle, on: bool):
+    """Locally conservative update weights (True) or the pointwise ones
+    (False, the default); see include/wadg.h."""
+    _check(load().wadg_set_conservation(mesh.handle, 1 if on else 0), "wadg_set_conservation", mesh)
+
+
 def wadg_step_host(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, stream=None):
     """wadg_step on host tensors (CPU, contiguous, the mesh precision; pinned
     memory gives the fastest copies): copied in, stepped, copied back."""

@@ -105,8 +105,8 @@ __global__ void geo_face_copy_kernel(int64_t K, int Nfq, const int32_t* __restri
 
 template <typename T>
 __global__ void geo_pack_kernel(int64_t K, int Nq, int Nfq, const double* __restrict__ J, const double* __restrict__ G,
-                                const double* __restrict__ c2, const double* __restrict__ nJ, T* __restrict__ vgeo,
-                                T* __restrict__ fgeo) {
+                                const double* __restrict__ c2, const double* __restrict__ Wpu, const double* __restrict__ nJ,
+                                T* __restrict__ vgeo, T* __restrict__ fgeo) {
   const int64_t nv = K * Nq, nf = K * 3 * 4 * Nfq;
   for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nv + nf; it += (int64_t)gridDim.x * blockDim.x) {
     if (it < nv) {
@@ -114,8 +114,8 @@ __global__ void geo_pack_kernel(int64_t K, int Nq, int Nfq, const double* __rest
       const int q = (int)(it % Nq);
       const double Jq = J[it];
       for (int c = 0; c < 9; ++c) vgeo[(k * 11 + c) * Nq + q] = (T)G[(k * 9 + c) * Nq + q];
-      vgeo[(k * 11 + 9) * Nq + q] = (T)((c2 ? c2[it] : 1.0) / Jq);
-      vgeo[(k * 11 + 10) * Nq + q] = (T)(1.0 / Jq);
+      vgeo[(k * 11 + 9) * Nq + q] = (T)(Wpu ? Wpu[(k * 2) * Nq + q] : (c2 ? c2[it] : 1.0) / Jq);
+      vgeo[(k * 11 + 10) * Nq + q] = (T)(Wpu ? Wpu[(k * 2 + 1) * Nq + q] : 1.0 / Jq);
     } else {
       const int64_t j = it - nv;
       fgeo[j] = (T)nJ[j];
@@ -130,8 +130,8 @@ __global__ void geo_pack_kernel(int64_t K, int Nq, int Nfq, const double* __rest
 //   fgeo_il[k/128][d * 4 + face][q/4][k % 128][q % 4] (q < 4 ceil(Nfq/4)),
 // zero in the padding (points beyond Nq or Nfq, elements beyond K).
 __global__ void geo_pack_il_kernel(int64_t K, int Nq, int Nfq, const double* __restrict__ J, const double* __restrict__ G,
-                                   const double* __restrict__ c2, const double* __restrict__ nJ, float* __restrict__ vgeo,
-                                   float* __restrict__ fgeo) {
+                                   const double* __restrict__ c2, const double* __restrict__ Wpu,
+                                   const double* __restrict__ nJ, float* __restrict__ vgeo, float* __restrict__ fgeo) {
   const int nq4 = (Nq + 3) / 4, nf4 = (Nfq + 3) / 4;
   const int64_t Kt = (K + 127) / 128;
   const int64_t nv = Kt * 11 * nq4 * 512, nf = Kt * 12 * nf4 * 512;
@@ -152,6 +152,7 @@ __global__ void geo_pack_il_kernel(int64_t K, int Nq, int Nfq, const double* __r
       if (k < K && q < Nq) {
         const double Jq = J[k * Nq + q];
         if (row < 9) v = (float)G[(k * 9 + row) * Nq + q];
+        else if (Wpu) v = (float)Wpu[(k * 2 + (row - 9)) * Nq + q];
         else if (row == 9) v = (float)((c2 ? c2[k * Nq + q] : 1.0) / Jq);
         else v = (float)(1.0 / Jq);
       }
@@ -180,8 +181,8 @@ template cudaError_t launch_to_precision<float>(int64_t, const double*, float*, 
 template cudaError_t launch_to_precision<double>(int64_t, const double*, double*, cudaStream_t);
 
 cudaError_t launch_geo_pack_il(int64_t K, int Nq, int Nfq, const double* J, const double* G, const double* c2,
-                               const double* nJ, float* vgeo_il, float* fgeo_il, cudaStream_t st) {
-  geo_pack_il_kernel<<<2048, 256, 0, st>>>(K, Nq, Nfq, J, G, c2, nJ, vgeo_il, fgeo_il);
+                               const double* Wpu, const double* nJ, float* vgeo_il, float* fgeo_il, cudaStream_t st) {
+  geo_pack_il_kernel<<<2048, 256, 0, st>>>(K, Nq, Nfq, J, G, c2, Wpu, nJ, vgeo_il, fgeo_il);
   return cudaGetLastError();
 }
 
@@ -325,8 +326,49 @@ cudaError_t launch_geo_face(int64_t K, int Np, int Nfq, const double* X, const d
 
 template <typename T>
 cudaError_t launch_geo_pack(int64_t K, int Nq, int Nfq, const double* J, const double* G, const double* c2,
-                            const double* nJ, T* vgeo, T* fgeo, cudaStream_t st) {
-  geo_pack_kernel<T><<<2048, 256, 0, st>>>(K, Nq, Nfq, J, G, c2, nJ, vgeo, fgeo);
+                            const double* Wpu, const double* nJ, T* vgeo, T* fgeo, cudaStream_t st) {
+  geo_pack_kernel<T><<<2048, 256, 0, st>>>(K, Nq, Nfq, J, G, c2, Wpu, nJ, vgeo, fgeo);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Locally conservative weights (Sec. 3, the remark after the moment estimate):
+// the mass weights w_p = J/c^2 and w_u = J are replaced by their projections
+// onto P^N within the weight-adjusted inner product, Pi_N w = V_q P_q w_q, and
+// the update uses W = 1 / Pi_N w at the volume points.  Wpu [K][2][Nq]
+// (pressure, velocity).  One block per element, FP64.
+// ---------------------------------------------------------------------------
+__global__ void geo_conservative_kernel(int64_t K, int Np, int Nq, const double* __restrict__ J,
+                                        const double* __restrict__ c2, const double* __restrict__ Vq,
+                                        const double* __restrict__ Pq, double* __restrict__ Wpu,
+                                        int* __restrict__ nbad) {
+  extern __shared__ double sw[];
+  double* f = sw;            // [Nq]
+  double* coef = sw + Nq;    // [Np]
+  const int64_t k = blockIdx.x;
+  for (int kind = 0; kind < 2; ++kind) {
+    for (int q = threadIdx.x; q < Nq; q += blockDim.x)
+      f[q] = J[k * Nq + q] / (kind == 0 && c2 ? c2[k * Nq + q] : 1.0);
+    __syncthreads();
+    for (int n = threadIdx.x; n < Np; n += blockDim.x) {
+      double acc = 0.0;
+      for (int q = 0; q < Nq; ++q) acc += Pq[n * Nq + q] * f[q];
+      coef[n] = acc;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < Nq; q += blockDim.x) {
+      double g = 0.0;
+      for (int n = 0; n < Np; ++n) g += Vq[q * Np + n] * coef[n];
+      if (!(g > 0.0)) atomicAdd(nbad, 1);
+      Wpu[(k * 2 + kind) * Nq + q] = 1.0 / g;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_geo_conservative(int64_t K, int Np, int Nq, const double* J, const double* c2, const double* Vq,
+                                    const double* Pq, double* Wpu, int* nbad, cudaStream_t st) {
+  geo_conservative_kernel<<<(unsigned)K, 128, (Nq + Np) * sizeof(double), st>>>(K, Np, Nq, J, c2, Vq, Pq, Wpu, nbad);
   return cudaGetLastError();
 }
 
@@ -375,9 +417,9 @@ template cudaError_t launch_receivers_adjoint<double>(int, int, int, const doubl
 template cudaError_t launch_receivers_adjoint<float>(int, int, int, const float*, const int32_t*, const float*, float*,
                                                      cudaStream_t);
 template cudaError_t launch_geo_pack<double>(int64_t, int, int, const double*, const double*, const double*,
-                                             const double*, double*, double*, cudaStream_t);
+                                             const double*, const double*, double*, double*, cudaStream_t);
 template cudaError_t launch_geo_pack<float>(int64_t, int, int, const double*, const double*, const double*,
-                                            const double*, float*, float*, cudaStream_t);
+                                            const double*, const double*, float*, float*, cudaStream_t);
 template cudaError_t launch_project<double>(int64_t, int, int, int, const double*, const double*, const double*,
                                             const double*, double*, cudaStream_t);
 template cudaError_t launch_project<float>(int64_t, int, int, int, const double*, const double*, const double*,

@@ -10,11 +10,17 @@ cudaError_t launch_geo_volume(int64_t K, int Np, int Nq, const double* X, const 
                               double* G, double* xq, int* nbad, cudaStream_t st);
 cudaError_t launch_geo_face(int64_t K, int Np, int Nfq, const double* X, const double* Vfa, const uint8_t* owner,
                             const int32_t* EToE, const int32_t* EToF, double* nJ, cudaStream_t st);
+// Wpu (nullable): update weights [K][2][Nq] (pressure, velocity) replacing
+// c^2/J and 1/J (the locally conservative weights of launch_geo_conservative).
 template <typename T>
 cudaError_t launch_geo_pack(int64_t K, int Nq, int Nfq, const double* J, const double* G, const double* c2,
-                            const double* nJ, T* vgeo, T* fgeo, cudaStream_t st);
+                            const double* Wpu, const double* nJ, T* vgeo, T* fgeo, cudaStream_t st);
 cudaError_t launch_geo_pack_il(int64_t K, int Nq, int Nfq, const double* J, const double* G, const double* c2,
-                               const double* nJ, float* vgeo_il, float* fgeo_il, cudaStream_t st);
+                               const double* Wpu, const double* nJ, float* vgeo_il, float* fgeo_il, cudaStream_t st);
+// Wpu [K][2][Nq] = 1 / Pi_N(J/c^2), 1 / Pi_N(J) at the volume points; nbad
+// counts points where a projected weight is not positive.
+cudaError_t launch_geo_conservative(int64_t K, int Np, int Nq, const double* J, const double* c2, const double* Vq,
+                                    const double* Pq, double* Wpu, int* nbad, cudaStream_t st);
 // out[i] = (T) in[i], i < n.
 template <typename T>
 cudaError_t launch_to_precision(int64_t n, const double* in, T* out, cudaStream_t st);

@@ -159,6 +159,33 @@ int upload_ops(wadg_mesh* m, DevOps<T>& ops) {
   return WADG_OK;
 }
 
+// The update weights of the locally conservative variant (m->d_Wpu), or
+// nothing for the pointwise weights; depends on J and c^2.
+int conservative_weights(wadg_mesh* m) {
+  if (!m->conservative) {
+    dfree(m->d_Wpu);
+    return WADG_OK;
+  }
+  const RefOps& o = m->ref;
+  const int64_t K = m->K;
+  if (!m->d_Wpu) WADG_CUDA(m, cudaMalloc((void**)&m->d_Wpu, (size_t)K * 2 * o.Nq * 8));
+  int* d_nbad = nullptr;
+  WADG_CUDA(m, cudaMalloc((void**)&d_nbad, sizeof(int)));
+  int nbad = 0;
+  const double* dVq = m->d_ref64;
+  const double* dPq = dVq + 4 * (size_t)o.Nq * o.Np;  // after Vq and the three Vqa
+  cudaError_t e = cudaMemset(d_nbad, 0, sizeof(int));
+  if (e == cudaSuccess) e = launch_geo_conservative(K, o.Np, o.Nq, m->d_J, m->d_c2, dVq, dPq, m->d_Wpu, d_nbad, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(&nbad, d_nbad, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_nbad);
+  if (e != cudaSuccess) return cuda_fail(m, e, "conservative weights");
+  if (nbad > 0) {
+    dfree(m->d_Wpu);
+    return fail(m, WADG_EGEOM, "the projection of J or J/c^2 onto P^N is not positive at %d volume points", nbad);
+  }
+  return WADG_OK;
+}
+
 // Sizes of the strong-form stage tables for a runtime (N, form).
 struct StrongSizes {
   int nqs = 0, nfqs = 0, nqsc = 0, nfqsp = 0;
@@ -476,6 +503,7 @@ void wadg_mesh_destroy(wadg_mesh* m) {
   if (m->ops64.base) cudaFree(m->ops64.base);
   if (m->ops32.base) cudaFree(m->ops32.base);
   free_strong(m);
+  dfree(m->d_Wpu);
   dfree(m->d_Qtmp);
   dfree(m->d_red);
   dfree(m->d_tcops);
@@ -722,18 +750,23 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
     dfree(m->d_vgeo);
     dfree(m->d_fgeo);
   }
+  {
+    const int st = conservative_weights(m);
+    if (st != WADG_OK) return st;
+  }
+  const double* Wpu = m->conservative ? m->d_Wpu : nullptr;
   const size_t ts = tsize(precision);
   if (!m->d_vgeo) WADG_CUDA(m, cudaMalloc(&m->d_vgeo, (size_t)K * 11 * Nq * ts));
   if (!m->d_fgeo) WADG_CUDA(m, cudaMalloc(&m->d_fgeo, (size_t)K * 12 * Nfq * ts));
   if (precision == WADG_FP64) {
-    WADG_CUDA(m, launch_geo_pack<double>(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, m->d_nJ, (double*)m->d_vgeo,
+    WADG_CUDA(m, launch_geo_pack<double>(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, Wpu, m->d_nJ, (double*)m->d_vgeo,
                                          (double*)m->d_fgeo, 0));
     if (!m->ops64.base) {
       int st = upload_ops<double>(m, m->ops64);
       if (st != WADG_OK) return st;
     }
   } else {
-    WADG_CUDA(m, launch_geo_pack<float>(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, m->d_nJ, (float*)m->d_vgeo,
+    WADG_CUDA(m, launch_geo_pack<float>(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, Wpu, m->d_nJ, (float*)m->d_vgeo,
                                         (float*)m->d_fgeo, 0));
     if (!m->ops32.base) {
       int st = upload_ops<float>(m, m->ops32);
@@ -752,7 +785,7 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
       const int64_t nq4 = (Nq + 3) / 4, nf4 = (Nfq + 3) / 4;
       if (!m->d_vgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_vgeo_il, (size_t)Kt * 128 * 11 * nq4 * 4 * sizeof(float)));
       if (!m->d_fgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_fgeo_il, (size_t)Kt * 128 * 12 * nf4 * 4 * sizeof(float)));
-      WADG_CUDA(m, launch_geo_pack_il(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, m->d_nJ, m->d_vgeo_il, m->d_fgeo_il, 0));
+      WADG_CUDA(m, launch_geo_pack_il(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, Wpu, m->d_nJ, m->d_vgeo_il, m->d_fgeo_il, 0));
     }
   }
   if (!m->d_err) {
@@ -949,6 +982,41 @@ int wadg_set_formulation(wadg_mesh* m, int form) {
     return st;
   }
   if (form != prev) ++m->generation;  // a captured solve graph holds the other formulation's kernels
+  return WADG_OK;
+}
+
+int wadg_set_conservation(wadg_mesh* m, int on) {
+  if (!m) return WADG_EINVAL;
+  if (on != 0 && on != 1) return fail(m, WADG_EINVAL, "conservation %d (0 pointwise weights, 1 conservative)", on);
+  DeviceGuard g(m->device);
+  const int prev = m->conservative;
+  m->conservative = on;
+  if (m->precision >= 0 && on != prev) {
+    // repack the two weight rows of the geometric factors (all precisions)
+    int st = conservative_weights(m);
+    const double* Wpu = m->conservative ? m->d_Wpu : nullptr;
+    const RefOps& o = m->ref;
+    cudaError_t e = cudaSuccess;
+    if (st == WADG_OK) {
+      e = m->precision == WADG_FP64
+              ? launch_geo_pack<double>(m->K, o.Nq, o.Nfq, m->d_J, m->d_G, m->d_c2, Wpu, m->d_nJ,
+                                        (double*)m->d_vgeo, (double*)m->d_fgeo, 0)
+              : launch_geo_pack<float>(m->K, o.Nq, o.Nfq, m->d_J, m->d_G, m->d_c2, Wpu, m->d_nJ, (float*)m->d_vgeo,
+                                       (float*)m->d_fgeo, 0);
+      if (e == cudaSuccess && m->d_vgeo_il)
+        e = launch_geo_pack_il(m->K, o.Nq, o.Nfq, m->d_J, m->d_G, m->d_c2, Wpu, m->d_nJ, m->d_vgeo_il, m->d_fgeo_il, 0);
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) st = cuda_fail(m, e, "repacking the update weights");
+    }
+    if (st != WADG_OK) {
+      const std::string msg = m->last_error;
+      m->conservative = prev;
+      dfree(m->d_Wpu);
+      m->last_error = msg;
+      return st;
+    }
+  }
+  if (on != prev) ++m->generation;
   return WADG_OK;
 }
 
@@ -1204,6 +1272,8 @@ int wadg_step_record(wadg_mesh* m, void* Q, void* res, double t0, double dt, voi
   int st = check_ready(m);
   if (st != WADG_OK) return st;
   if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
+  if (m->conservative && ystore)
+    return fail(m, WADG_EUNSUPPORTED, "the c^2 gradient is built for the pointwise update weights");
   if (!Q || !res || Q == res || !aligned16(Q) || !aligned16(res))
     return fail(m, WADG_EINVAL, "Q and res must be distinct 16-byte aligned device pointers");
   if (!std::isfinite(dt) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "dt/t0");
@@ -1221,6 +1291,8 @@ int wadg_step_adjoint(wadg_mesh* m, void* lamQ, void* lamR, double dt, const voi
   if (!lamQ || !lamR || lamQ == lamR || !aligned16(lamQ) || !aligned16(lamR))
     return fail(m, WADG_EINVAL, "lambda_Q and lambda_res must be distinct 16-byte aligned device pointers");
   if ((dc2 != nullptr) != (ystore != nullptr)) return fail(m, WADG_EINVAL, "ystore and dc2 go together");
+  if (m->conservative && ystore)
+    return fail(m, WADG_EUNSUPPORTED, "the c^2 gradient is built for the pointwise update weights");
   if (!std::isfinite(dt)) return fail(m, WADG_EINVAL, "dt");
   DeviceGuard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;

@@ -203,6 +203,8 @@ struct wadg_mesh {
   void* d_sfgeo = nullptr;     // [K][3][4 NFQS]
   wadg::StrongOps<double> sops64;
   wadg::StrongOps<float> sops32;
+  int conservative = 0;        // 1: update weights 1 / Pi_N(J/c^2), 1 / Pi_N(J) (local conservation)
+  double* d_Wpu = nullptr;     // [K][2][Nq] those weights (FP64), while conservative
   void* d_hostQ = nullptr;     // device copies for wadg_step_host
   void* d_hostR = nullptr;
   size_t host_io_bytes = 0;

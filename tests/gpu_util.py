@@ -69,3 +69,56 @@ def to_torch(a, dtype):
 
 def random_Q(K, S, Np, seed):
     return random_fields((4, K, S, Np), seed)
+
+
+FACE_VERTS = ((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3))
+
+
+def face_neighbours(EToV):
+    """EToE (K, 4) from matching sorted vertex triples, -1 on the boundary."""
+    EToV = np.asarray(EToV, dtype=np.int64)
+    K = len(EToV)
+    tri = np.sort(EToV[:, np.array(FACE_VERTS)], axis=2).reshape(-1, 3)
+    nv = int(EToV.max()) + 1
+    key = (tri[:, 0] * nv + tri[:, 1]) * nv + tri[:, 2]
+    order = np.argsort(key, kind="stable")
+    sk = key[order]
+    i = np.nonzero(sk[1:] == sk[:-1])[0]
+    a, b = order[i], order[i + 1]
+    E = -np.ones(4 * K, dtype=np.int64)
+    E[a] = b // 4
+    E[b] = a // 4
+    return E.reshape(K, 4)
+
+
+def sample_columns(EToV, S, count, seed):
+    """Seeded (element, shot) columns: the first and last element, elements
+    with a boundary face, and random ones."""
+    rng = np.random.default_rng(seed)
+    K = len(EToV)
+    bd = np.nonzero((face_neighbours(EToV) < 0).any(1))[0]
+    ks = [0, K - 1] + list(rng.choice(bd, size=min(len(bd), count // 4), replace=False))
+    ks += list(rng.choice(K, size=count - len(ks), replace=False))
+    return [(int(k), int(rng.integers(S))) for k in ks]
+
+
+def sampled_oracle_rhs(VXYZ, EToV, geom, N, Q, cols, c2fun=None, c2q_all=None, **kw):
+    """The oracle's RHS at sampled columns (k, s) of a large mesh, nodal,
+    shape (4, len(cols), Np).  The RHS of element k depends only on k and its
+    face neighbours, so each column is evaluated on that sub-mesh; its
+    elements keep their increasing global order, so every shared face keeps
+    its owner (the lower index) and its quadrature points.  c^2 at the volume
+    points: c2fun(x), or per-point values c2q_all (K, Nq), or 1."""
+    from oracle import wadg as OW
+    from oracle.discretization import Mesh, RefTet
+    EToV = np.asarray(EToV)
+    ref = RefTet(N)
+    E = face_neighbours(EToV)
+    out = []
+    for k, s in cols:
+        ks = np.unique(np.concatenate([[k], E[k][E[k] >= 0]]))
+        sub = Mesh(ref, VXYZ, EToV[ks], geom[ks])
+        c2q = c2q_all[ks] if c2q_all is not None else (None if c2fun is None else c2fun(sub.xq))
+        r = OW.rhs_nodal(sub, Q[:, ks, s], c2q=c2q, **kw)
+        out.append(r[:, int(np.nonzero(ks == k)[0][0])])
+    return np.stack(out, 1)
