@@ -269,7 +269,8 @@ def accuracy(W):
     steps in every precision; L2 error of p against the analytic solution at T
     by the volume rule.  Two meshes: 8^3 x 6 tets at N = 3 (discretisation
     error well above FP32 rounding) and 16^3 x 6 tets at N = 4 (discretisation
-    error near the FP32 floor)."""
+    error near the FP32 floor).  fp64_conservative: the FP64 path with the
+    locally conservative update weights."""
     import torch
     from synthetic import warped_cube, standing_wave
     out = {}
@@ -279,9 +280,11 @@ def accuracy(W):
         h = 2.0 / n
         dt_max = 0.5 * (h / 2) / (N + 1) ** 2
         case = {"workload": f"warped cube {n}^3x6, N={N}, c^2=1, standing wave to T={T}, dt_max={dt_max:.3e}"}
-        for prec in ("fp64", "fp32", "fp32_3xbf16", "fp32_tf32"):
+        for prec in ("fp64", "fp32", "fp32_3xbf16", "fp32_tf32", "fp64_conservative"):
             m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
-            W.wadg_set_operators(m, prec, 1, 1.0, 1.0, None)
+            W.wadg_set_operators(m, prec.replace("_conservative", ""), 1, 1.0, 1.0, None)
+            if prec.endswith("_conservative"):
+                W.wadg_set_conservation(m, True)
             xq = W.wadg_volume_points(m)
             Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
             W.wadg_project(m, torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda(), Q)
@@ -290,7 +293,7 @@ def accuracy(W):
             err = W.wadg_l2_error(m, Q, torch.from_numpy(standing_wave(xq, T)[:, :, None, :]).cuda(), 1)
             case[prec] = {"l2_error_p": err, "nsteps": nsteps}
         e64 = case["fp64"]["l2_error_p"]
-        for prec in ("fp32", "fp32_3xbf16", "fp32_tf32"):
+        for prec in ("fp32", "fp32_3xbf16", "fp32_tf32", "fp64_conservative"):
             case[prec]["ratio_to_fp64"] = case[prec]["l2_error_p"] / e64
             case[prec]["equal_l2_error"] = bool(case[prec]["l2_error_p"] <= 1.05 * e64)
         out[f"n{n}_N{N}"] = case
