@@ -63,16 +63,22 @@ FACE_ORIENT = np.array([-1.0, 1.0, 1.0, -1.0])
 class RefTet:
     """Modal reference operators for degree N (M^ = I in this basis)."""
 
-    def __init__(self, N: int, qdeg_pts: int | None = None, face_pts: int | None = None):
+    def __init__(self, N: int, qdeg_pts: int | None = None, face_pts: int | None = None, volume_rule=None):
         """Collapsed rules with qdeg_pts points per direction on the volume
         and face_pts on the faces (defaults: N+1, exact to degree 2N+1;
-        face_pts defaults to qdeg_pts)."""
+        face_pts defaults to qdeg_pts), or an explicit volume rule
+        volume_rule = (rst (n, 3), w (n,)) on the reference tetrahedron with the
+        default face rule."""
         self.N = N
         self.Np = (N + 1) * (N + 2) * (N + 3) // 6
         self.Nfp = (N + 1) * (N + 2) // 2
         nq = N + 1 if qdeg_pts is None else qdeg_pts
         nf = nq if face_pts is None else face_pts
-        self.rst_q, self.w_q = P.tet_rule(nq)               # degree 2 nq - 1 volume rule
+        if volume_rule is None:
+            self.rst_q, self.w_q = P.tet_rule(nq)           # degree 2 nq - 1 volume rule
+        else:
+            self.rst_q = np.asarray(volume_rule[0], dtype=np.float64)
+            self.w_q = np.asarray(volume_rule[1], dtype=np.float64)
         self.Nq = len(self.w_q)
         self.rs_f, self.w_f = P.tri_rule(nf)                # degree 2 nf - 1 face rule
         self.Nfq = len(self.w_f)

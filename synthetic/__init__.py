@@ -2,8 +2,10 @@
 
 This package describes inputs only: mesh topology, vertex and curved
 geometry-node coordinates, material fields, initial data, source and receiver
-positions.  It holds none of the discretisation arithmetic (no quadrature, no
-basis, no geometric factors, no operators); the oracle and the CUDA library
+positions, and the tabulated fewer-point volume rules (quadrature.py: stored
+points and weights, an input like the paper's tabulated rules).  It holds none
+of the discretisation arithmetic (no basis, no geometric factors, no
+operators, no rule construction at run time); the oracle and the CUDA library
 each compute those on their own from what is produced here.
 """
 from .warped_cube import (  # noqa: F401
@@ -23,3 +25,4 @@ from .warped_cube import (  # noqa: F401
     receiver_positions,
     random_fields,
 )
+from .quadrature import SYMMETRIC_RULES, symmetric_rule, fewer_point_rule  # noqa: F401

@@ -696,3 +696,82 @@ def test_rhs_conservative_flag_reaches_the_update():
         got = W.rhs(mesh, c, form=form, conservative=True)
         want = W.wadg_apply(mesh, a_h(mesh, c, 1.0, 1.0), conservative=True)
         assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
+# ----------------------------------------------------------------------------
+# Fewer-point symmetric volume rules (tabulated inputs)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,npts", [(3, 35), (4, 63)])
+def test_fewer_point_rules_exact_to_2N_plus_1_and_not_beyond(N, npts):
+    """Every monomial of degree <= 2N+1 integrates exactly (closed form), some
+    of degree 2N+2 do not; positive weights, interior points."""
+    from synthetic import fewer_point_rule
+    rst, w = fewer_point_rule(N)
+    assert len(w) == npts and w.min() > 0
+    lam = np.column_stack([-(1 + rst.sum(1)) / 2, (1 + rst) / 2])
+    assert lam.min() > 0
+    worst, beyond = 0.0, 0.0
+    for a in range(2 * N + 3):
+        for b in range(2 * N + 3 - a):
+            for c in range(2 * N + 3 - a - b):
+                v = np.sum(w * (1 + rst[:, 0]) ** a * (1 + rst[:, 1]) ** b * (1 + rst[:, 2]) ** c)
+                e = abs(v - _tet_monomial(a, b, c)) / _tet_monomial(a, b, c)
+                if a + b + c <= 2 * N + 1:
+                    worst = max(worst, e)
+                else:
+                    beyond = max(beyond, e)
+    assert worst < 1e-12 and beyond > 1e-9
+
+
+@pytest.mark.parametrize("degree", [7, 9])
+def test_fewer_point_rules_are_symmetric(degree):
+    """The point set with its weights is invariant under the 24 vertex
+    permutations of the tetrahedron."""
+    from synthetic import symmetric_rule
+    rst, w = symmetric_rule(degree)
+    lam = np.column_stack([-(1 + rst.sum(1)) / 2, (1 + rst) / 2])
+    key = {tuple(np.round(l, 12)): wi for l, wi in zip(lam, w)}
+    assert len(key) == len(w)
+    for perm in __import__("itertools").permutations(range(4)):
+        for l, wi in zip(lam, w):
+            assert abs(key[tuple(np.round(l[list(perm)], 12))] - wi) < 1e-15
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_fewer_point_rule_rhs_equals_collapsed_rule_on_affine_elements(N):
+    """On affine elements with c^2 = 1 every integrand of the right-hand side
+    and of the update is a polynomial of degree <= 2N, which both rules
+    integrate exactly: the two discretisations coincide."""
+    from synthetic import fewer_point_rule
+    VXYZ, EToV, geom = warped_cube(2, N, 0.0)
+    a = Mesh(RefTet(N), VXYZ, EToV, geom)
+    b = Mesh(RefTet(N, volume_rule=fewer_point_rule(N)), VXYZ, EToV, geom)
+    assert b.ref.Nq < a.ref.Nq
+    c = np.random.default_rng(6).standard_normal((4, a.K, a.ref.Np))
+    ra, rb = W.rhs(a, c), W.rhs(b, c)
+    assert np.abs(ra - rb).max() < 1e-11 * np.abs(ra).max()
+    _, curved = _mesh(2, N)
+    cb = Mesh(RefTet(N, volume_rule=fewer_point_rule(N)), curved.VXYZ, curved.EToV, curved.geom_xyz)
+    d = np.abs(W.rhs(curved, c) - W.rhs(cb, c)).max() / np.abs(W.rhs(curved, c)).max()
+    assert 1e-10 < d < 1e-1     # curved: both rules under-integrate the rational integrands, differently
+
+
+def test_fewer_point_rule_has_the_collapsed_rule_accuracy():
+    """Standing wave on the curved 48-tet mesh, N = 3, to T = 0.1 (same dt):
+    the L2 errors against the analytic solution with the two degree-7 rules
+    agree within 5 %."""
+    from synthetic import fewer_point_rule
+    N, T = 3, 0.1
+    VXYZ, EToV, geom = warped_cube(2, N, 0.1)
+    errs = []
+    for rule in (None, fewer_point_rule(N)):
+        mesh = Mesh(RefTet(N, volume_rule=rule), VXYZ, EToV, geom)
+        c = W.wadg_projection(mesh, standing_wave(mesh.xq, 0.0))
+        res = np.zeros_like(c)
+        nst = 8
+        dt = T / nst
+        for k in range(nst):
+            c, res = W.lsrk_step(lambda q, t: W.rhs(mesh, q), c, res, k * dt, dt)
+        errs.append(W.l2_error(mesh, c, lambda x: standing_wave(x, T)))
+    assert abs(errs[1] - errs[0]) < 0.05 * errs[0], errs
