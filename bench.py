@@ -38,12 +38,13 @@ METRIC = "WADG RHS DOF*stage/s (RHS + weight-adjusted update + LSRK stage)"
 UNIT = "DOF*stage/s"
 
 
-def algorithmic(N: int, S: int, s: int):
+def algorithmic(N: int, S: int, s: int, nq: int | None = None):
     """Per element and stage: algorithmic bytes (fields read/written once,
     geometric factors read once, neighbour reads counted as L2 hits) and flops
-    (dense reference-operator products)."""
+    (dense reference-operator products); nq: points of the volume rule
+    (default the collapsed (N+1)^3)."""
     Np = (N + 1) * (N + 2) * (N + 3) // 6
-    Nq, Nfq = (N + 1) ** 3, (N + 1) ** 2
+    Nq, Nfq = ((N + 1) ** 3 if nq is None else nq), (N + 1) ** 2
     B = s * (16 * Np * S + 11 * Nq + 12 * Nfq) + 32
     F = (24 + 16) * Nq * Np * S + 16 * Np * 4 * Nfq * S
     return B, F
@@ -59,8 +60,15 @@ def peaks():
         return 6800.0, "fallback", 2070.0
 
 
+def headline_rule():
+    """The volume rule of the workload: the fewer-point symmetric rule exact
+    to degree 2N+1 where one is tabulated (N = 3, 4), else the collapsed rule."""
+    from synthetic import fewer_point_rule
+    return fewer_point_rule(WORKLOAD["N"]) if WORKLOAD["N"] in (3, 4) else None
+
+
 TC_SOURCES = ("paper_1608_03836_gb300/csrc/stage_tc.cu", "paper_1608_03836_gb300/csrc/tc_ops.cuh")
-TC_PROFILE = "profiles/stage_tc_kernel_n20_full.md"
+TC_PROFILE = "profiles/stage_tc_kernel_63pt_n20_full.md"
 
 
 def tc_source_hash() -> str:
@@ -150,11 +158,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_case(W, precision, rank):
+def build_case(W, precision, rank, rule=None):
     import torch
     from synthetic import warped_cube, c2_heterogeneous, standing_wave
     VXYZ, EToV, geom = warped_cube(WORKLOAD["n"], WORKLOAD["N"], WORKLOAD["warp"])
-    m = W.wadg_mesh_create(WORKLOAD["N"], VXYZ, EToV, geom)
+    m = W.wadg_mesh_create(WORKLOAD["N"], VXYZ, EToV, geom, rule=rule)
     xq = W.wadg_volume_points(m)
     W.wadg_set_operators(m, precision, 1, 1.0, 1.0, c2_heterogeneous(xq))
     fq = torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda()
@@ -269,8 +277,10 @@ def accuracy(W):
     steps in every precision; L2 error of p against the analytic solution at T
     by the volume rule.  Two meshes: 8^3 x 6 tets at N = 3 (discretisation
     error well above FP32 rounding) and 16^3 x 6 tets at N = 4 (discretisation
-    error near the FP32 floor).  fp64_conservative: the FP64 path with the
-    locally conservative update weights."""
+    error near the FP32 floor).  All on the fewer-point symmetric volume rule
+    (35 points at N = 3, 63 at N = 4) except fp64_collapsed_rule (the (N+1)^3
+    rule); fp64_conservative: the FP64 path with the locally conservative
+    update weights."""
     import torch
     from synthetic import warped_cube, standing_wave
     out = {}
@@ -280,9 +290,11 @@ def accuracy(W):
         h = 2.0 / n
         dt_max = 0.5 * (h / 2) / (N + 1) ** 2
         case = {"workload": f"warped cube {n}^3x6, N={N}, c^2=1, standing wave to T={T}, dt_max={dt_max:.3e}"}
-        for prec in ("fp64", "fp32", "fp32_3xbf16", "fp32_tf32", "fp64_conservative"):
-            m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
-            W.wadg_set_operators(m, prec.replace("_conservative", ""), 1, 1.0, 1.0, None)
+        from synthetic import fewer_point_rule
+        for prec in ("fp64", "fp32", "fp32_3xbf16", "fp32_tf32", "fp64_conservative", "fp64_collapsed_rule"):
+            collapsed = prec.endswith("_collapsed_rule")
+            m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=None if collapsed else fewer_point_rule(N))
+            W.wadg_set_operators(m, prec.split("_c")[0], 1, 1.0, 1.0, None)
             if prec.endswith("_conservative"):
                 W.wadg_set_conservation(m, True)
             xq = W.wadg_volume_points(m)
@@ -293,7 +305,7 @@ def accuracy(W):
             err = W.wadg_l2_error(m, Q, torch.from_numpy(standing_wave(xq, T)[:, :, None, :]).cuda(), 1)
             case[prec] = {"l2_error_p": err, "nsteps": nsteps}
         e64 = case["fp64"]["l2_error_p"]
-        for prec in ("fp32", "fp32_3xbf16", "fp32_tf32", "fp64_conservative"):
+        for prec in ("fp32", "fp32_3xbf16", "fp32_tf32", "fp64_conservative", "fp64_collapsed_rule"):
             case[prec]["ratio_to_fp64"] = case[prec]["l2_error_p"] / e64
             case[prec]["equal_l2_error"] = bool(case[prec]["l2_error_p"] <= 1.05 * e64)
         out[f"n{n}_N{N}"] = case
@@ -433,7 +445,7 @@ class OracleSample:
         self.OW = OW
         n, N = 16, WORKLOAD["N"]
         VXYZ, EToV, geom = warped_cube(n, N, WORKLOAD["warp"])
-        self.ref = RefTet(N)
+        self.ref = RefTet(N, volume_rule=headline_rule())
         self.mesh = Mesh(self.ref, VXYZ, EToV, geom)
         self.c2 = c2_heterogeneous(self.mesh.xq)
         self.c = self.ref.to_modal(random_fields((4, self.mesh.K, self.ref.Np), 1))
@@ -450,8 +462,8 @@ class OracleSample:
         return time.perf_counter() - t0
 
     def describe(self, stages, seconds):
-        return (f"warped cube 16^3 x 6 = {self.mesh.K} tets, N={self.ref.N}, heterogeneous c^2, FP64, "
-                f"{stages} stages in {seconds:.1f} s (1 thread)")
+        return (f"warped cube 16^3 x 6 = {self.mesh.K} tets, N={self.ref.N}, {self.ref.Nq}-point volume rule, "
+                f"heterogeneous c^2, FP64, {stages} stages in {seconds:.1f} s (1 thread)")
 
 
 def cpu_baseline(budget_s: float = 20.0):
@@ -502,8 +514,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic", "vs_baseline": None,
-            "config": {"workload": "warped Kuhn cube, N=4, heterogeneous c^2; FP64 oracle on a 16^3x6 = 24576-tet "
-                                   "sample of the 196608-tet workload, one stage per step"},
+            "config": {"workload": "warped Kuhn cube, N=4, 63-point symmetric volume rule, heterogeneous c^2; FP64 "
+                                   "oracle on a 16^3x6 = 24576-tet sample of the 196608-tet workload, one stage per step",
+                       "volume_points": o.ref.Nq},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": o.describe(args.steps, t), "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -553,7 +566,8 @@ def main():
             dist.barrier()
 
     headline = "fp32_3xbf16"
-    m, Q = build_case(W, headline, rank)
+    rule = headline_rule()
+    m, Q = build_case(W, headline, rank, rule=rule)
     Np, K = m.Np, m.K
     dof = 4 * K * Np
     barrier()
@@ -568,17 +582,31 @@ def main():
     e2e_ms, nbytes = e2e_steps(W, m, Q, max(2, args.steps // 2))
     e2e_value = ws * dof * 5 / (e2e_ms * 1e-3)
     hbm, peak_kind, sm_max = peaks()
-    B, F = algorithmic(WORKLOAD["N"], 1, 4)
+    nq = m.Nq
+    B, F = algorithmic(WORKLOAD["N"], 1, 4, nq=nq)
     achieved_gbs = B * K / (stage_ms * 1e-3) / 1e9
     achieved_tf = F * K / (stage_ms * 1e-3) / 1e12
     tpe = tc_traffic_per_element()
     variants = {headline: {"value": value, "ms_per_step": ms_per_step, "stage_ms": stage_ms,
                            "achieved_tflops": achieved_tf, "achieved_gbs": achieved_gbs,
-                           "dtype": "f32 fields, bf16x3 tensor products"}}
+                           "dtype": "f32 fields, bf16x3 tensor products", "volume_points": nq}}
     del Q, m
     torch.cuda.empty_cache()
 
-    mtf, Qtf = build_case(W, "fp32_tf32", rank)
+    # the same precision on the collapsed (N+1)^3 rule
+    mc, Qc = build_case(W, headline, rank)
+    tcl, scl = time_steps(W, mc, Qc, args.steps, 3)
+    W.wadg_device_status(mc)
+    Bc, _ = algorithmic(WORKLOAD["N"], 1, 4)
+    variants[headline + "_collapsed_rule"] = {
+        "value": ws * dof * 5 / (tcl / args.steps * 1e-3), "ms_per_step": tcl / args.steps, "stage_ms": scl,
+        "achieved_gbs": Bc * K / (scl * 1e-3) / 1e9, "hbm_frac": Bc * K / (scl * 1e-3) / 1e9 / hbm,
+        "algorithmic_bytes_per_element": Bc, "volume_points": mc.Nq,
+        "dtype": "f32 fields, bf16x3 tensor products"}
+    del Qc, mc
+    torch.cuda.empty_cache()
+
+    mtf, Qtf = build_case(W, "fp32_tf32", rank, rule=rule)
     ttf, stf = time_steps(W, mtf, Qtf, args.steps, 3)
     W.wadg_device_status(mtf)
     variants["fp32_tf32"] = {"value": ws * dof * 5 / (ttf / args.steps * 1e-3), "ms_per_step": ttf / args.steps,
@@ -588,7 +616,7 @@ def main():
     torch.cuda.empty_cache()
 
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, CUDA-core FMA
-    m32, Q32 = build_case(W, "fp32", rank)
+    m32, Q32 = build_case(W, "fp32", rank, rule=rule)
     t32, s32 = time_steps(W, m32, Q32, args.steps, 3)
     variants["fp32"] = {"value": ws * dof * 5 / (t32 / args.steps * 1e-3), "ms_per_step": t32 / args.steps,
                         "stage_ms": s32, "achieved_tflops": F * K / (s32 * 1e-3) / 1e12,
@@ -597,10 +625,10 @@ def main():
     del Q32, m32
     torch.cuda.empty_cache()
     if not args.no_fp64:
-        m64, Q64 = build_case(W, "fp64", rank)
+        m64, Q64 = build_case(W, "fp64", rank, rule=rule)
         t64, s64 = time_steps(W, m64, Q64, max(1, args.steps // 5), 3)
         ms64 = t64 / max(1, args.steps // 5)
-        B64, _ = algorithmic(WORKLOAD["N"], 1, 8)
+        B64, _ = algorithmic(WORKLOAD["N"], 1, 8, nq=nq)
         variants["fp64"] = {"value": ws * dof * 5 / (ms64 * 1e-3), "ms_per_step": ms64, "stage_ms": s64,
                             "achieved_tflops": F * K / (s64 * 1e-3) / 1e12,
                             "achieved_gbs": B64 * K / (s64 * 1e-3) / 1e9, "dtype": "f64"}
@@ -623,15 +651,17 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3/f32", "data": "synthetic",
         "config": {"workload": f"warped Kuhn cube {WORKLOAD['n']}^3x6 = {K} curved tets, N=4 (Np=35), "
-                               "heterogeneous c^2, 1 shot, LSRK(5,4) step = 5 fused stage launches",
+                               f"{nq}-point symmetric volume rule exact to degree 9, heterogeneous c^2, 1 shot, "
+                               "LSRK(5,4) step = 5 fused stage launches",
+                   "volume_points": nq,
                    "elements": K, "N": WORKLOAD["N"], "shots": 1, "dof": dof, "precision": headline,
-                   "l2": "inputs larger than L2 (1.1 GB FP32 geometric factors)",
+                   "l2": "inputs larger than L2 (0.55 GB FP32 geometric factors)",
                    "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                      "frac": achieved_gbs / hbm,
                      "traffic": None if tpe is None else tpe * K,
                      "peak_kind": peak_kind,
-                     "kernel": "stage_tc_kernel<4,1> (one launch = one LSRK stage over all elements)",
+                     "kernel": f"stage_tc_kernel<4,1,0,{nq}> (one launch = one LSRK stage over all elements)",
                      "algorithmic_bytes_per_element": B,
                      "tensor": {"achieved_fp32_equiv_tflops": achieved_tf,
                                 "note": "flops counted once per product; each runs as three bf16 MMAs"}},

@@ -97,6 +97,21 @@ int wadg_version(void);
 int wadg_mesh_create(int N, int64_t Nv, const double* VXYZ, int64_t K, const int64_t* EToV,
                      const double* geom_xyz, wadg_mesh** out);
 
+/* wadg_mesh_create with an explicit volume rule: nq points
+ * rule[q] = (r, s, t, w) on the reference tetrahedron (vertices (-1,-1,-1),
+ * (1,-1,-1), (-1,1,-1), (-1,-1,1); weights positive, summing to its volume
+ * 4/3), used for the volume terms, the weight-adjusted update, the
+ * geometric factors, c^2 and the diagnostics; the face rule stays the
+ * collapsed one.  It must be exact to degree 2N (checked: P_q V_q = I,
+ * WADG_EUNSUPPORTED otherwise) and should be exact to 2N+1 (Sec. 4, Sec. 6.2).
+ * The stage kernels are built for nq = (N+1)^3 and for the fewer-point
+ * symmetric rules with nq = 35 (N = 3) and 63 (N = 4); other sizes are
+ * WADG_EUNSUPPORTED.  With the fewer-point sizes the strong formulations, the
+ * adjoint and batches are not available (WADG_EUNSUPPORTED / WADG_ESTATE).
+ * rule = NULL is wadg_mesh_create. */
+int wadg_mesh_create_rule(int N, int64_t Nv, const double* VXYZ, int64_t K, const int64_t* EToV,
+                          const double* geom_xyz, int nq, const double* rule, wadg_mesh** out);
+
 /* Select precision and material, and allocate the library's work buffers.
  *   precision WADG_FP64 or WADG_FP32.
  *   shots     S >= 1 right-hand sides sharing the mesh (columns [K][S]).

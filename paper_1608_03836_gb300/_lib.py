@@ -15,6 +15,8 @@ P_int64 = ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
     "wadg_version": (c_int, []),
     "wadg_mesh_create": (c_int, [c_int, c_int64, P_double, c_int64, P_int64, P_double, ctypes.POINTER(c_void_p)]),
+    "wadg_mesh_create_rule": (c_int, [c_int, c_int64, P_double, c_int64, P_int64, P_double, c_int, P_double,
+                                      ctypes.POINTER(c_void_p)]),
     "wadg_set_operators": (c_int, [c_void_p, c_int, c_int, c_double, c_double, P_double]),
     "wadg_device_status": (c_int, [c_void_p, c_void_p]),
     "wadg_selftest_bounded_wait": (c_int, [c_void_p, ctypes.c_uint32, c_void_p]),

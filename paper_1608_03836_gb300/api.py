@@ -69,15 +69,24 @@ def wadg_version() -> int:
     return load().wadg_version()
 
 
-def wadg_mesh_create(N: int, VXYZ, EToV, geom_xyz=None) -> MeshHandle:
+def wadg_mesh_create(N: int, VXYZ, EToV, geom_xyz=None, rule=None) -> MeshHandle:
+    """rule: None (the collapsed (N+1)^3 volume rule) or (rst (nq, 3), w (nq,))
+    on the reference tetrahedron (wadg_mesh_create_rule)."""
     lib = load()
     V = np.ascontiguousarray(VXYZ, dtype=np.float64)
     E = np.ascontiguousarray(EToV, dtype=np.int64)
     G = None if geom_xyz is None else np.ascontiguousarray(geom_xyz, dtype=np.float64)
     out = ctypes.c_void_p()
-    st = lib.wadg_mesh_create(int(N), V.shape[0], _dptr(V), E.shape[0],
-                              E.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                              None if G is None else _dptr(G), ctypes.byref(out))
+    if rule is None:
+        st = lib.wadg_mesh_create(int(N), V.shape[0], _dptr(V), E.shape[0],
+                                  E.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  None if G is None else _dptr(G), ctypes.byref(out))
+    else:
+        rst, w = rule
+        R = np.ascontiguousarray(np.column_stack([np.asarray(rst, dtype=np.float64), np.asarray(w, dtype=np.float64)]))
+        st = lib.wadg_mesh_create_rule(int(N), V.shape[0], _dptr(V), E.shape[0],
+                                       E.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       None if G is None else _dptr(G), R.shape[0], _dptr(R), ctypes.byref(out))
     _check(st, "wadg_mesh_create")
     return MeshHandle(out)
 

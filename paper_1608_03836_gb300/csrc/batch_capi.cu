@@ -155,8 +155,9 @@ int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
   if (!b) return WADG_ENOMEM;
   b->meshes.assign(meshes, meshes + count);
   for (int i = 0; i < count; ++i) {
+    const int n1 = meshes[i] ? meshes[i]->N + 1 : 0;
     if (!meshes[i] || meshes[i]->precision != WADG_FP32 || meshes[i]->form != 0 ||
-        meshes[i]->device != meshes[0]->device) {
+        meshes[i]->ref.Nq != n1 * n1 * n1 || meshes[i]->device != meshes[0]->device) {
       delete b;
       return WADG_ESTATE;
     }

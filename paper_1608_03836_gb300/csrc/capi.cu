@@ -186,6 +186,10 @@ int conservative_weights(wadg_mesh* m) {
   return WADG_OK;
 }
 
+// The mesh uses the collapsed (N+1)^3 volume rule (or another rule of that
+// size); the strong forms, the adjoint and batches are built for it only.
+bool collapsed_size(const wadg_mesh* m) { return m->ref.Nq == (m->N + 1) * (m->N + 1) * (m->N + 1); }
+
 // Sizes of the strong-form stage tables for a runtime (N, form).
 struct StrongSizes {
   int nqs = 0, nfqs = 0, nqsc = 0, nfqsp = 0;
@@ -525,14 +529,20 @@ void wadg_mesh_destroy(wadg_mesh* m) {
 
 int wadg_mesh_create(int N, int64_t Nv, const double* VXYZ, int64_t K, const int64_t* EToV, const double* geom_xyz,
                      wadg_mesh** out) {
+  return wadg_mesh_create_rule(N, Nv, VXYZ, K, EToV, geom_xyz, 0, nullptr, out);
+}
+
+int wadg_mesh_create_rule(int N, int64_t Nv, const double* VXYZ, int64_t K, const int64_t* EToV,
+                          const double* geom_xyz, int nq, const double* rule, wadg_mesh** out) {
   if (!out) return WADG_EINVAL;
   *out = nullptr;
   if (N < 1 || N > 6) return WADG_EUNSUPPORTED;
   if (Nv < 4 || K < 1 || K > (int64_t)1 << 30 || !VXYZ || !EToV) return WADG_EINVAL;
+  if (rule && nq != (N + 1) * (N + 1) * (N + 1) && nq != fewer_point_nq(N)) return WADG_EUNSUPPORTED;
   wadg_mesh* m = new (std::nothrow) wadg_mesh();
   if (!m) return WADG_ENOMEM;
   char err[256];
-  if (!build_refops(N, m->ref, err, sizeof(err))) {
+  if (!build_refops(N, m->ref, err, sizeof(err), rule ? nq : 0, rule)) {
     delete m;
     return WADG_EUNSUPPORTED;
   }
@@ -838,6 +848,7 @@ StageParams<T> base_params(const wadg_mesh* m) {
   p.sgeo = (const T*)m->d_sgeo;
   p.sfgeo = (const T*)m->d_sfgeo;
   p.sops = sops_of(m, T());
+  p.nq = m->ref.Nq;
   p.ncols = m->K * m->S;
   p.S = m->S;
   p.tau_p = (T)m->tau_p;
@@ -968,6 +979,8 @@ int wadg_set_formulation(wadg_mesh* m, int form) {
   if (form < 0 || form > 2)
     return fail(m, WADG_EINVAL, "formulation %d (0 strong-weak, 1 strong, 2 strong on the 2N+1 rules)", form);
   if (form != 0 && m->N > 5) return fail(m, WADG_EUNSUPPORTED, "the strong formulation is built for N <= 5");
+  if (form != 0 && !collapsed_size(m))
+    return fail(m, WADG_EUNSUPPORTED, "the strong formulation is built for the (N+1)^3-point volume rule");
   if (form != 0 && (m->precision == WADG_FP32_3XBF16 || m->precision == WADG_FP32_TF32))
     return fail(m, WADG_EUNSUPPORTED, "the strong formulation runs on the CUDA-core precisions (FP64, FP32)");
   DeviceGuard g(m->device);
@@ -1260,6 +1273,7 @@ int wadg_rhs_adjoint(wadg_mesh* m, const void* lam, void* out, wadg_stream strea
   int st = check_ready(m);
   if (st != WADG_OK) return st;
   if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
+  if (!collapsed_size(m)) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the (N+1)^3-point volume rule");
   if (!lam || !out || lam == out || !aligned16(lam) || !aligned16(out))
     return fail(m, WADG_EINVAL, "lambda and out must be distinct 16-byte aligned device pointers");
   DeviceGuard g(m->device);
@@ -1272,6 +1286,7 @@ int wadg_step_record(wadg_mesh* m, void* Q, void* res, double t0, double dt, voi
   int st = check_ready(m);
   if (st != WADG_OK) return st;
   if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
+  if (!collapsed_size(m)) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the (N+1)^3-point volume rule");
   if (m->conservative && ystore)
     return fail(m, WADG_EUNSUPPORTED, "the c^2 gradient is built for the pointwise update weights");
   if (!Q || !res || Q == res || !aligned16(Q) || !aligned16(res))
@@ -1288,6 +1303,7 @@ int wadg_step_adjoint(wadg_mesh* m, void* lamQ, void* lamR, double dt, const voi
   int st = check_ready(m);
   if (st != WADG_OK) return st;
   if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
+  if (!collapsed_size(m)) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the (N+1)^3-point volume rule");
   if (!lamQ || !lamR || lamQ == lamR || !aligned16(lamQ) || !aligned16(lamR))
     return fail(m, WADG_EINVAL, "lambda_Q and lambda_res must be distinct 16-byte aligned device pointers");
   if ((dc2 != nullptr) != (ystore != nullptr)) return fail(m, WADG_EINVAL, "ystore and dc2 go together");

@@ -314,7 +314,7 @@ bool build_rule_ops(const RefOps& o, int nv, int nf, RuleOps& out, char* err, in
   return true;
 }
 
-bool build_refops(int N, RefOps& o, char* err, int errlen) {
+bool build_refops(int N, RefOps& o, char* err, int errlen, int nq, const double* rule) {
   if (N < 1 || N > 6) {
     std::snprintf(err, errlen, "degree N=%d outside 1..6", N);
     return false;
@@ -322,7 +322,7 @@ bool build_refops(int N, RefOps& o, char* err, int errlen) {
   o.N = N;
   o.Np = (N + 1) * (N + 2) * (N + 3) / 6;
   o.Nfp = (N + 1) * (N + 2) / 2;
-  o.Nq = (N + 1) * (N + 1) * (N + 1);
+  o.Nq = rule ? nq : (N + 1) * (N + 1) * (N + 1);
   o.Nfq = (N + 1) * (N + 1);
   const int Np = o.Np, Nq = o.Nq, Nfp = o.Nfp, Nfq = o.Nfq, n1 = N + 1;
 
@@ -340,7 +340,31 @@ bool build_refops(int N, RefOps& o, char* err, int errlen) {
       }
 
   // rules
-  tet_rule(n1, o.rq, o.sq, o.tq, o.wq);
+  if (rule) {
+    if (nq < 1) {
+      std::snprintf(err, errlen, "volume rule with %d points", nq);
+      return false;
+    }
+    o.rq.resize(nq);
+    o.sq.resize(nq);
+    o.tq.resize(nq);
+    o.wq.resize(nq);
+    for (int q = 0; q < nq; ++q) {
+      o.rq[q] = rule[4 * q];
+      o.sq[q] = rule[4 * q + 1];
+      o.tq[q] = rule[4 * q + 2];
+      o.wq[q] = rule[4 * q + 3];
+      const double l0 = -(1.0 + o.rq[q] + o.sq[q] + o.tq[q]) / 2;
+      const bool inside = std::isfinite(l0) && l0 >= -1e-12 && o.rq[q] >= -1 - 1e-12 && o.sq[q] >= -1 - 1e-12 &&
+                          o.tq[q] >= -1 - 1e-12;
+      if (!inside || !(o.wq[q] > 0)) {
+        std::snprintf(err, errlen, "volume rule point %d is outside the tetrahedron or has weight <= 0", q);
+        return false;
+      }
+    }
+  } else {
+    tet_rule(n1, o.rq, o.sq, o.tq, o.wq);
+  }
   tri_rule(n1, o.rf, o.sf, o.wf);
 
   // Vandermonde at the lattice and its inverse

@@ -64,8 +64,11 @@ extern const int kPerm[6][3];
 // Reference outward normal times reference face area scale, per face.
 extern const double kFaceNormal[4][3];
 
-// Builds the operators; returns false (and a message) on failure.
-bool build_refops(int N, RefOps& ops, char* err, int errlen);
+// Builds the operators; returns false (and a message) on failure.  The volume
+// rule is the collapsed (N+1)^3 rule, or, when rule is given, its nq points
+// rule[q] = (r, s, t, w) on the reference tetrahedron (weights positive,
+// points inside; the operators are checked for P_q V_q = I).
+bool build_refops(int N, RefOps& ops, char* err, int errlen, int nq = 0, const double* rule = nullptr);
 
 // Gauss-Jacobi rule for the weight (1-x)^alpha (1+x)^beta, ascending nodes.
 void gauss_jacobi(int n, double alpha, double beta, double* x, double* w);

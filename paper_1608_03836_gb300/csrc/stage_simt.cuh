@@ -33,10 +33,12 @@
 
 namespace wadg {
 
-template <int N>
+// Sizes for degree N and a volume rule of NQX points (default: the collapsed
+// (N+1)^3 rule; fewer_point_nq(N) for the symmetric rules).
+template <int N, int NQX = (N + 1) * (N + 1) * (N + 1)>
 struct Dims {
   static constexpr int NP = (N + 1) * (N + 2) * (N + 3) / 6;
-  static constexpr int NQ = (N + 1) * (N + 1) * (N + 1);
+  static constexpr int NQ = NQX;
   static constexpr int NFP = (N + 1) * (N + 2) / 2;
   static constexpr int NFQ = (N + 1) * (N + 1);
   static constexpr int XV = 6 * NQ;                    // volume quadrature arrays
@@ -77,11 +79,11 @@ constexpr bool strong_mode(int mode) {
   return mode == kRhsStrong || mode == kLsrkStrong || mode == kRhsStrongU || mode == kLsrkStrongU;
 }
 // Shared values per column of a mode: the strong modes use their own layout.
-template <int N, int MODE>
+template <int N, int MODE, int NQX>
 constexpr int mode_per_col() {
   if constexpr (MODE == kRhsStrong || MODE == kLsrkStrong) return StrongDims<N, 1>::PER_COL;
   if constexpr (MODE == kRhsStrongU || MODE == kLsrkStrongU) return StrongDims<N, 2>::PER_COL;
-  return Dims<N>::PER_COL;
+  return Dims<N, NQX>::PER_COL;
 }
 
 constexpr int kStageThreads = 256;
@@ -145,10 +147,11 @@ __device__ __forceinline__ void tile_dot(const T* __restrict__ A, const T* in, i
   }
 }
 
-// One block's tile: columns [blk*E, blk*E + E) of the mesh described by p.
-template <typename T, int N, int E, int MODE>
+// One block's tile: columns [blk*E, blk*E + E) of the mesh described by p,
+// whose volume rule has NQX points.
+template <typename T, int N, int E, int MODE, int NQX = (N + 1) * (N + 1) * (N + 1)>
 __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk, unsigned char* smem_raw) {
-  using Dm = Dims<N>;
+  using Dm = Dims<N, NQX>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NFP = Dm::NFP, NFQ = Dm::NFQ;
   constexpr int NQP = Dm::NQP, NPP = Dm::NPP, NFQP = Dm::NFQP, NFPP = Dm::NFPP;
   constexpr int NG = E / 4;
@@ -559,20 +562,20 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
   }
 }
 
-template <typename T, int N, int E, int MODE>
+template <typename T, int N, int E, int MODE, int NQX>
 __global__ void __launch_bounds__(kStageThreads) stage_kernel(const StageParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_tile<T, N, E, MODE>(p, blockIdx.x, smem_raw);
+  stage_tile<T, N, E, MODE, NQX>(p, blockIdx.x, smem_raw);
 }
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int NQX = (N + 1) * (N + 1) * (N + 1)>
 cudaError_t launch_stage_mode(const StageParams<T>& p, cudaStream_t stream) {
-  constexpr int PER = mode_per_col<N, MODE>();
+  constexpr int PER = mode_per_col<N, MODE, NQX>();
   constexpr int E = cols_for<T, N, PER>();
   const size_t smem = (size_t)PER * E * sizeof(T);
   const int64_t blocks = (p.ncols + E - 1) / E;
   if (blocks == 0) return cudaSuccess;
-  auto kern = stage_kernel<T, N, E, MODE>;
+  auto kern = stage_kernel<T, N, E, MODE, NQX>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<(unsigned)blocks, kStageThreads, smem, stream>>>(p);
@@ -581,6 +584,16 @@ cudaError_t launch_stage_mode(const StageParams<T>& p, cudaStream_t stream) {
 
 template <typename T, int N>
 cudaError_t launch_stage_n(const StageParams<T>& p, int mode, cudaStream_t stream) {
+  if (p.nq != Dims<N>::NQ) {
+    // a fewer-point volume rule: the RHS and LSRK stages
+    if constexpr (fewer_point_nq(N) > 0) {
+      if (p.nq == fewer_point_nq(N)) {
+        if (mode == kRhs) return launch_stage_mode<T, N, kRhs, fewer_point_nq(N)>(p, stream);
+        if (mode == kLsrk) return launch_stage_mode<T, N, kLsrk, fewer_point_nq(N)>(p, stream);
+      }
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (mode) {
     case kRhs: return launch_stage_mode<T, N, kRhs>(p, stream);
     case kLsrk: return launch_stage_mode<T, N, kLsrk>(p, stream);

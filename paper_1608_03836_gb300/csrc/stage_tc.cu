@@ -36,9 +36,9 @@
 
 namespace wadg {
 
-template <int N>
+template <int N, int NQX = (N + 1) * (N + 1) * (N + 1)>
 struct TcDims {
-  using D = Dims<N>;
+  using D = Dims<N, NQX>;
   static constexpr int NP = D::NP, NQ = D::NQ, NFP = D::NFP, NFQ = D::NFQ;
   static constexpr int KP = (NP + 15) / 16 * 16;  // node count padded to the MMA K / N granule
   static constexpr int NPS = NP | 1;              // odd row stride of FP32 tiles in shared memory
@@ -203,10 +203,10 @@ struct OpFmt<1> {
 
 }  // namespace
 
-template <int N, int MODE, int FMT>
+template <int N, int MODE, int FMT, int NQX>
 __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStageParams P) {
   using OF = OpFmt<FMT>;
-  using T = TcDims<N>;
+  using T = TcDims<N, NQX>;
   constexpr int NP = T::NP, NQ = T::NQ, NFP = T::NFP, NFQ = T::NFQ, KP = T::KP, QC = T::QC, NPS = T::NPS;
   constexpr int TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16, NCH = T::NCH;
   constexpr int NQ4 = (NQ + 3) / 4, NF4 = (NFQ + 3) / 4;  // groups of four points in the interleaved geometry
@@ -857,24 +857,34 @@ cudaError_t launch_bounded_wait_selftest(int* err, uint32_t max_iters, cudaStrea
   return cudaGetLastError();
 }
 
-template <int N, int MODE, int FMT>
+template <int N, int MODE, int FMT, int NQX>
 cudaError_t launch_one(const TcStageParams& P, int grid, cudaStream_t stream) {
-  using T = TcDims<N>;
-  auto kern = stage_tc_kernel<N, MODE, FMT>;
+  using T = TcDims<N, NQX>;
+  auto kern = stage_tc_kernel<N, MODE, FMT, NQX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, T::SMEM, stream>>>(P);
   return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t launch_stage_tc_n(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream) {
-  using T = TcDims<N>;
+template <int N, int NQX>
+cudaError_t launch_stage_tc_q(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream) {
+  using T = TcDims<N, NQX>;
   const int64_t ntiles = (P.s.ncols + T::TILE - 1) / T::TILE;
   if (ntiles == 0) return cudaSuccess;
   const int g = (int)(ntiles < grid ? ntiles : grid);
-  if (mode == kRhs) return fmt == 0 ? launch_one<N, kRhs, 0>(P, g, stream) : launch_one<N, kRhs, 1>(P, g, stream);
-  return fmt == 0 ? launch_one<N, kLsrk, 0>(P, g, stream) : launch_one<N, kLsrk, 1>(P, g, stream);
+  if (mode == kRhs)
+    return fmt == 0 ? launch_one<N, kRhs, 0, NQX>(P, g, stream) : launch_one<N, kRhs, 1, NQX>(P, g, stream);
+  return fmt == 0 ? launch_one<N, kLsrk, 0, NQX>(P, g, stream) : launch_one<N, kLsrk, 1, NQX>(P, g, stream);
+}
+
+// The volume rule: the collapsed (N+1)^3 rule or the fewer-point rule.
+template <int N>
+cudaError_t launch_stage_tc_n(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream) {
+  if (P.s.nq == Dims<N>::NQ) return launch_stage_tc_q<N, Dims<N>::NQ>(P, mode, fmt, grid, stream);
+  if constexpr (fewer_point_nq(N) > 0)
+    if (P.s.nq == fewer_point_nq(N)) return launch_stage_tc_q<N, fewer_point_nq(N)>(P, mode, fmt, grid, stream);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream) {
@@ -884,16 +894,6 @@ cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, in
     case 3: return launch_stage_tc_n<3>(P, mode, fmt, grid, stream);
     case 4: return launch_stage_tc_n<4>(P, mode, fmt, grid, stream);
     default: return cudaErrorInvalidValue;
-  }
-}
-
-size_t tc_ops_bytes(int N) {
-  switch (N) {
-    case 1: return (size_t)TcDims<1>::SZ_OPS + TcDims<1>::SZ_FOPS;
-    case 2: return (size_t)TcDims<2>::SZ_OPS + TcDims<2>::SZ_FOPS;
-    case 3: return (size_t)TcDims<3>::SZ_OPS + TcDims<3>::SZ_FOPS;
-    case 4: return (size_t)TcDims<4>::SZ_OPS + TcDims<4>::SZ_FOPS;
-    default: return 0;
   }
 }
 
@@ -953,9 +953,9 @@ void put_tile(int fmt, uint8_t* dst, size_t part_bytes, int R, int K, F value) {
     }
 }
 
-template <int N>
+template <int N, int NQX>
 void pack_n(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
-  using T = TcDims<N>;
+  using T = TcDims<N, NQX>;
   const int Np = o.Np, Nq = o.Nq, KP = T::KP, QC = T::QC;
   out.assign((size_t)T::SZ_OPS + T::SZ_FOPS, 0);
   for (int ch = 0; ch < T::NCH; ++ch) {
@@ -1005,12 +1005,26 @@ void pack_n(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
 
 }  // namespace
 
+template <int N>
+bool pack_q(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
+  if (o.Nq == Dims<N>::NQ) {
+    pack_n<N, Dims<N>::NQ>(o, fmt, out);
+    return true;
+  }
+  if constexpr (fewer_point_nq(N) > 0)
+    if (o.Nq == fewer_point_nq(N)) {
+      pack_n<N, fewer_point_nq(N)>(o, fmt, out);
+      return true;
+    }
+  return false;
+}
+
 bool pack_tc_ops(int N, const RefOps& o, int fmt, std::vector<uint8_t>& out) {
   switch (N) {
-    case 1: pack_n<1>(o, fmt, out); return true;
-    case 2: pack_n<2>(o, fmt, out); return true;
-    case 3: pack_n<3>(o, fmt, out); return true;
-    case 4: pack_n<4>(o, fmt, out); return true;
+    case 1: return pack_q<1>(o, fmt, out);
+    case 2: return pack_q<2>(o, fmt, out);
+    case 3: return pack_q<3>(o, fmt, out);
+    case 4: return pack_q<4>(o, fmt, out);
     default: return false;
   }
 }

@@ -53,6 +53,10 @@ enum StageMode {
   kRhsStrong = 5, kLsrkStrong = 6, kRhsStrongU = 7, kLsrkStrongU = 8
 };
 
+// Points of the fewer-point symmetric volume rules the stage kernels are
+// built for (exact to degree 2N+1): 35 at N = 3, 63 at N = 4; 0: none.
+constexpr int fewer_point_nq(int N) { return N == 3 ? 35 : (N == 4 ? 63 : 0); }
+
 // Sizes of the strong-form stage for degree N and formulation FORM (1: the
 // energy-stable rules, 2: the degree 2N+1 rules).  The volume terms walk the
 // NQS points in NCH chunks of QC points (a multiple of 4; the operator tables
@@ -111,6 +115,7 @@ struct StageParams {
   const T* src_vec = nullptr;         // [S][Np] l_n(x^_s)
   T src_amp = 0;
   T* yrec = nullptr;                  // record mode: [ncols][Nq]
+  int nq = 0;                         // points of the volume rule (selects the kernel)
   // strong form on its own rules (kRhsStrong, kLsrkStrong)
   const T* sgeo = nullptr;   // [K][9][NQS]: G_ai at the strong volume points
   const T* sfgeo = nullptr;  // [K][3][4 NFQS]: n J^f at the strong face points (owner order)

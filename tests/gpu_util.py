@@ -26,15 +26,15 @@ def make_mesh_inputs(n, N, amp=0.1):
     return warped_cube(n, N, amp)
 
 
-def oracle_case(VXYZ, EToV, geom, N):
+def oracle_case(VXYZ, EToV, geom, N, rule=None):
     from oracle.discretization import Mesh, RefTet
-    ref = RefTet(N)
+    ref = RefTet(N, volume_rule=rule)
     return Mesh(ref, VXYZ, EToV, geom)
 
 
-def library_mesh(VXYZ, EToV, geom, N, precision="fp64", shots=1, c2="one", tau=(1.0, 1.0)):
+def library_mesh(VXYZ, EToV, geom, N, precision="fp64", shots=1, c2="one", tau=(1.0, 1.0), rule=None):
     import paper_1608_03836_gb300 as W
-    m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
+    m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
     c2q = None
     if isinstance(c2, np.ndarray):
         c2q = c2
@@ -102,7 +102,7 @@ def sample_columns(EToV, S, count, seed):
     return [(int(k), int(rng.integers(S))) for k in ks]
 
 
-def sampled_oracle_rhs(VXYZ, EToV, geom, N, Q, cols, c2fun=None, c2q_all=None, **kw):
+def sampled_oracle_rhs(VXYZ, EToV, geom, N, Q, cols, c2fun=None, c2q_all=None, rule=None, **kw):
     """The oracle's RHS at sampled columns (k, s) of a large mesh, nodal,
     shape (4, len(cols), Np).  The RHS of element k depends only on k and its
     face neighbours, so each column is evaluated on that sub-mesh; its
@@ -112,7 +112,7 @@ def sampled_oracle_rhs(VXYZ, EToV, geom, N, Q, cols, c2fun=None, c2q_all=None, *
     from oracle import wadg as OW
     from oracle.discretization import Mesh, RefTet
     EToV = np.asarray(EToV)
-    ref = RefTet(N)
+    ref = RefTet(N, volume_rule=rule)
     E = face_neighbours(EToV)
     out = []
     for k, s in cols:

@@ -4,7 +4,8 @@ stage over all columns), on sampled columns that the oracle evaluates one by
 one from each element's neighbourhood:
 
   * warped cube 32^3 x 6 = 196,608 tets, N = 4, heterogeneous c^2: FP64, FP32,
-    split bf16 and TF32 tensor cores; the strong form and the conservative
+    split bf16 and TF32 tensor cores, also on the 63-point volume rule; the
+    strong form and the conservative
     weights in FP32; one LSRK step (tensor cores and CUDA cores) against five
     RHS launches composed on the device;
   * 24^3 x 6 = 82,944 tets, N = 5, FP32;
@@ -39,11 +40,12 @@ def cube(n, N):
     return _CUBES[(n, N)]
 
 
-def run_sampled(W, n, N, precision, S=1, c2="heterogeneous", form="strong_weak", conservative=False, seed=0):
+def run_sampled(W, n, N, precision, S=1, c2="heterogeneous", form="strong_weak", conservative=False, seed=0,
+                rule=None):
     import torch
     from synthetic import c2_heterogeneous, random_fields
     VXYZ, EToV, geom = cube(n, N)
-    m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
+    m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
     xq = W.wadg_volume_points(m)
     c2q, c2fun = None, None
     if isinstance(c2, np.ndarray):
@@ -63,10 +65,11 @@ def run_sampled(W, n, N, precision, S=1, c2="heterogeneous", form="strong_weak",
     got = out.double().cpu().numpy()
     cols = sample_columns(EToV, S, SAMPLES, seed)
     want = sampled_oracle_rhs(VXYZ, EToV, geom, N, Q, cols, c2fun=c2fun,
-                              c2q_all=c2 if isinstance(c2, np.ndarray) else None, form=form, conservative=conservative)
+                              c2q_all=c2 if isinstance(c2, np.ndarray) else None, rule=rule, form=form,
+                              conservative=conservative)
     g = np.stack([got[:, k, s] for k, s in cols], 1)
     l2, mx = rel_errors(g, want)
-    print(f"n={n} N={N} K={m.K} S={S} {precision} {form}{' conservative' if conservative else ''}: "
+    print(f"n={n} N={N} K={m.K} Nq={m.Nq} S={S} {precision} {form}{' conservative' if conservative else ''}: "
           f"{len(cols)} sampled columns, rel L2 {l2:.3e}, max {mx:.3e}")
     assert l2 < TOL[precision] and mx < 10 * TOL[precision]
     return m
@@ -109,6 +112,12 @@ def test_c1_lsrk_step_composes_rhs(W, precision):
     er = float((R - res).norm()) / float(res.norm())
     print(f"{precision}: one LSRK step vs composed RHS: Q {eq:.3e} (of the increment), res {er:.3e}")
     assert eq < 10 * TOL[precision] and er < 10 * TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_3xbf16", "fp32_tf32"])
+def test_c1_fewer_point_rule_sampled(W, precision):
+    from synthetic import fewer_point_rule
+    run_sampled(W, 32, 4, precision, seed=6, rule=fewer_point_rule(4))
 
 
 def test_c2_rhs_sampled(W):
