@@ -406,8 +406,9 @@ def c2_study(W):
 
 def e2e_steps(W, m, Q, steps):
     """Same metric end to end through the C ABI with host buffers: every step
-    one wadg_step_host call (pinned host Q and res copied to the device, one
-    LSRK step, both copied back; the call returns when the copies are done)."""
+    one wadg_step_host call (pinned host Q copied to the device, one LSRK
+    step, Q and res copied back; the call returns when the copies are done).
+    Returns the time per step and the bytes copied in and out per step."""
     import torch
     Qh = Q.cpu().pin_memory()
     Rh = torch.zeros_like(Qh).pin_memory()
@@ -421,8 +422,8 @@ def e2e_steps(W, m, Q, steps):
         W.wadg_step_host(m, Qh, Rh, 0.0, dt, 1)
     b.record(stream)
     torch.cuda.synchronize()
-    nbytes = 2 * Q.numel() * Q.element_size()
-    return a.elapsed_time(b) / steps, nbytes
+    nq = Q.numel() * Q.element_size()
+    return a.elapsed_time(b) / steps, nq, 2 * nq
 
 
 class OracleSample:
@@ -579,7 +580,7 @@ def main():
     total_ms = max_over_ranks(total_ms, ws)
     ms_per_step = total_ms / args.steps
     value = job_value(dof, 5, ms_per_step, ws)
-    e2e_ms, nbytes = e2e_steps(W, m, Q, max(2, args.steps // 2))
+    e2e_ms, h2d, d2h = e2e_steps(W, m, Q, max(2, args.steps // 2))
     e2e_value = ws * dof * 5 / (e2e_ms * 1e-3)
     hbm, peak_kind, sm_max = peaks()
     nq = m.Nq
@@ -665,7 +666,7 @@ def main():
                      "algorithmic_bytes_per_element": B,
                      "tensor": {"achieved_fp32_equiv_tflops": achieved_tf,
                                 "note": "flops counted once per product; each runs as three bf16 MMAs"}},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
         "variants": variants,

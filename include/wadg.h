@@ -159,7 +159,9 @@ int wadg_rhs(wadg_mesh* mesh, const void* Q, void* dQdt, wadg_stream stream);
 
 /* nsteps steps of LSRK(5,4) (Sec. 5.2) from time t0 with step dt.  Each stage:
  * res = a_s res + dt (-M~^{-1} A_h Q + source); Q = Q + b_s res.
- *   Q, res   device [4][K][S][Np], updated in place (res = 0 at a cold start).
+ *   Q, res   device [4][K][S][Np], updated in place.  The first stage has
+ *            a_1 = 0, so the incoming res is not read (a step does not depend
+ *            on it); on return res holds the last stage's residual.
  *   traces   device [nsteps][S][R] in the mesh precision: pressure at the
  *            receivers after every step, or NULL (ignored when R = 0).
  * Sources and receivers are those set by wadg_set_sources/wadg_set_receivers. */
@@ -201,9 +203,11 @@ int wadg_set_formulation(wadg_mesh* mesh, int form);
 int wadg_set_conservation(wadg_mesh* mesh, int on);
 
 /* wadg_step on host fields: Q and res are HOST [4][K][S][Np] arrays in the
- * mesh precision (pinned memory gives the fastest copies), copied to device
- * buffers owned by the mesh, stepped nsteps times, and copied back before the
- * call returns (the call waits for the stream).  No receiver traces. */
+ * mesh precision (pinned memory gives the fastest copies).  Q is copied to a
+ * device buffer owned by the mesh, stepped nsteps times, and Q and res are
+ * copied back before the call returns (the call waits for the stream).  The
+ * incoming res is not copied: a step does not read it (a_1 = 0, see
+ * wadg_step).  nsteps = 0 leaves both unchanged.  No receiver traces. */
 int wadg_step_host(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nsteps, wadg_stream stream);
 
 /* Solve from t0 to t0 + T (Sec. 5.2 time stepping): nsteps = ceil(T/dt_max)

@@ -1038,6 +1038,7 @@ int wadg_step_host(wadg_mesh* m, void* Q, void* res, double t0, double dt, int n
   if (st != WADG_OK) return st;
   if (!Q || !res || Q == res) return fail(m, WADG_EINVAL, "Q and res must be distinct host pointers");
   if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "nsteps/dt/t0");
+  if (nsteps == 0) return WADG_OK;
   DeviceGuard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)4 * m->K * m->S * m->ref.Np * tsize(m->precision);
@@ -1049,8 +1050,9 @@ int wadg_step_host(wadg_mesh* m, void* Q, void* res, double t0, double dt, int n
     WADG_CUDA(m, cudaMalloc(&m->d_hostR, bytes));
     m->host_io_bytes = bytes;
   }
+  // res is not copied in: the first stage of every step has a_1 = 0 and does
+  // not read the incoming residual
   WADG_CUDA(m, cudaMemcpyAsync(m->d_hostQ, Q, bytes, cudaMemcpyHostToDevice, s));
-  WADG_CUDA(m, cudaMemcpyAsync(m->d_hostR, res, bytes, cudaMemcpyHostToDevice, s));
   st = m->precision == WADG_FP64 ? step_t<double>(m, m->d_hostQ, m->d_hostR, t0, dt, nsteps, nullptr, s)
                                  : step_t<float>(m, m->d_hostQ, m->d_hostR, t0, dt, nsteps, nullptr, s);
   if (st != WADG_OK) return st;

@@ -552,7 +552,8 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
           if (RHS_OUT) {
             p.out[idx] = acc[r][e];
           } else {
-            const T rr = p.rk_a * p.res[idx] + p.dt * acc[r][e];
+            // the first stage (a_1 = 0) does not read the incoming residual
+            const T rr = p.rk_a != T(0) ? p.rk_a * p.res[idx] + p.dt * acc[r][e] : p.dt * acc[r][e];
             p.res[idx] = rr;
             p.Qout[idx] = sQ[(fld * NP + m) * E + g * 4 + e] + p.rk_b * rr;
           }

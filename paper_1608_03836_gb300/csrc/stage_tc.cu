@@ -815,7 +815,8 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         if (MODE == kRhs) {
           p.out[idx] = v;
         } else {
-          const float rr = p.rk_a * p.res[idx] + p.dt * v;
+          // the first stage (a_1 = 0) does not read the incoming residual
+          const float rr = p.rk_a != 0.f ? p.rk_a * p.res[idx] + p.dt * v : p.dt * v;
           p.res[idx] = rr;
           p.Qout[idx] = __ldg(p.Qin + idx) + p.rk_b * rr;
         }

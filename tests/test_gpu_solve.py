@@ -83,3 +83,22 @@ def test_step_host_equals_step(W, precision):
     W.wadg_step_host(m, Qh, Rh, 0.0, 0.003, 4)
     torch.cuda.synchronize()
     assert torch.equal(Qh, Qd.cpu()) and torch.equal(Rh, Rd.cpu())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
+def test_step_does_not_read_the_incoming_residual(W, precision):
+    """LSRK(5,4) has a_1 = 0: a step with a residual full of NaN gives exactly
+    the result of a step from a zero residual (device and host entry points)."""
+    import torch
+    VXYZ, EToV, geom = make_mesh_inputs(2, 3)
+    m = library_mesh(VXYZ, EToV, geom, 3, precision, shots=2, c2="heterogeneous")
+    Q0 = to_torch(random_Q(m.K, 2, m.Np, 13), m.dtype)
+    Qa, Ra = Q0.clone(), torch.zeros_like(Q0)
+    Qb, Rb = Q0.clone(), torch.full_like(Q0, float("nan"))
+    W.wadg_step(m, Qa, Ra, 0.0, 0.003, 2)
+    W.wadg_step(m, Qb, Rb, 0.0, 0.003, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(Qa, Qb) and torch.equal(Ra, Rb)
+    Qh, Rh = Q0.cpu().pin_memory(), torch.full_like(Q0, float("nan")).cpu().pin_memory()
+    W.wadg_step_host(m, Qh, Rh, 0.0, 0.003, 2)
+    assert torch.equal(Qh, Qa.cpu()) and torch.equal(Rh, Ra.cpu())
