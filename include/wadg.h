@@ -207,7 +207,9 @@ int wadg_set_conservation(wadg_mesh* mesh, int on);
  * device buffer owned by the mesh, stepped nsteps times, and Q and res are
  * copied back before the call returns (the call waits for the stream).  The
  * incoming res is not copied: a step does not read it (a_1 = 0, see
- * wadg_step).  nsteps = 0 leaves both unchanged.  No receiver traces. */
+ * wadg_step).  res may be NULL: the residual is then kept on the device and
+ * not returned (only the state Q crosses the link).  nsteps = 0 leaves both
+ * unchanged.  No receiver traces. */
 int wadg_step_host(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nsteps, wadg_stream stream);
 
 /* Solve from t0 to t0 + T (Sec. 5.2 time stepping): nsteps = ceil(T/dt_max)

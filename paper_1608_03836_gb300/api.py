@@ -188,13 +188,16 @@ def wadg_set_conservation(mesh: MeshHandle, on: bool):
 
 def wadg_step_host(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, stream=None):
     """wadg_step on host tensors (CPU, contiguous, the mesh precision; pinned
-    memory gives the fastest copies): copied in, stepped, copied back."""
-    import torch
+    memory gives the fastest copies): Q copied in, stepped, Q and res copied
+    back; res=None keeps the residual on the device."""
     shape = tuple(mesh.field_shape())
     for name, x in (("Q", Q), ("res", res)):
+        if x is None and name == "res":
+            continue
         if x.is_cuda or x.dtype != mesh.dtype or tuple(x.shape) != shape or not x.is_contiguous():
             raise ValueError(f"{name} must be a contiguous CPU tensor {shape} of {mesh.dtype}")
-    _check(load().wadg_step_host(mesh.handle, ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(res.data_ptr()),
+    rp = None if res is None else ctypes.c_void_p(res.data_ptr())
+    _check(load().wadg_step_host(mesh.handle, ctypes.c_void_p(Q.data_ptr()), rp,
                                  float(t0), float(dt), int(nsteps), _stream(stream)), "wadg_step_host", mesh)
 
 

@@ -1036,7 +1036,7 @@ int wadg_set_conservation(wadg_mesh* m, int on) {
 int wadg_step_host(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, wadg_stream stream) {
   int st = check_ready(m);
   if (st != WADG_OK) return st;
-  if (!Q || !res || Q == res) return fail(m, WADG_EINVAL, "Q and res must be distinct host pointers");
+  if (!Q || Q == res) return fail(m, WADG_EINVAL, "Q and res must be distinct host pointers (res may be NULL)");
   if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "nsteps/dt/t0");
   if (nsteps == 0) return WADG_OK;
   DeviceGuard g(m->device);
@@ -1057,7 +1057,7 @@ int wadg_step_host(wadg_mesh* m, void* Q, void* res, double t0, double dt, int n
                                  : step_t<float>(m, m->d_hostQ, m->d_hostR, t0, dt, nsteps, nullptr, s);
   if (st != WADG_OK) return st;
   WADG_CUDA(m, cudaMemcpyAsync(Q, m->d_hostQ, bytes, cudaMemcpyDeviceToHost, s));
-  WADG_CUDA(m, cudaMemcpyAsync(res, m->d_hostR, bytes, cudaMemcpyDeviceToHost, s));
+  if (res) WADG_CUDA(m, cudaMemcpyAsync(res, m->d_hostR, bytes, cudaMemcpyDeviceToHost, s));
   WADG_CUDA(m, cudaStreamSynchronize(s));
   return WADG_OK;
 }

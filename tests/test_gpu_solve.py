@@ -102,3 +102,6 @@ def test_step_does_not_read_the_incoming_residual(W, precision):
     Qh, Rh = Q0.cpu().pin_memory(), torch.full_like(Q0, float("nan")).cpu().pin_memory()
     W.wadg_step_host(m, Qh, Rh, 0.0, 0.003, 2)
     assert torch.equal(Qh, Qa.cpu()) and torch.equal(Rh, Ra.cpu())
+    Qn = Q0.cpu().pin_memory()
+    W.wadg_step_host(m, Qn, None, 0.0, 0.003, 2)  # the residual stays on the device
+    assert torch.equal(Qn, Qa.cpu())
