@@ -674,6 +674,14 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     wait_all(6, par_m2);
     par_m2 ^= 1u;
     if (tid == 0) {  // update operators of chunks 0 and 1
+      if (MODE == kLsrk && bulkq) {
+        // the epilogue's reads of Q_in and res for this tile, into L2 while the update runs
+        const uint32_t bytes = (uint32_t)(ncol_t * NP * 4);
+        for (int f = 0; f < 4; ++f) {
+          tc::bulk_prefetch_l2(p.Qin + f * fs + col0 * NP, bytes);
+          if (p.rk_a != 0.f) tc::bulk_prefetch_l2(p.res + f * fs + col0 * NP, bytes);
+        }
+      }
       load_slot(0, upd_ops, T::SZ_UA);
       load_slot(2, upd_ops + T::SZ_UA, T::SZ_UB);
       if (T::UNCH > 1) {

@@ -202,6 +202,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
+// Prefetch [src, src + bytes) into L2 with the bulk-copy engine (start
+// 16-byte aligned, bytes a multiple of 16; nothing is written).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Split eight values x = hi + lo and store both parts as one 16-byte row each.
 __device__ __forceinline__ void split_store8(uint8_t* hi, uint8_t* lo, const float (&x)[8]) {
   uint32_t h[4], l[4];
