@@ -813,20 +813,41 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     sync_check();
     {
       const int nval = ncol_t * NP;
+      if (MODE == kRhs) {
 #pragma unroll 4
-      for (int i = tid; i < 4 * TILE * NP; i += kThreads) {
-        const int f = i / (TILE * NP), r = i - f * (TILE * NP);
-        if (r >= nval) continue;
-        const int c = r / NP, n = r - c * NP;
-        const float v = sTT[(f * TILE + c) * NPS + n];
-        const int64_t idx = f * fs + col0 * NP + r;
-        if (MODE == kRhs) {
-          p.out[idx] = v;
-        } else {
-          // the first stage (a_1 = 0) does not read the incoming residual
-          const float rr = p.rk_a != 0.f ? p.rk_a * p.res[idx] + p.dt * v : p.dt * v;
-          p.res[idx] = rr;
-          p.Qout[idx] = __ldg(p.Qin + idx) + p.rk_b * rr;
+        for (int i = tid; i < 4 * TILE * NP; i += kThreads) {
+          const int f = i / (TILE * NP), r = i - f * (TILE * NP);
+          if (r >= nval) continue;
+          const int c = r / NP, n = r - c * NP;
+          p.out[f * fs + col0 * NP + r] = sTT[(f * TILE + c) * NPS + n];
+        }
+      } else {
+        // LSRK (Sec. 5.2): res = a res + dt r, Q_out = Q_in + b res.  The loads of
+        // EB iterations are issued before their stores, so that EB round trips
+        // to L2 overlap.  The first stage (a_1 = 0) does not read res.
+        constexpr int NIT = (4 * TILE * NP + kThreads - 1) / kThreads, EB = 5;
+        const bool rd = p.rk_a != 0.f;
+        for (int i0 = 0; i0 < NIT; i0 += EB) {
+          float vv[EB], rs[EB], qi[EB];
+          int64_t ix[EB];
+#pragma unroll
+          for (int e = 0; e < EB; ++e) {
+            const int i = tid + (i0 + e) * kThreads;
+            const int f = i / (TILE * NP), r = i - f * (TILE * NP);
+            const bool ok = i0 + e < NIT && i < 4 * TILE * NP && r < nval;
+            const int c = r / NP, n = r - c * NP;
+            ix[e] = ok ? f * fs + col0 * NP + r : -1;
+            vv[e] = ok ? sTT[(f * TILE + c) * NPS + n] : 0.f;
+            rs[e] = ok && rd ? __ldg(p.res + ix[e]) : 0.f;
+            qi[e] = ok ? __ldg(p.Qin + ix[e]) : 0.f;
+          }
+#pragma unroll
+          for (int e = 0; e < EB; ++e) {
+            if (ix[e] < 0) continue;
+            const float rr = rd ? p.rk_a * rs[e] + p.dt * vv[e] : p.dt * vv[e];
+            p.res[ix[e]] = rr;
+            p.Qout[ix[e]] = qi[e] + p.rk_b * rr;
+          }
         }
       }
     }
