@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         // LSRK (Sec. 5.2): res = a res + dt r, Q_out = Q_in + b res.  The loads of
         // EB iterations are issued before their stores, so that EB round trips
         // to L2 overlap.  The first stage (a_1 = 0) does not read res.
-        constexpr int NIT = (4 * TILE * NP + kThreads - 1) / kThreads, EB = 5;
+        constexpr int NIT = (4 * TILE * NP + kThreads - 1) / kThreads, EB = 7;
         const bool rd = p.rk_a != 0.f;
         for (int i0 = 0; i0 < NIT; i0 += EB) {
           float vv[EB], rs[EB], qi[EB];
