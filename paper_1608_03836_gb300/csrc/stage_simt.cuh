@@ -540,20 +540,38 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
       const int fld = it / (RG * NG);
       T acc[2][4];
       tile_dot<T, E, 2, NPP, NQ>(ops.PqT, sX + fld * NQ * E + g * 4, m0, acc);
+      if (RHS_OUT) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int64_t c = col0 + g * 4 + e;
-        if (c >= ncols) continue;
+        for (int e = 0; e < 4; ++e) {
+          const int64_t c = col0 + g * 4 + e;
+          if (c >= ncols) continue;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int m = m0 + r;
-          if (m >= NP) continue;
-          const int64_t idx = fld * fs + c * NP + m;
-          if (RHS_OUT) {
-            p.out[idx] = acc[r][e];
-          } else {
-            // the first stage (a_1 = 0) does not read the incoming residual
-            const T rr = p.rk_a != T(0) ? p.rk_a * p.res[idx] + p.dt * acc[r][e] : p.dt * acc[r][e];
+          for (int r = 0; r < 2; ++r)
+            if (m0 + r < NP) p.out[fld * fs + c * NP + m0 + r] = acc[r][e];
+        }
+      } else {
+        // The first stage (a_1 = 0) does not read the incoming residual.  Each
+        // res element is read once and then written by this thread only: its
+        // eight values are loaded (read-only path) before any store.
+        const bool rd = p.rk_a != T(0);
+        T rs[2][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int64_t c = col0 + g * 4 + e;
+            rs[r][e] = rd && c < ncols && m0 + r < NP ? __ldg(p.res + fld * fs + c * NP + m0 + r) : T(0);
+          }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t c = col0 + g * 4 + e;
+          if (c >= ncols) continue;
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int m = m0 + r;
+            if (m >= NP) continue;
+            const int64_t idx = fld * fs + c * NP + m;
+            const T rr = rd ? p.rk_a * rs[r][e] + p.dt * acc[r][e] : p.dt * acc[r][e];
             p.res[idx] = rr;
             p.Qout[idx] = sQ[(fld * NP + m) * E + g * 4 + e] + p.rk_b * rr;
           }
