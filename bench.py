@@ -213,9 +213,11 @@ def batched_shots(W, steps):
     from synthetic import warped_cube, random_fields
     n, N, S = 16, 4, 64
     VXYZ, EToV, geom = warped_cube(n, N, 0.1)
-    out = {"workload": f"warped cube 16^3x6 = {len(EToV)} tets, N=4, 64 shots (columns K*S = {len(EToV) * S})"}
+    rule = headline_rule()
+    out = {"workload": f"warped cube 16^3x6 = {len(EToV)} tets, N=4, 64 shots (columns K*S = {len(EToV) * S}), "
+                       f"{'collapsed' if rule is None else str(len(rule[1])) + '-point'} volume rule"}
     for prec in ("fp32", "fp32_3xbf16"):
-        m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
+        m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
         W.wadg_set_operators(m, prec, S, 1.0, 1.0, None)
         Q = torch.from_numpy(random_fields((4, m.K, S, m.Np), 3).astype(np.float32)).cuda()
         tot, st = time_steps(W, m, Q, steps, 3)
