@@ -206,24 +206,42 @@ def time_steps(W, m, Q, steps, warmup):
 
 
 def batched_shots(W, steps):
-    """Shots as columns: the 16^3 x 6 = 24,576-tet N=4 cube with 64 shots of
-    independent (seeded) data sharing the geometry, FP32 and FP32 + split-bf16
-    tensor cores; DOF = 4 K Np S."""
+    """Shots as columns: the 16^3 x 6 = 24,576-tet N=4 cube with 64 shots
+    sharing the geometry, each with its own Ricker point source (f0 = 5,
+    seeded position in [-0.8, 0.8]^3) and 8 receivers sampled after every
+    step, from zero fields; FP32 and FP32 + split-bf16 tensor cores; DOF =
+    4 K Np S; CUDA events around one wadg_step call of `steps` steps after 3
+    warm-up steps."""
     import torch
-    from synthetic import warped_cube, random_fields
-    n, N, S = 16, 4, 64
+    from synthetic import warped_cube, source_positions, receiver_positions
+    n, N, S, R = 16, 4, 64, 8
     VXYZ, EToV, geom = warped_cube(n, N, 0.1)
     rule = headline_rule()
     out = {"workload": f"warped cube 16^3x6 = {len(EToV)} tets, N=4, 64 shots (columns K*S = {len(EToV) * S}), "
-                       f"{'collapsed' if rule is None else str(len(rule[1])) + '-point'} volume rule"}
+                       f"{'collapsed' if rule is None else str(len(rule[1])) + '-point'} volume rule, one Ricker "
+                       "point source (f0 = 5) and 8 receivers per shot"}
     for prec in ("fp32", "fp32_3xbf16"):
         m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
         W.wadg_set_operators(m, prec, S, 1.0, 1.0, None)
-        Q = torch.from_numpy(random_fields((4, m.K, S, m.Np), 3).astype(np.float32)).cuda()
-        tot, st = time_steps(W, m, Q, steps, 3)
+        W.wadg_set_sources(m, source_positions(S), 5.0, 0.24)
+        W.wadg_set_receivers(m, receiver_positions(R * S).reshape(S, R, 3))
+        Q = torch.zeros((4, m.K, S, m.Np), dtype=torch.float32, device="cuda")
+        Rs = torch.zeros_like(Q)
+        dt = 0.5 * (1.0 / n) / (N + 1) ** 2
+        tr = torch.zeros((steps, S, R), dtype=torch.float32, device="cuda")
+        W.wadg_step(m, Q, Rs, 0.0, dt, 3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        W.wadg_step(m, Q, Rs, 3 * dt, dt, steps, tr)
+        b.record()
+        torch.cuda.synchronize()
+        W.wadg_device_status(m)
+        ms = a.elapsed_time(b) / steps
         dof = 4 * m.K * S * m.Np
-        out[prec] = {"value": dof * 5 / (tot / steps * 1e-3), "ms_per_step": tot / steps, "stage_ms": st}
-        del Q, m
+        out[prec] = {"value": dof * 5 / (ms * 1e-3), "ms_per_step": ms, "stage_ms": ms / 5,
+                     "max_abs_trace": float(tr.abs().max())}
+        del Q, Rs, m, tr
         torch.cuda.empty_cache()
     return out
 
@@ -272,6 +290,49 @@ def uneven_batch(W, steps, small=False):
             "dof": dof, "items": info["items"],
             "grid": grid, "value": dof * 5 / (t_batch * 1e-3), "ms_per_step": t_batch,
             "sequential_ms_per_step": t_seq, "launches_per_step": 5, "sequential_launches_per_step": 60}
+
+
+def adjoint_timing(W, nsteps=300, checkpoint=20):
+    """The differentiation configuration: warped cube 16^3 x 6 = 24,576 tets,
+    N = 3, FP32 (CUDA cores, collapsed rule), c^2 perturbed by 10 % per volume
+    point (seeded), 16 seeded receivers, 300 LSRK(5,4) steps from the
+    projected standing wave; misfit = sum of squared receiver pressures.
+    Times the forward pass (traces, a checkpoint every 20 steps) and the
+    backward pass (gradients with respect to the initial pressure and c^2:
+    each segment recomputed forward with the stage factors recorded, then the
+    discrete adjoint steps), CUDA events on the current stream."""
+    import torch
+    from synthetic import warped_cube, c2_perturbed_samples, receiver_positions, standing_wave
+    from paper_1608_03836_gb300.adjoint import receiver_traces
+    n, N = 16, 3
+    VXYZ, EToV, geom = warped_cube(n, N, 0.1)
+    m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
+    c2q = c2_perturbed_samples((len(EToV), (N + 1) ** 3), seed=4)
+    W.wadg_set_operators(m, "fp32", 1, 1.0, 1.0, c2q)
+    W.wadg_set_receivers(m, receiver_positions(16).reshape(1, 16, 3))
+    xq = W.wadg_volume_points(m)
+    Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
+    W.wadg_project(m, torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda(), Q)
+    dt = 0.5 * (1.0 / n) / ((N + 1) ** 2 * 1.1 ** 0.5)
+    p0 = Q[0].clone().requires_grad_(True)
+    c2 = torch.tensor(c2q, dtype=torch.float64, device="cuda", requires_grad=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    tr = receiver_traces(m, p0, c2, dt, nsteps, checkpoint=checkpoint)
+    ev[1].record()
+    loss = (tr.double() ** 2).sum()
+    loss.backward()
+    ev[2].record()
+    torch.cuda.synchronize()
+    W.wadg_device_status(m)
+    fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    dof = 4 * m.K * m.Np
+    return {"workload": f"warped cube 16^3x6 = {m.K} tets, N={N}, FP32, c^2 perturbed 10 %, 16 receivers, "
+                        f"{nsteps} steps, checkpoint every {checkpoint}",
+            "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+            "forward_dof_stage_per_s": dof * 5 * nsteps / (fwd * 1e-3),
+            "misfit": float(loss), "grad_p0_norm": float(p0.grad.norm()), "grad_c2_norm": float(c2.grad.norm())}
 
 
 def accuracy(W):
@@ -658,6 +719,7 @@ def main():
         extras["uneven_batch_small"] = uneven_batch(W, max(2, args.steps), small=True)
         extras["accuracy"] = accuracy(W)
         extras["formulations"] = formulations(W, args.steps)
+        extras["adjoint"] = adjoint_timing(W)
 
     if rank != 0:
         return
