@@ -332,7 +332,7 @@ def adjoint_timing(W, nsteps=300, checkpoint=20):
                         f"{nsteps} steps, checkpoint every {checkpoint}",
             "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
             "forward_dof_stage_per_s": dof * 5 * nsteps / (fwd * 1e-3),
-            "misfit": float(loss), "grad_p0_norm": float(p0.grad.norm()), "grad_c2_norm": float(c2.grad.norm())}
+            "misfit": float(loss.detach()), "grad_p0_norm": float(p0.grad.norm()), "grad_c2_norm": float(c2.grad.norm())}
 
 
 def accuracy(W):
