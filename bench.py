@@ -300,7 +300,8 @@ def adjoint_timing(W, nsteps=300, checkpoint=20):
     Times the forward pass (traces, a checkpoint every 20 steps) and the
     backward pass (gradients with respect to the initial pressure and c^2:
     each segment recomputed forward with the stage factors recorded, then the
-    discrete adjoint steps), CUDA events on the current stream."""
+    discrete adjoint steps), CUDA events on the current stream, after a
+    2-step warm-up pass."""
     import torch
     from synthetic import warped_cube, c2_perturbed_samples, receiver_positions, standing_wave
     from paper_1608_03836_gb300.adjoint import receiver_traces
@@ -316,6 +317,10 @@ def adjoint_timing(W, nsteps=300, checkpoint=20):
     dt = 0.5 * (1.0 / n) / ((N + 1) ** 2 * 1.1 ** 0.5)
     p0 = Q[0].clone().requires_grad_(True)
     c2 = torch.tensor(c2q, dtype=torch.float64, device="cuda", requires_grad=True)
+    # warm-up: the first autograd backward pass of a process carries a
+    # one-time cost of several seconds outside the library
+    (receiver_traces(m, p0, c2, dt, 2, checkpoint=checkpoint) ** 2).sum().backward()
+    p0.grad, c2.grad = None, None
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
     ev[0].record()
