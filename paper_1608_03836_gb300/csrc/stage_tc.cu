@@ -29,6 +29,7 @@
 // copies are bounded; on expiry the CTA records an error in P.err, drains its
 // copies and products, frees its TMEM and returns.
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "stage_simt.cuh"
@@ -98,6 +99,44 @@ struct TcDims {
   static_assert(2 * T1U <= TB && SZ_UA <= SZ_SLOT && SZ_UB <= SZ_SLOT, "update plan");
   static_assert(SMEM <= 232448, "shared memory");
 };
+
+// Volume nodes of each reference face (t = -1, s = -1, r + s + t = -1,
+// r = -1) on the equispaced lattice, node (i, j, k) at index
+// sum_{k' < k} (N-k'+1)(N-k'+2)/2 + j (N-k+1) - j (j-1)/2 + i.  Fixed by N and
+// the face alone; the host checks them against the runtime face tables.
+template <int N>
+struct FaceNodeList {
+  static constexpr int NFP = (N + 1) * (N + 2) / 2;
+  int v[4][NFP];
+};
+template <int N>
+constexpr int lattice_index(int i, int j, int k) {
+  int base = 0;
+  for (int kk = 0; kk < k; ++kk) base += (N - kk + 1) * (N - kk + 2) / 2;
+  return base + j * (N - k + 1) - j * (j - 1) / 2 + i;
+}
+template <int N>
+constexpr FaceNodeList<N> make_face_nodes() {
+  FaceNodeList<N> r{};
+  for (int f = 0; f < 4; ++f) {
+    int t = 0;
+    for (int k = 0; k <= N; ++k)
+      for (int j = 0; j <= N - k; ++j)
+        for (int i = 0; i <= N - j - k; ++i) {
+          const bool on = f == 0 ? k == 0 : f == 1 ? j == 0 : f == 2 ? i + j + k == N : i == 0;
+          if (on) r.v[f][t++] = lattice_index<N>(i, j, k);
+        }
+  }
+  return r;
+}
+// 8-column TMEM groups of the b accumulators that face F's nodes fall in.
+template <int N, int F>
+constexpr uint32_t face_group_mask() {
+  constexpr FaceNodeList<N> L = make_face_nodes<N>();
+  uint32_t m = 0;
+  for (int t = 0; t < FaceNodeList<N>::NFP; ++t) m |= 1u << (L.v[F][t] >> 3);
+  return m;
+}
 
 namespace {
 
@@ -424,37 +463,52 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         for (int j8 = 0; j8 < NFP16 / 8; ++j8) tc::pin8(L[j8]);
 #pragma unroll
         for (int j = 0; j < NFP; ++j) sLS[(grp * NFP16 + j) * TILE + mrow] = __uint_as_float(L[j >> 3][j & 7]);
-        // add to this field's b accumulator (the first face initialises it)
+        // add to this field's b accumulator (the first face initialises it):
+        // only the face's nodes change, and f is uniform across the CTA
         const int16_t* gi = sGI + (f * 6 + pio) * NP;
         const uint32_t tb = lane_base + T::TB + KP * grp;
-        uint32_t acc[KP / 8][8];
-        if (f > 0) {
+        auto add_face = [&](auto fc) {
+          constexpr int F = decltype(fc)::value;
+          constexpr FaceNodeList<N> FN = make_face_nodes<N>();
+          constexpr uint32_t gm = F == 0 ? (1u << (KP / 8)) - 1u : face_group_mask<N, F>();
+          uint32_t acc[KP / 8][8];
+          if (F > 0) {
 #pragma unroll
-          for (int n8 = 0; n8 < KP / 8; ++n8) tc::tmem_ld8_nw(tb + 8 * n8, acc[n8]);
-          tc::wait_ld();
+            for (int n8 = 0; n8 < KP / 8; ++n8)
+              if (gm & (1u << n8)) tc::tmem_ld8_nw(tb + 8 * n8, acc[n8]);
+            tc::wait_ld();
 #pragma unroll
-          for (int n8 = 0; n8 < KP / 8; ++n8) tc::pin8(acc[n8]);
-        } else {
+            for (int n8 = 0; n8 < KP / 8; ++n8)
+              if (gm & (1u << n8)) tc::pin8(acc[n8]);
+          } else {
 #pragma unroll
-          for (int n8 = 0; n8 < KP / 8; ++n8)
+            for (int n8 = 0; n8 < KP / 8; ++n8)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[n8][j] = 0u;
-        }
+              for (int j = 0; j < 8; ++j) acc[n8][j] = 0u;
+          }
 #pragma unroll
-        for (int n = 0; n < NP; ++n) {
-          const int jj = gi[n];
-          if (jj >= 0)
+          for (int t = 0; t < NFP; ++t) {
+            const int n = FN.v[F][t];
+            const int jj = gi[n];
             acc[n >> 3][n & 7] =
                 __float_as_uint(__uint_as_float(acc[n >> 3][n & 7]) + sLS[(grp * NFP16 + jj) * TILE + mrow]);
-        }
+          }
 #pragma unroll
-        for (int n8 = 0; n8 < KP / 8; ++n8) {
-          float v[8];
+          for (int n8 = 0; n8 < KP / 8; ++n8)
+            if (gm & (1u << n8)) {
+              float v[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(acc[n8][j]);
-          tc::tmem_st8(tb + 8 * n8, v);
+              for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(acc[n8][j]);
+              tc::tmem_st8(tb + 8 * n8, v);
+            }
+          tc::wait_st();
+        };
+        switch (f) {
+          case 0: add_face(std::integral_constant<int, 0>()); break;
+          case 1: add_face(std::integral_constant<int, 1>()); break;
+          case 2: add_face(std::integral_constant<int, 2>()); break;
+          default: add_face(std::integral_constant<int, 3>()); break;
         }
-        tc::wait_st();
       }
     };
     load_nv(0);
@@ -1035,8 +1089,24 @@ void pack_n(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
 
 }  // namespace
 
+// The kernel's compile-time face node lists equal the runtime face tables:
+// node n lies on face f exactly when ginv[f][pi][n] >= 0, for every pi.
+template <int N>
+bool face_nodes_match(const RefOps& o) {
+  constexpr FaceNodeList<N> FN = make_face_nodes<N>();
+  for (int f = 0; f < 4; ++f)
+    for (int pi = 0; pi < 6; ++pi) {
+      std::vector<int> on(o.Np, 0);
+      for (int t = 0; t < FaceNodeList<N>::NFP; ++t) on[FN.v[f][t]] = 1;
+      for (int n = 0; n < o.Np; ++n)
+        if ((o.ginv[(f * 6 + pi) * o.Np + n] >= 0) != (on[n] != 0)) return false;
+    }
+  return true;
+}
+
 template <int N>
 bool pack_q(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
+  if (!face_nodes_match<N>(o)) return false;
   if (o.Nq == Dims<N>::NQ) {
     pack_n<N, Dims<N>::NQ>(o, fmt, out);
     return true;
