@@ -13,15 +13,20 @@
 //   surface (Sec. 4.1, Sec. 6.4), face by face: 16 lanes gather the face nodes
 //     of one column ([p], {u}, [u] in the owner's node order), V_tri products
 //     to the face points, the strong-weak flux with n J^f on the CUDA cores,
-//     lift products, and the lifted values scattered to the volume nodes and
-//     summed in the b accumulators in TMEM;
+//     lift products, and the lifted values scattered to the face's volume
+//     nodes (lists fixed at compile time) and summed in the b accumulators in
+//     TMEM;
 //   volume (Sec. 6.4), chunks of 16 points, software-pipelined: V_q u_i and
 //     V_q^a p of chunk c + 2 and the test products of chunk c run on the tensor
 //     cores while the CUDA cores form U^a = sum_i G_ai u_i and
 //     g_i = -sum_a G_ai dp/dx^_a of chunk c + 1;
 //   update (Sec. 6.2, Eq. (matfree); Sec. 7), chunks of 32 points: b -> V_q
 //     M^^{-1} b, times W = c^2/J or 1/J, P_q (...) accumulated in TMEM;
-//   epilogue: dQ/dt, or the LSRK update (Sec. 5.2), written coalesced.
+//   epilogue: dQ/dt, or the LSRK update (Sec. 5.2), written coalesced; in
+//     LSRK mode the tile's Q_in and res are prefetched into L2 during the
+//     update and read several iterations ahead of the stores.
+// The volume rule has NQ points (the collapsed (N+1)^3 rule or a fewer-point
+// symmetric rule), a template parameter.
 // Geometric factors come from copies interleaved over 128 elements in groups
 // of four points (one 16-byte load per four points).  Every tcgen05.mma holds
 // its issuing thread for 100-200 cycles, so lane 0 of every warp issues at
