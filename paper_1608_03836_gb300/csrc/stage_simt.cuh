@@ -15,8 +15,9 @@
 //   3. the weight-adjusted update (Sec. 6.2, Eq. (matfree); Sec. 7):
 //        r = P_q diag(W) (V_q M^^{-1}) b,  W = c^2/J (p) or 1/J (u);
 //   4. RHS mode: dQ/dt = r.  LSRK mode (Sec. 5.2): res = a res + dt r,
-//      Q_out = Q + b res (the first stage, a = 0, reads no res).  Record mode: LSRK, and also stores
-//      y_q = (V_q M^^{-1} b_p)_q / J_q, the factor of dr_p/dc^2_q.
+//      Q_out = Q + b res (the first stage, a = 0, reads no res).  Record
+//      mode: LSRK, and also stores y_q = (V_q M^^{-1} b_p)_q / J_q, the factor
+//      of dr_p/dc^2_q.
 // Strong modes (Sec. 4.1, Sec. 6.3) replace step 1 by the strong form's volume
 // terms -V^T diag(w) (J div u, J grad p) on their own rule (the energy-stable
 // degree 4N-3 rule, or the 2N+1 rule), walked in chunks of points, and carry
