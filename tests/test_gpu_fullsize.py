@@ -80,9 +80,15 @@ def test_c1_rhs_sampled(W, precision):
     run_sampled(W, 32, 4, precision, seed=1)
 
 
-@pytest.mark.parametrize("form,conservative", [("strong", False), ("strong_weak", True)])
-def test_c1_variants_sampled(W, form, conservative):
-    run_sampled(W, 32, 4, "fp32", form=form, conservative=conservative, seed=2)
+@pytest.mark.parametrize("precision,form,conservative", [("fp32", "strong", False), ("fp64", "strong", False),
+                                                        ("fp32", "strong_weak", True)])
+def test_c1_variants_sampled(W, precision, form, conservative):
+    run_sampled(W, 32, 4, precision, form=form, conservative=conservative, seed=2)
+
+
+def test_c1_conservative_tensor_cores_on_the_fewer_point_rule_sampled(W):
+    from synthetic import fewer_point_rule
+    run_sampled(W, 32, 4, "fp32_3xbf16", conservative=True, seed=7, rule=fewer_point_rule(4))
 
 
 @pytest.mark.parametrize("precision", ["fp32_3xbf16", "fp32"])
