@@ -16,12 +16,13 @@ namespace wadg {
 
 // Tile rules: rule 0 is the single-mesh rule (cols_per_block); rule 1 caps
 // every degree to ~76 KB of shared memory so that a mixed batch keeps three
-// blocks per SM (degrees 5 and 6 then take 4 columns per tile).
+// blocks per SM, taking the widest of the single-mesh width, 8 and 4 columns
+// that fits (degree 5 then takes 8 columns per tile, degree 6 takes 4).
 template <int N, int RULE>
 constexpr int batch_cols() {
   constexpr int per = Dims<N>::PER_COL * 4;
   constexpr int e0 = cols_per_block<float, N>();
-  return RULE == 0 ? e0 : (per * e0 <= 77824 ? e0 : 4);
+  return RULE == 0 ? e0 : (per * e0 <= 77824 ? e0 : (per * 8 <= 77824 ? 8 : 4));
 }
 
 template <int MODE, int RULE>
