@@ -60,8 +60,9 @@ struct Dims {
 
 // Columns per block E.  E = 4 (mod 8) makes the row stride of the [row][E]
 // shared arrays 16 words modulo 32 banks, so that the 4x4 register tiles of a
-// warp (column group fastest) store without bank conflicts.  Budget: about
-// 76 KB of shared memory (3 blocks per SM), 112 KB for N >= 5.
+// warp (column group fastest) store without bank conflicts; E = 8 is taken
+// where 12 columns do not fit.  Budget: about 76 KB of shared memory (3
+// blocks per SM).
 // FP64 is bound by the FP64 pipe, not by shared memory: it keeps ~96 KB
 // blocks with E a multiple of 4.
 template <typename T, int N, int PER>
@@ -71,9 +72,12 @@ constexpr int cols_for() {
     constexpr int e8 = (98304 / per) / 4 * 4;
     return e8 < 4 ? 4 : (e8 > 32 ? 32 : e8);
   }
-  constexpr int budget = N >= 5 ? 114688 : 77824;
+  // ~76 KB: three blocks per SM (measured at N = 5: 8 columns in 69 KB beat
+  // 12 columns in 103 KB at two blocks per SM by 18 %; at N = 6, 4 columns in
+  // 48 KB beat 8 columns in 96 KB)
+  constexpr int budget = 77824;
   constexpr int fit = budget / per;
-  constexpr int e = fit >= 28 ? 28 : (fit >= 20 ? 20 : (fit >= 12 ? 12 : 4));
+  constexpr int e = fit >= 28 ? 28 : (fit >= 20 ? 20 : (fit >= 12 ? 12 : (fit >= 8 ? 8 : 4)));
   return e;
 }
 template <typename T, int N>
