@@ -287,7 +287,7 @@ def uneven_batch(W, steps, small=False):
     t_seq = e0.elapsed_time(e1) / steps
     info = W.wadg_batch_info(b)
     return {"workload": "12 warped cubes, " + ("n = 2..5" if small else "n = 4..16") + ", N = 2..6, FP32",
-            "dof": dof, "items": info["items"],
+            "dof": dof, "items": info["items"], "tile_rule": info["rule"],
             "grid": grid, "value": dof * 5 / (t_batch * 1e-3), "ms_per_step": t_batch,
             "sequential_ms_per_step": t_seq, "launches_per_step": 5, "sequential_launches_per_step": 60}
 

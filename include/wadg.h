@@ -307,21 +307,32 @@ typedef struct wadg_batch wadg_batch;
  * owned); destroy it before the meshes. */
 int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out);
 
-/* info[0..3] = meshes, work items, persistent blocks in use, largest
- * resident grid (occupancy x SMs) for the tile rule in use. */
-int wadg_batch_info(const wadg_batch* batch, int64_t info[4]);
+/* info[0..4] = meshes, work items, persistent blocks in use, largest
+ * resident grid (occupancy x SMs) for the tile rule in use, the tile rule in
+ * use (0, 1 or 2; see wadg_batch_autotune). */
+int wadg_batch_info(const wadg_batch* batch, int64_t info[5]);
 
 /* Number of persistent blocks (clamped to the number of work items). */
 int wadg_batch_set_grid(wadg_batch* batch, int grid);
 
-/* Autotuner: for each of two tile rules (the single-mesh columns-per-tile
- * rule, and one capped so that every degree fits three blocks per SM), times
- * right-hand-side launches of the whole batch with 1, 2, 3, 4, 6, 8 blocks
- * per SM (as occupancy allows) and one block per item; keeps the fastest rule
- * and grid and returns the grid in grid_out (nullable).  Q and res are not
- * modified; each mesh's work buffer is overwritten.  Synchronises `stream`.
- * Either rule gives bitwise the results of wadg_step: every column's
- * products are accumulated in the same order whatever the tile width. */
+/* Tile rule (0, 1 or 2; WADG_EINVAL otherwise), as wadg_batch_autotune
+ * describes them; the grid is clamped to the rule's work items.  A captured
+ * solve is captured again with the new rule or grid on its next call. */
+int wadg_batch_set_rule(wadg_batch* batch, int rule);
+
+/* Autotuner: for each of three tile rules, times right-hand-side launches of
+ * the whole batch with 1, 2, 3, 4, 6, 8 blocks per SM (as occupancy allows)
+ * and one block per item; keeps the fastest rule and grid and returns the
+ * grid in grid_out (nullable).  The rules (one kernel holds every degree, so
+ * its registers are the largest degree's and its shared memory the largest
+ * tile's):
+ *   0: the single-mesh columns per tile, registers capped for 2 blocks per SM;
+ *   1: the same tiles, registers capped for 3 blocks per SM;
+ *   2: tiles of at most 56 KB, registers capped for 4 blocks per SM.
+ * Q and res are not modified; each mesh's work buffer is overwritten.
+ * Synchronises `stream`.  Every rule gives bitwise the results of wadg_step:
+ * every column's products are accumulated in the same order whatever the
+ * tile width. */
 int wadg_batch_autotune(wadg_batch* batch, void* const* Q, void* const* res, int* grid_out, wadg_stream stream);
 
 /* nsteps LSRK(5,4) steps of every mesh (5 launches per step in total). */

@@ -26,6 +26,7 @@ from .api import (  # noqa: E402,F401
     wadg_batch_info,
     wadg_batch_last_error,
     wadg_batch_set_grid,
+    wadg_batch_set_rule,
     wadg_batch_solve,
     wadg_batch_step,
     wadg_energy,

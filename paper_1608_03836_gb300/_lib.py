@@ -43,6 +43,7 @@ SIGNATURES = {
     "wadg_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p)]),
     "wadg_batch_info": (c_int, [c_void_p, P_int64]),
     "wadg_batch_set_grid": (c_int, [c_void_p, c_int]),
+    "wadg_batch_set_rule": (c_int, [c_void_p, c_int]),
     "wadg_batch_autotune": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                     ctypes.POINTER(c_int), c_void_p]),
     "wadg_batch_step": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_double, c_double,

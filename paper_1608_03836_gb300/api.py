@@ -339,13 +339,17 @@ def wadg_batch_create(meshes) -> BatchHandle:
 
 
 def wadg_batch_info(batch: BatchHandle) -> dict:
-    info = (ctypes.c_int64 * 4)()
+    info = (ctypes.c_int64 * 5)()
     _bcheck(load().wadg_batch_info(batch.handle, info), "wadg_batch_info", batch)
-    return {"meshes": info[0], "items": info[1], "grid": info[2], "max_grid": info[3]}
+    return {"meshes": info[0], "items": info[1], "grid": info[2], "max_grid": info[3], "rule": info[4]}
 
 
 def wadg_batch_set_grid(batch: BatchHandle, grid: int):
     _bcheck(load().wadg_batch_set_grid(batch.handle, int(grid)), "wadg_batch_set_grid", batch)
+
+
+def wadg_batch_set_rule(batch: BatchHandle, rule: int):
+    _bcheck(load().wadg_batch_set_rule(batch.handle, int(rule)), "wadg_batch_set_rule", batch)
 
 
 def wadg_batch_autotune(batch: BatchHandle, Q, res, stream=None) -> int:

@@ -2,8 +2,8 @@
 // persistent launch per LSRK stage walks a work list of (mesh, tile) items,
 // each block dispatching on the item's degree to the CUDA-core stage tile
 // (stage_simt.cuh), so that 12 meshes cost 5 launches per step instead of 60.
-// Items are ordered heaviest degree first; an autotuner picks the number of
-// persistent blocks.  FP32 fields (WADG_FP32 meshes).
+// Items are ordered heaviest degree first; an autotuner picks the tile rule
+// and the number of persistent blocks.  FP32 fields (WADG_FP32 meshes).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -14,19 +14,32 @@
 
 namespace wadg {
 
-// Tile rules: rule 0 is the single-mesh rule (cols_per_block); rule 1 caps
-// every degree to ~76 KB of shared memory so that a mixed batch keeps three
-// blocks per SM, taking the widest of the single-mesh width, 8 and 4 columns
-// that fits (degree 5 then takes 8 columns per tile, degree 6 takes 4).
+// Tile rules.  One kernel holds every degree's tile, so its register count is
+// the largest over the degrees and its shared memory the largest tile's.
+//   rule 0: the single-mesh tile widths (cols_per_block, about 76 KB),
+//           registers capped for two blocks per SM (128);
+//   rule 1: the same widths, registers capped for three blocks per SM (80);
+//   rule 2: tiles of at most 56 KB (the widest of the single-mesh width, 20,
+//           12, 8 and 4 columns that fits) and registers capped for four
+//           blocks per SM (64), the occupancy that degree 6 reaches on its own.
+// The cap trades per-tile speed (registers, spills) for resident blocks: a
+// batch of many tiles gains from occupancy, a batch of few tiles from per-tile
+// latency, which is why the autotuner times all three (kBatchRules).
+
 template <int N, int RULE>
 constexpr int batch_cols() {
   constexpr int per = Dims<N>::PER_COL * 4;
   constexpr int e0 = cols_per_block<float, N>();
-  return RULE == 0 ? e0 : (per * e0 <= 77824 ? e0 : (per * 8 <= 77824 ? 8 : 4));
+  constexpr int cap = 57344;
+  if constexpr (RULE < 2) return e0;
+  return per * e0 <= cap ? e0 : (per * 20 <= cap ? 20 : (per * 12 <= cap ? 12 : (per * 8 <= cap ? 8 : 4)));
 }
 
+template <int RULE>
+constexpr int batch_min_blocks() { return RULE + 2; }
+
 template <int MODE, int RULE>
-__global__ void __launch_bounds__(kStageThreads) batch_stage_kernel(const StageParams<float>* __restrict__ params,
+__global__ void __launch_bounds__(kStageThreads, batch_min_blocks<RULE>()) batch_stage_kernel(const StageParams<float>* __restrict__ params,
                                                                     const int* __restrict__ item_mesh,
                                                                     const int* __restrict__ item_blk,
                                                                     const int* __restrict__ mesh_N, int nitems) {
@@ -73,7 +86,9 @@ static size_t per_col_bytes(int N) {
   }
 }
 
-int batch_cols_per_block(int N, int rule) { return rule == 0 ? cols_rule<0>(N) : cols_rule<1>(N); }
+int batch_cols_per_block(int N, int rule) {
+  return rule == 0 ? cols_rule<0>(N) : (rule == 1 ? cols_rule<1>(N) : cols_rule<2>(N));
+}
 
 size_t batch_smem_bytes(int N, int rule) { return per_col_bytes(N) * batch_cols_per_block(N, rule); }
 
@@ -91,16 +106,20 @@ cudaError_t launch_batch_stage(int mode, int rule, const StageParams<float>* par
                                const int* item_blk, const int* mesh_N, int nitems, int grid, size_t smem,
                                cudaStream_t st) {
   if (nitems == 0) return cudaSuccess;
-  if (mode == kRhs)
-    return rule == 0 ? launch_rule<kRhs, 0>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st)
-                     : launch_rule<kRhs, 1>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st);
-  return rule == 0 ? launch_rule<kLsrk, 0>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st)
-                   : launch_rule<kLsrk, 1>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st);
+  if (mode == kRhs) {
+    if (rule == 0) return launch_rule<kRhs, 0>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st);
+    if (rule == 1) return launch_rule<kRhs, 1>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st);
+    return launch_rule<kRhs, 2>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st);
+  }
+  if (rule == 0) return launch_rule<kLsrk, 0>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st);
+  if (rule == 1) return launch_rule<kLsrk, 1>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st);
+  return launch_rule<kLsrk, 2>(params, item_mesh, item_blk, mesh_N, nitems, grid, smem, st);
 }
 
 int batch_max_blocks_per_sm(int rule, size_t smem) {
   int n = 0;
-  auto kern = rule == 0 ? batch_stage_kernel<kLsrk, 0> : batch_stage_kernel<kLsrk, 1>;
+  auto kern = rule == 0 ? batch_stage_kernel<kLsrk, 0>
+                        : (rule == 1 ? batch_stage_kernel<kLsrk, 1> : batch_stage_kernel<kLsrk, 2>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kStageThreads, smem) != cudaSuccess) return 1;
   return n > 0 ? n : 1;

@@ -13,13 +13,13 @@ using namespace wadg;
 struct wadg_batch {
   std::vector<wadg_mesh*> meshes;
   int device = 0;
-  // work lists for the two tile rules (see batch.cu)
+  // work lists of the tile rules (see batch.cu)
   int rule = 0;
-  int nitems_r[2] = {0, 0};
-  int* d_item_mesh_r[2] = {nullptr, nullptr};
-  int* d_item_blk_r[2] = {nullptr, nullptr};
-  size_t smem_r[2] = {0, 0};
-  int max_grid_r[2] = {0, 0};
+  int nitems_r[kBatchRules] = {};
+  int* d_item_mesh_r[kBatchRules] = {};
+  int* d_item_blk_r[kBatchRules] = {};
+  size_t smem_r[kBatchRules] = {};
+  int max_grid_r[kBatchRules] = {};
   int* d_mesh_N = nullptr;
   int grid = 0;
   int nitems() const { return nitems_r[rule]; }
@@ -34,7 +34,7 @@ struct wadg_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> gkeyQ, gkeyR;
   double gkey_t0 = NAN, gkey_dt = NAN;
-  int gkey_n = -1;
+  int gkey_n = -1, gkey_rule = -1, gkey_grid = -1;
   std::string last_error;
 };
 
@@ -139,7 +139,7 @@ void wadg_batch_destroy(wadg_batch* b) {
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->stream) cudaStreamDestroy(b->stream);
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < kBatchRules; ++r) {
     cudaFree(b->d_item_mesh_r[r]);
     cudaFree(b->d_item_blk_r[r]);
   }
@@ -173,7 +173,7 @@ int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
   bool ok = cudaMalloc((void**)&b->d_mesh_N, mn.size() * sizeof(int)) == cudaSuccess &&
             cudaMalloc((void**)&b->d_params, 11 * count * sizeof(StageParams<float>)) == cudaSuccess &&
             cudaMemcpy(b->d_mesh_N, mn.data(), mn.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
-  for (int r = 0; r < 2 && ok; ++r) {
+  for (int r = 0; r < kBatchRules && ok; ++r) {
     std::vector<int> im, ib;
     for (int i = 0; i < count; ++i) b->smem_r[r] = std::max(b->smem_r[r], batch_smem_bytes(meshes[i]->N, r));
     for (int oi : order) {
@@ -202,12 +202,20 @@ int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
   return WADG_OK;
 }
 
-int wadg_batch_info(const wadg_batch* b, int64_t info[4]) {
+int wadg_batch_info(const wadg_batch* b, int64_t info[5]) {
   if (!b || !info) return WADG_EINVAL;
   info[0] = (int64_t)b->meshes.size();
   info[1] = b->nitems();
   info[2] = b->grid;
   info[3] = b->max_grid_r[b->rule];
+  info[4] = b->rule;
+  return WADG_OK;
+}
+
+int wadg_batch_set_rule(wadg_batch* b, int rule) {
+  if (!b || rule < 0 || rule >= kBatchRules) return WADG_EINVAL;
+  b->rule = rule;
+  b->grid = std::min(b->grid, std::max(1, b->nitems()));
   return WADG_OK;
 }
 
@@ -244,7 +252,7 @@ int wadg_batch_autotune(wadg_batch* b, void* const* Q, void* const* res, int* gr
   const size_t nm = b->meshes.size();
   float best = 1e30f;
   int best_g = b->grid, best_r = b->rule;
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < kBatchRules; ++r) {
     std::vector<int> cands;
     for (int mult : {1, 2, 3, 4, 6, 8})
       if (mult * nsm <= b->max_grid_r[r]) cands.push_back(mult * nsm);
@@ -302,7 +310,8 @@ int wadg_batch_solve(wadg_batch* b, void* const* Q, void* const* res, double t0,
     BCUDA(b, cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
   }
   const size_t nm = b->meshes.size();
-  bool same = b->exec && b->gkey_t0 == t0 && b->gkey_dt == dt && b->gkey_n == nsteps;
+  bool same = b->exec && b->gkey_t0 == t0 && b->gkey_dt == dt && b->gkey_n == nsteps &&
+              b->gkey_rule == b->rule && b->gkey_grid == b->grid;
   for (size_t i = 0; same && i < nm; ++i) same = b->gkeyQ[i] == Q[i] && b->gkeyR[i] == res[i];
   if (!same) {
     if (b->exec) {
@@ -330,6 +339,8 @@ int wadg_batch_solve(wadg_batch* b, void* const* Q, void* const* res, double t0,
     b->gkey_t0 = t0;
     b->gkey_dt = dt;
     b->gkey_n = nsteps;
+    b->gkey_rule = b->rule;
+    b->gkey_grid = b->grid;
   }
   BCUDA(b, cudaEventRecord(b->ev_in, (cudaStream_t)stream));
   BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev_in, 0));

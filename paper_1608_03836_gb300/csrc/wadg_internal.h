@@ -152,6 +152,8 @@ bool pack_tc_ops(int N, const RefOps& o, int fmt, std::vector<uint8_t>& out);
 cudaError_t launch_bounded_wait_selftest(int* err, uint32_t max_iters, cudaStream_t stream);
 
 // Batches of FP32 meshes (batch.cu).
+// Tile rules of mesh batches (batch.cu): 0, 1, 2.
+constexpr int kBatchRules = 3;
 int batch_cols_per_block(int N, int rule);
 size_t batch_smem_bytes(int N, int rule);
 int batch_max_blocks_per_sm(int rule, size_t smem);

@@ -58,6 +58,25 @@ def test_batch_step_equals_per_mesh_steps(W):
         assert n == ns
         for (Qr, Rr), Q, R in zip(ref, Qg, Rg):
             assert torch.equal(Qr, Q) and torch.equal(Rr, R)
+    # every tile rule (tile widths and register caps differ), stepped and as a
+    # captured solve that is captured again after the rule changes
+    for rule in (2, 0, 1):
+        W.wadg_batch_set_rule(b, rule)
+        info = W.wadg_batch_info(b)
+        assert info["rule"] == rule and 1 <= info["grid"] <= info["items"]
+        Qs = [q.clone() for q in Q0]
+        Rs = [torch.zeros_like(q) for q in Q0]
+        W.wadg_batch_step(b, Qs, Rs, 0.0, dt, ns)
+        Qg = [q.clone() for q in Q0]
+        Rg = [torch.zeros_like(q) for q in Q0]
+        W.wadg_batch_solve(b, Qg, Rg, 0.0, dt * ns, dt)
+        torch.cuda.synchronize()
+        for (Qr, Rr), Q, R, Q2, R2 in zip(ref, Qs, Rs, Qg, Rg):
+            assert torch.equal(Qr, Q) and torch.equal(Rr, R)
+            assert torch.equal(Qr, Q2) and torch.equal(Rr, R2)
+    with pytest.raises(W.WadgError) as e:
+        W.wadg_batch_set_rule(b, 3)
+    assert e.value.status == -1
 
 
 def test_batch_rejects_other_precisions(W):
