@@ -607,6 +607,8 @@ def main():
                     help="run only the N = 5 precision study (82,944 tets, T = 0.5) and print its JSON")
     ap.add_argument("--forms", action="store_true",
                     help="run only the formulation comparison on the headline mesh and print its JSON")
+    ap.add_argument("--batch", action="store_true",
+                    help="run only the uneven-batch study (12 meshes, N = 2..6, large and small) and print its JSON")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
     args = ap.parse_args()
@@ -630,6 +632,11 @@ def main():
     if args.forms:
         if rank == 0:
             print(json.dumps({"formulations": formulations(W, args.steps)}))
+        return
+    if args.batch:
+        if rank == 0:
+            print(json.dumps({"uneven_batch": uneven_batch(W, max(2, args.steps)),
+                              "uneven_batch_small": uneven_batch(W, max(2, args.steps), small=True)}))
         return
 
     def barrier():
