@@ -105,3 +105,58 @@ def test_step_does_not_read_the_incoming_residual(W, precision):
     Qn = Q0.cpu().pin_memory()
     W.wadg_step_host(m, Qn, None, 0.0, 0.003, 2)  # the residual stays on the device
     assert torch.equal(Qn, Qa.cpu())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16"])
+def test_resume_from_a_host_checkpoint_equals_the_uninterrupted_run(W, precision):
+    """Checkpoint / resume: six steps in one call against three steps, a dump
+    of (Q, res) to host memory, and three more steps from fresh device buffers
+    restored from the dump, started at t0 + 3 dt.  With point sources (two
+    shots) and dt a power of two, every stage time t0 + n dt + c_s dt is the
+    same double in both runs, and the two runs agree bit for bit, receiver
+    traces included."""
+    import torch
+    from synthetic import source_positions, receiver_positions
+    N, S, R = 3, 2, 2
+    VXYZ, EToV, geom = make_mesh_inputs(2, N)
+    m = library_mesh(VXYZ, EToV, geom, N, precision, shots=S)
+    W.wadg_set_sources(m, source_positions(S), 5.0, 0.02)
+    W.wadg_set_receivers(m, receiver_positions(S * R).reshape(S, R, 3))
+    dt = 2.0 ** -9
+    Q0 = to_torch(random_Q(m.K, S, m.Np, seed=91), m.dtype) * 1e-3
+    Qa, Ra = Q0.clone(), torch.zeros_like(Q0)
+    tra = torch.zeros((6, S, R), dtype=m.dtype, device="cuda")
+    W.wadg_step(m, Qa, Ra, 0.0, dt, 6, tra)
+    Qb, Rb = Q0.clone(), torch.zeros_like(Q0)
+    trb = torch.zeros((3, S, R), dtype=m.dtype, device="cuda")
+    W.wadg_step(m, Qb, Rb, 0.0, dt, 3, trb)
+    dump = (Qb.cpu(), Rb.cpu())                      # the checkpoint, on the host
+    del Qb, Rb
+    Qc, Rc = dump[0].cuda(), dump[1].cuda()
+    trc = torch.zeros((3, S, R), dtype=m.dtype, device="cuda")
+    W.wadg_step(m, Qc, Rc, 0.0 + 3 * dt, dt, 3, trc)
+    torch.cuda.synchronize()
+    W.wadg_device_status(m)
+    assert not torch.equal(Qc, Q0)
+    assert torch.equal(Qa, Qc) and torch.equal(Ra, Rc)
+    assert torch.equal(tra[:3], trb) and torch.equal(tra[3:], trc)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_blow_up_is_reported_by_the_energy(W, precision):
+    """Blow-up detector: a state with a non-finite value gives WADG_EUNSTABLE
+    from the energy reduction (both entry points); a finite state does not."""
+    import torch
+    N = 2
+    VXYZ, EToV, geom = make_mesh_inputs(2, N)
+    m = library_mesh(VXYZ, EToV, geom, N, precision)
+    Q = to_torch(random_Q(m.K, 1, m.Np, seed=92), m.dtype)
+    assert np.isfinite(W.wadg_energy(m, Q)) and W.wadg_energy(m, Q) > 0
+    for bad in (float("nan"), float("inf")):
+        Qb = Q.clone()
+        Qb[2, m.K // 2, 0, 3] = bad
+        for fn in (W.wadg_energy, W.wadg_energy_noalloc):
+            with pytest.raises(W.WadgError) as e:
+                fn(m, Qb)
+            assert e.value.status == -7
+    assert W.wadg_energy(m, Q) > 0
