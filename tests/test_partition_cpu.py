@@ -130,7 +130,7 @@ def _rank_worker(rank, ws, port, nsteps, out):
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_step_like_the_whole_mesh():
+def test_two_gloo_ranks_step_like_the_whole_mesh(part_mod):
     """Two ranks (gloo), two LSRK(5,4) steps with a halo exchange before each
     stage, each rank starting from its owned columns only (ghosts NaN until
     the first exchange): the owned columns gathered from both ranks equal the
