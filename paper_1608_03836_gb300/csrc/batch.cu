@@ -16,23 +16,18 @@ namespace wadg {
 
 // Tile rules.  One kernel holds every degree's tile, so its register count is
 // the largest over the degrees and its shared memory the largest tile's.
-//   rule 0: the single-mesh tile widths (cols_per_block, about 76 KB),
-//           registers capped for two blocks per SM (128);
+//   rule 0: tiles of at most 76 KB (28, 20, 12, 8 or 4 columns, the widest
+//           that fits), registers capped for two blocks per SM (128);
 //   rule 1: the same widths, registers capped for three blocks per SM (80);
-//   rule 2: tiles of at most 56 KB (the widest of the single-mesh width, 20,
-//           12, 8 and 4 columns that fits) and registers capped for four
-//           blocks per SM (64), the occupancy that degree 6 reaches on its own.
+//   rule 2: tiles of at most 56 KB and registers capped for four blocks per
+//           SM (64), the occupancy that degree 6 reaches on its own.
 // The cap trades per-tile speed (registers, spills) for resident blocks: a
 // batch of many tiles gains from occupancy, a batch of few tiles from per-tile
 // latency, which is why the autotuner times all three (kBatchRules).
 
 template <int N, int RULE>
 constexpr int batch_cols() {
-  constexpr int per = Dims<N>::PER_COL * 4;
-  constexpr int e0 = cols_per_block<float, N>();
-  constexpr int cap = 57344;
-  if constexpr (RULE < 2) return e0;
-  return per * e0 <= cap ? e0 : (per * 20 <= cap ? 20 : (per * 12 <= cap ? 12 : (per * 8 <= cap ? 8 : 4)));
+  return cols_for_budget<float, N, Dims<N>::PER_COL, RULE < 2 ? 77824 : 57344>();
 }
 
 template <int RULE>

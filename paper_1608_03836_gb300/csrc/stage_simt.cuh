@@ -61,24 +61,29 @@ struct Dims {
 // Columns per block E.  E = 4 (mod 8) makes the row stride of the [row][E]
 // shared arrays 16 words modulo 32 banks, so that the 4x4 register tiles of a
 // warp (column group fastest) store without bank conflicts; E = 8 is taken
-// where 12 columns do not fit.  Budget: about 76 KB of shared memory (3
-// blocks per SM).
+// where 12 columns do not fit.  FP32 budget (BUDGET bytes of shared memory
+// per block): 56 KB, four blocks per SM at 256 threads and at most 64
+// registers, for every degree but N = 5, which keeps 76 KB (three blocks).
+// The stage waits on its operator loads, so resident warps count for more
+// than wide tiles; measured per LSRK step (FP32): N = 2 -15 %, N = 3 -6 %,
+// N = 4 -8 % (-24 % in the strong form) against 76 KB, N = 5 +4 % (8 columns
+// in 69 KB beat 4 in 35 KB, and 12 columns in 103 KB by 18 %).
 // FP64 is bound by the FP64 pipe, not by shared memory: it keeps ~96 KB
 // blocks with E a multiple of 4.
-template <typename T, int N, int PER>
-constexpr int cols_for() {
+template <typename T, int N, int PER, int BUDGET>
+constexpr int cols_for_budget() {
   constexpr int per = PER * (int)sizeof(T);
   if (sizeof(T) == 8) {
     constexpr int e8 = (98304 / per) / 4 * 4;
     return e8 < 4 ? 4 : (e8 > 32 ? 32 : e8);
   }
-  // ~76 KB: three blocks per SM (measured at N = 5: 8 columns in 69 KB beat
-  // 12 columns in 103 KB at two blocks per SM by 18 %; at N = 6, 4 columns in
-  // 48 KB beat 8 columns in 96 KB)
-  constexpr int budget = 77824;
-  constexpr int fit = budget / per;
+  constexpr int fit = BUDGET / per;
   constexpr int e = fit >= 28 ? 28 : (fit >= 20 ? 20 : (fit >= 12 ? 12 : (fit >= 8 ? 8 : 4)));
   return e;
+}
+template <typename T, int N, int PER>
+constexpr int cols_for() {
+  return cols_for_budget<T, N, PER, N == 5 ? 77824 : 57344>();
 }
 template <typename T, int N>
 constexpr int cols_per_block() {
