@@ -58,3 +58,24 @@ def test_job_value_counts_every_rank():
     b = _bench()
     assert b.job_value(4 * 196608 * 35, 5, 2.0, 1) == pytest.approx(4 * 196608 * 35 * 5 / 2e-3)
     assert b.job_value(100, 5, 2.0, 4) == pytest.approx(4 * b.job_value(100, 5, 2.0, 1))
+
+
+def test_both_arms_report_the_same_config():
+    """The reference arm (the oracle on a bounded sample, on the host) prints
+    the native arm's config; the sample is described in its cpu_baseline."""
+    import json
+    import os
+    import subprocess
+    import sys
+    b = _bench()
+    cfg = b.headline_config(1)
+    assert cfg["elements"] == 196608 and cfg["volume_points"] == 63 and cfg["dof"] == 4 * 196608 * 35
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["config"] == cfg
+    assert line["metric"] == b.METRIC and line["unit"] == b.UNIT and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and "sample" in line["cpu_baseline"]["sample"]
