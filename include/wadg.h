@@ -240,10 +240,10 @@ int wadg_energy(wadg_mesh* mesh, const void* Q, double* E, wadg_stream stream);
 
 /* The energy of wadg_energy, computed without allocating anything.  The paper
  * has no counterpart: this entry point serves callers that must not call
- * cudaMalloc when they need the value -- code running while a stream is being
- * captured into a CUDA graph, code inside a framework whose caching allocator
- * owns the device memory budget, and real-time loops that must not wait on the
- * driver's allocator.  Its scratch is a fixed array of 2^20 + 1 doubles
+ * cudaMalloc when they need the value -- code inside a framework whose caching
+ * allocator owns the device memory budget, and real-time loops that must not
+ * wait on the driver's allocator.  Like wadg_energy it returns E on the host,
+ * so it synchronises `stream` before returning.  Its scratch is a fixed array of 2^20 + 1 doubles
  * (8 MiB) in device memory that every GPU loading the library holds until the
  * process exits; a mesh with K*S > 2^20 columns is rejected with WADG_EINVAL.
  * The first call on a device looks up the array's address

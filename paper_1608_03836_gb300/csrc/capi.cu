@@ -950,6 +950,10 @@ int step_t(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, v
 
 }  // namespace
 
+// The readiness check of the entry points that read the operators, shared
+// with the allocation-free energy (csrc/noalloc.cu).
+int wadg_mesh_ready(wadg_mesh* m) { return check_ready(m); }
+
 extern "C" {
 
 int wadg_rhs(wadg_mesh* m, const void* Q, void* dQdt, wadg_stream stream) {

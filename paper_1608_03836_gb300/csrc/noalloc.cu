@@ -1,14 +1,14 @@
 // wadg_energy_noalloc: the energy reduction without any allocation.
 //
 // Some callers cannot call cudaMalloc at the moment they need a diagnostic:
-// code that runs while a CUDA stream is being captured into a graph (an
-// allocation there would invalidate the capture), code that lives inside a
-// framework whose caching allocator already owns the device memory budget,
+// code inside a framework whose caching allocator already owns the device
+// memory budget (a cudaMalloc behind its back can fail or evict its cache),
 // and real-time loops that must not block on the driver's allocator.  This
 // entry point gives them the energy of a field without allocating: the
 // per-column partial sums go to a fixed array in device memory that is part
 // of the library image, instead of the scratch that wadg_set_operators
-// allocates for wadg_energy.
+// allocates for wadg_energy.  Like wadg_energy, it returns the value on the
+// host, so it synchronises the caller's stream before it returns.
 #include <cmath>
 #include <mutex>
 
@@ -38,8 +38,8 @@ int set_error(wadg_mesh* m, int status, const char* msg) {
 }  // namespace
 
 extern "C" int wadg_energy_noalloc(wadg_mesh* m, const void* Q, double* E, wadg_stream stream) {
-  if (!m) return WADG_EINVAL;
-  if (m->precision < 0) return set_error(m, WADG_ESTATE, "wadg_set_operators has not been called");
+  const int ready = wadg_mesh_ready(m);  // the same checks, status and message as wadg_energy
+  if (ready != WADG_OK) return ready;
   if (!Q || !E) return set_error(m, WADG_EINVAL, "null pointer");
   const int64_t ncols = m->K * m->S;
   if (ncols > kMaxColumns)

@@ -245,3 +245,8 @@ struct wadg_mesh {
   uint64_t generation = 0;  // bumped by every call that changes operators, sources or receivers
   std::string last_error;
 };
+
+// WADG_OK when the entry points that read the operators may run (operators
+// uploaded; strong-form tables built when a strong form is selected), else
+// the status those entry points return, with last_error set.
+int wadg_mesh_ready(wadg_mesh* m);

@@ -1,11 +1,11 @@
 """The allocation-free energy entry point (wadg_energy_noalloc).
 
 Some callers cannot allocate device memory when they want the energy: code
-running during CUDA graph capture, code inside a framework that owns the
-device memory, real-time loops.  wadg_energy_noalloc serves them from a fixed
-scratch array in the library image.  This file is collected last so that a
-run stopping at the first failure has already run every other test; it also
-passes on its own in a fresh process.
+inside a framework whose allocator owns the device memory, and real-time loops
+that must not wait on the driver's allocator.  wadg_energy_noalloc serves them
+from a fixed scratch array in the library image.  This file is collected last
+so that a run stopping at the first failure has already run every other test;
+it also passes on its own in a fresh process.
 """
 import numpy as np
 import pytest
