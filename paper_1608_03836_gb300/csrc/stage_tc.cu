@@ -31,8 +31,10 @@
 // of four points (one 16-byte load per four points).  Every tcgen05.mma holds
 // its issuing thread for 100-200 cycles, so lane 0 of every warp issues at
 // most one accumulator chain per step.  Waits on the tensor cores and the bulk
-// copies are bounded; on expiry the CTA records an error in P.err, drains its
-// copies and products, frees its TMEM and returns.
+// copies are bounded; on expiry the CTA records an error in P.err, issues no
+// further copies or products, waits (again bounded) for those already issued,
+// frees its TMEM and returns.  The report is best effort: work still in flight
+// when the drain's own bound runs out is not waited for.
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -311,8 +313,12 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   const uint8_t* vol_ops = P.ops;
   const uint8_t* upd_ops = P.ops + (size_t)NCH * T::SZ_OPV;
 
+  // once a wait has expired (sflag set) no further copy or product is issued,
+  // so the drain at the end only waits for work issued before the failure
+  auto live = [&]() { return *(volatile int*)sflag == 0; };
   // thread 0: operator slots (bulk copies completing on bars[s])
   auto load_slot = [&](int s, const uint8_t* src, int bytes) {
+    if (!live()) return;
     tc::mbar_expect_tx(bar(s), (uint32_t)bytes);
     tc::bulk_g2s(slot_addr(s), src, (uint32_t)bytes, bar(s));
     pend |= 1u << s;
@@ -347,6 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   // U1 chains (9 instructions each at N = 4) on warps 8-11, the DW and U2
   // chains (3 each) on warps 0-5.
   auto issue_V = [&](int c, int w) {  // u_i = V_q u_i (N = 16 each), dp/dx^_a = V_q^a p (N = 48)
+    if (!live()) return;
     const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1);
     const int i = w - 8;
     if (i >= 0 && i < 3)
@@ -359,6 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   // b_p += sum_a Dw_a U^a (one accumulator per a; a = r holds the surface
   // term), b_ui += Vw g_i (onto the surface terms)
   auto issue_DW = [&](int c, int i) {
+    if (!live()) return;
     const uint32_t sl = slot_addr(2 + (c & 1)), bvw = sl + 6 * T::B_P;
     if (i < 3)
       OF::template chain<16>(mk_mma3(tmem + (i == 0 ? T::TB : T::TBX + KP * (i - 1)), ax + (2 * i) * T::A_CH,
@@ -369,6 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
                             bvw, bvw + T::B_P, sbo_16, OF::idesc(128, KP), true));
   };
   auto issue_U1 = [&](int c, int w) {  // (V_q M^^{-1}) b per field (N = 32)
+    if (!live()) return;
     const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1U);
     const int f = w - 8;
     if (f >= 0 && f < 4)
@@ -376,6 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
                                      sl, sl + T::B_UV, sbo_KP, OF::idesc(128, T::UQC), false));
   };
   auto issue_U2 = [&](int c, int f) {  // r += P_q (W ...) per field (N = KP, K = 32)
+    if (!live()) return;
     const uint32_t sl = slot_addr(2 + (c & 1)), sbo_32 = OF::sbo(T::UQC);
     if (f < 4)
       OF::template chain<T::UQC>(mk_mma3(tmem + T::TB + KP * f, ax + (2 * f) * T::A_UCH, ax + (2 * f + 1) * T::A_UCH,
@@ -387,6 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   const bool bulkq = NPS == NP && P.bulk_q != 0;
   uint32_t par_q = 0;
   auto load_q = [&](int64_t t) {  // thread 0
+    if (!live()) return;
     const int64_t c0 = t * TILE;
     const uint32_t bytes = (uint32_t)((ncols - c0 < TILE ? ncols - c0 : TILE) * NP * 4);
     tc::mbar_expect_tx(bar(9), 4 * bytes);
@@ -563,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       sync_check();
       if (failed) break;
       if (issuer) {
-        if (warp < 7)
+        if (warp < 7 && live())
           OF::template chain<NFP16>(mk_mma3(tmem + T::TI + warp * NFQ16, fa + (2 * warp) * T::A_FN,
                                          fa + (2 * warp + 1) * T::A_FN, OF::sbo(NFP16), ft, ft + T::B_TRI,
                                          OF::sbo(NFP16), OF::idesc(128, NFQ16), false));
@@ -614,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       if (issuer) {
         const uint32_t bl = ft + 2 * T::B_TRI;
         const int fld = warp - 8;
-        if (fld >= 0 && fld < 4)
+        if (fld >= 0 && fld < 4 && live())
           OF::template chain<NFQ16>(mk_mma3(tmem + T::TL + fld * NFP16, fa + (2 * fld) * T::A_FQ,
                                          fa + (2 * fld + 1) * T::A_FQ, OF::sbo(NFQ16), bl, bl + T::B_TRI,
                                          OF::sbo(NFQ16), OF::idesc(128, NFP16), false));
