@@ -411,6 +411,53 @@ def test_convergence_energy_and_dg_agreement():
         assert rate > N + 0.5 - 0.15, (N, errs, rate)
 
 
+@pytest.mark.slow
+def test_convergence_rates_on_three_meshes():
+    """Sec. 5.3: the strong-weak WADG error to the analytic standing wave falls
+    at least like h^(N+1/2).  N = 2..4 on n = 2, 4, 8 hexes per side (48 to
+    3,072 tets, warped): the slope over the whole range and over the finest
+    pair must both reach N + 1/2 (a dropped or mis-signed term in the volume,
+    flux, lift or update costs at least one order).  T = 0.05 at CFL 1; the
+    time error (fourth order) is far below the spatial one."""
+    T = 0.05
+    for N in (2, 3, 4):
+        errs = []
+        for n in (2, 4, 8):
+            ref, mesh = _mesh(n, N)
+            dt = _cfl_dt(mesh, N, cfl=1.0)
+            ns = int(math.ceil(T / dt))
+            dt = T / ns
+            c = W.wadg_projection(mesh, standing_wave(mesh.xq, 0.0))
+            res = np.zeros_like(c)
+            for s in range(ns):
+                c, res = W.lsrk_step(lambda q, t: W.rhs(mesh, q), c, res, s * dt, dt)
+            errs.append(W.l2_error(mesh, c, lambda x: standing_wave(x, T)))
+        overall = math.log2(errs[0] / errs[2]) / 2
+        finest = math.log2(errs[1] / errs[2])
+        assert overall >= N + 0.5 and finest >= N + 0.5, (N, errs, overall, finest)
+
+
+def test_quadrature_energy_weights_pressure_by_inverse_wave_speed():
+    """The energy 1/2 int (p^2/c^2 + |u|^2) in closed form on the warped cube
+    (N = 3: J has degree 6 <= 2N+1, so the rule integrates J exactly and the
+    curved elements fill the volume 8 of [-1,1]^3): p = 1, u = 0 with c^2 = 4
+    gives 1/2 * 8/4 = 1 (a missing 1/c^2 gives 4, an inverted one 16);
+    p = 0, u = (1, 1, 1) gives 12 whatever c^2 is; c^2 = 1 + x^2 sampled at
+    the points gives 1/2 int 1/(1 + x^2) = 1/2 * 4 * 2 arctan(1) = pi up to
+    the rule's error for a non-polynomial integrand."""
+    ref, mesh = _mesh(2, 3)
+    ones = np.ones((mesh.K, ref.Np))
+    zero = np.zeros_like(ones)
+    cp = ref.to_modal(np.stack([ones, zero, zero, zero]))
+    cu = ref.to_modal(np.stack([zero, ones, ones, ones]))
+    c2 = np.full(mesh.J.shape, 4.0)
+    assert abs(W.quadrature_energy(mesh, cp, c2q=c2) - 1.0) < 1e-13
+    assert abs(W.quadrature_energy(mesh, cp) - 4.0) < 1e-13
+    assert abs(W.quadrature_energy(mesh, cu, c2q=c2) - 12.0) < 1e-13
+    c2x = 1.0 + mesh.xq[..., 0] ** 2
+    assert abs(W.quadrature_energy(mesh, cp, c2q=c2x) - math.pi) < 2e-5
+
+
 def test_wave_speed_enters_the_pressure_row():
     """Sec. 7: with constant c^2 = 4 the standing wave oscillates at 2 omega.
     p = C cos(2 omega t), u = -grad C sin(2 omega t) / (2 omega).  A weight on
