@@ -13,13 +13,17 @@ from synthetic import warped_cube, c2_heterogeneous, random_fields
 # Parity bars (relative L2 over all compared values, and max-abs relative to
 # the largest expected value).  FP64: the target 1e-11.  FP32: unit roundoff
 # 6e-8 amplified by dot products of up to 3 Nq terms and the operator norms of
-# V_q^a / P_q (about 10^2 at N <= 6): 1e-5.  Split bf16 (x = hi + lo, three
-# products): each operand is represented to 2^-17 relative, so each product
-# to about 2^-16 = 1.5e-5 before the same amplification: 5e-5.  TF32 (10-bit
-# mantissa, round to nearest): each operand to 2^-11 = 4.9e-4, each product
-# to about 1e-3, three products in series (interpolate, weight, project) and
-# the same amplification: 5e-3.
-TOL = {"fp64": 1e-11, "fp32": 1e-5, "fp32_3xbf16": 5e-5, "fp32_tf32": 5e-3}
+# V_q^a / P_q; measured 5e-7 at N <= 4, 7e-7 at N = 5, 1.1e-6 at N = 6 (the
+# worst case), so the bar is 2e-6: a tenfold regression anywhere fails.
+# Split bf16 (x = hi + lo with bf16 parts of 8 significant bits, three
+# products hi*hi + hi*lo + lo*hi): |lo| <= 2^-8 |x|, the residual of the split
+# and the dropped lo*lo are each <= 2^-16 relative, so each product carries
+# about 2^-16 = 1.5e-5 before amplification; measured 1.2e-5 on the RHS and
+# 2.6e-5 on receiver samples of p (a few point values, less averaging): 3e-5.
+# TF32 (10-bit mantissa, round to nearest): each operand to 2^-11 = 4.9e-4,
+# each product to about 1e-3, three products in series (interpolate, weight,
+# project) and the same amplification: 5e-3 (measured 7e-4 to 1e-3).
+TOL = {"fp64": 1e-11, "fp32": 2e-6, "fp32_3xbf16": 3e-5, "fp32_tf32": 5e-3}
 
 
 def make_mesh_inputs(n, N, amp=0.1):

@@ -1,10 +1,11 @@
 """Batches of meshes of uneven size and degree: one persistent launch per
-stage gives bitwise the per-mesh results; the autotuner and the captured
+stage gives bitwise the per-mesh results, and each mesh of the batch matches
+the FP64 oracle's steps of that mesh alone; the autotuner and the captured
 solve keep them."""
 import numpy as np
 import pytest
 
-from gpu_util import library_mesh, make_mesh_inputs, random_Q, to_torch
+from gpu_util import TOL, library_mesh, make_mesh_inputs, oracle_c2, oracle_case, random_Q, rel_errors, to_torch
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +78,39 @@ def test_batch_step_equals_per_mesh_steps(W):
     with pytest.raises(W.WadgError) as e:
         W.wadg_batch_set_rule(b, 3)
     assert e.value.status == -1
+
+
+def test_batch_step_matches_oracle(W):
+    """Four meshes of uneven size and degree (N = 2..5, one with two shots,
+    heterogeneous c^2) stepped together by the persistent batch launch: every
+    mesh's state after three LSRK steps against the FP64 oracle's steps of
+    that mesh alone, element by element, at the FP32 bar."""
+    import torch
+    from oracle import wadg as OW
+    spec = [(2, 2, 1), (1, 5, 1), (2, 3, 2), (2, 4, 1)]
+    ms = _meshes(W, spec)
+    Q0 = [random_Q(m.K, m.S, m.Np, 60 + i) for i, m in enumerate(ms)]
+    Qs = [to_torch(q, torch.float32) for q in Q0]
+    Rs = [torch.zeros_like(q) for q in Qs]
+    b = W.wadg_batch_create(ms)
+    dt, ns = 1e-3, 3
+    W.wadg_batch_step(b, Qs, Rs, 0.0, dt, ns)
+    torch.cuda.synchronize()
+    for (n, N, S), q0, Q, R in zip(spec, Q0, Qs, Rs):
+        VXYZ, EToV, geom = make_mesh_inputs(n, N)
+        om = oracle_case(VXYZ, EToV, geom, N)
+        c2o = oracle_c2(om, "heterogeneous")
+        q0 = q0.astype(np.float32).astype(np.float64)
+        got_Q = Q.double().cpu().numpy()
+        got_R = R.double().cpu().numpy()
+        for s in range(S):
+            c = om.ref.to_modal(q0[:, :, s])
+            res = np.zeros_like(c)
+            for k in range(ns):
+                c, res = OW.lsrk_step(lambda q, t: OW.rhs(om, q, c2q=c2o), c, res, k * dt, dt)
+            l2, mx = rel_errors(got_Q[:, :, s], om.ref.to_nodal(c))
+            l2r, _ = rel_errors(got_R[:, :, s], om.ref.to_nodal(res))
+            assert l2 < TOL["fp32"] and mx < 10 * TOL["fp32"] and l2r < 10 * TOL["fp32"], (N, s, l2, mx, l2r)
 
 
 def test_batch_rejects_other_precisions(W):

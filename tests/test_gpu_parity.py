@@ -170,6 +170,25 @@ def test_projection_energy_and_error_match_oracle(W):
     assert abs(err - want) < 1e-9 * want
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_energy_matches_oracle_with_heterogeneous_wave_speed(W, precision):
+    """wadg_energy (FP64 reduction) against the oracle's 1/2 int (p^2/c^2 +
+    |u|^2) with c^2 = 1 + 0.5 sin sin sin at the volume points, two shots of
+    random fields (the oracle sees the same values the library holds)."""
+    from oracle import wadg as OW
+    N, S = 3, 2
+    VXYZ, EToV, geom = make_mesh_inputs(2, N)
+    om = oracle_case(VXYZ, EToV, geom, N)
+    m = library_mesh(VXYZ, EToV, geom, N, precision, shots=S, c2="heterogeneous")
+    Q = random_Q(m.K, S, m.Np, seed=17)
+    Qt = to_torch(Q, m.dtype)
+    Qh = Qt.double().cpu().numpy()
+    c2q = oracle_c2(om, "heterogeneous")
+    want = sum(OW.quadrature_energy(om, om.ref.to_modal(Qh[:, :, s]), c2q=c2q) for s in range(S))
+    got = W.wadg_energy(m, Qt)
+    assert abs(got - want) < 1e-12 * want, (got, want)
+
+
 def test_bad_arguments_are_rejected(W):
     import torch
     VXYZ, EToV, geom = make_mesh_inputs(1, 2)
