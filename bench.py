@@ -267,6 +267,44 @@ def batched_shots(W, steps):
                      "max_abs_trace": float(tr.abs().max())}
         del Q, Rs, m, tr
         torch.cuda.empty_cache()
+    out["accuracy_vs_fp64"] = shots_accuracy(W)
+    return out
+
+
+def shots_accuracy(W, S=4, nsteps=120, t_start=0.1):
+    """The batched-shot paths against FP64 on the same shots: the first S of
+    the 64 shots (same sources, receivers, mesh and rule), from zero fields at
+    t_start (the wavelet, centred at t0 = 0.24, is below 1 % of its peak
+    there) for nsteps steps; relative L2 difference from the FP64 run of the
+    final p (all shots) and of the receiver traces."""
+    import torch
+    from synthetic import warped_cube, source_positions, receiver_positions
+    n, N, R = 16, 4, 8
+    VXYZ, EToV, geom = warped_cube(n, N, 0.1)
+    rule = headline_rule()
+    dt = 0.5 * (1.0 / n) / (N + 1) ** 2
+    runs = {}
+    for prec in ("fp64", "fp32", "fp32_3xbf16", "fp32_tf32"):
+        m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
+        W.wadg_set_operators(m, prec, S, 1.0, 1.0, None)
+        W.wadg_set_sources(m, source_positions(64)[:S], 5.0, 0.24)
+        W.wadg_set_receivers(m, receiver_positions(R * 64).reshape(64, R, 3)[:S])
+        Q = torch.zeros((4, m.K, S, m.Np), dtype=m.dtype, device="cuda")
+        Rs = torch.zeros_like(Q)
+        tr = torch.zeros((nsteps, S, R), dtype=m.dtype, device="cuda")
+        W.wadg_step(m, Q, Rs, t_start, dt, nsteps, tr)
+        torch.cuda.synchronize()
+        W.wadg_device_status(m)
+        runs[prec] = (Q[0].double().cpu().numpy(), tr.double().cpu().numpy())
+        del Q, Rs, tr, m
+        torch.cuda.empty_cache()
+    p64, t64 = runs["fp64"]
+    out = {"workload": f"first {S} of the 64 shots, {nsteps} steps of dt = {dt:.3e} from t = {t_start}",
+           "fp64_max_abs_trace": float(np.abs(t64).max())}
+    for prec in ("fp32", "fp32_3xbf16", "fp32_tf32"):
+        p, t = runs[prec]
+        out[prec] = {"p_rel_l2_vs_fp64": float(np.linalg.norm(p - p64) / np.linalg.norm(p64)),
+                     "traces_rel_l2_vs_fp64": float(np.linalg.norm(t - t64) / np.linalg.norm(t64))}
     return out
 
 
@@ -404,6 +442,74 @@ def accuracy(W):
     return out
 
 
+EQUAL_ERROR_CASES = ((32, 2), (16, 3), (24, 3), (8, 4), (12, 4))
+
+
+def equal_error(W, T=0.25):
+    """The headline comparison: plain FP64 against the mixed-precision paths
+    on the same mesh, N, data (standing wave, c^2 = 1), dt and number of
+    steps; each whole solve to T is one captured graph (wadg_solve), timed
+    with CUDA events after an untimed first solve; error = L2 error of p
+    against the analytic solution by the volume rule.  'Equal' means within
+    1.05x of the FP64 error.  Meshes (n^3 x 6 tets) and degrees where the
+    discretisation error lies well above the FP32 rounding floor; the
+    fewer-point volume rules where tabulated (N = 3, 4), else the (N+1)^3
+    rule.  'headline' names the case with the most DOF where every
+    FP32-field path but TF32 keeps equal error."""
+    import torch
+    from synthetic import warped_cube, standing_wave, fewer_point_rule
+    out = {}
+    for n, N in EQUAL_ERROR_CASES:
+        VXYZ, EToV, geom = warped_cube(n, N, 0.1)
+        rule = fewer_point_rule(N) if N in (3, 4) else None
+        dt_max = 0.5 * (1.0 / n) / (N + 1) ** 2
+        case = {"workload": f"warped cube {n}^3x6 = {len(EToV)} tets, N={N}, "
+                            f"{'collapsed' if rule is None else str(len(rule[1])) + '-point'} volume rule, c^2=1, "
+                            f"standing wave to T={T}, dt_max={dt_max:.3e}"}
+        for prec in ("fp64", "fp32_3xbf16", "fp32", "fp32_tf32"):
+            m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
+            W.wadg_set_operators(m, prec, 1, 1.0, 1.0, None)
+            xq = W.wadg_volume_points(m)
+            f0 = torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda()
+            Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
+            R = torch.zeros_like(Q)
+            W.wadg_project(m, f0, Q)
+            W.wadg_solve(m, Q, R, 0.0, T, dt_max)       # captures the graph
+            W.wadg_project(m, f0, Q)
+            R.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            nsteps = W.wadg_solve(m, Q, R, 0.0, T, dt_max)
+            b.record()
+            torch.cuda.synchronize()
+            W.wadg_device_status(m)
+            ms = a.elapsed_time(b)
+            err = W.wadg_l2_error(m, Q, torch.from_numpy(standing_wave(xq, T)[:, :, None, :]).cuda(), 1)
+            dof = 4 * m.K * m.Np
+            case[prec] = {"l2_error_p": err, "nsteps": nsteps, "solve_ms": ms,
+                          "value": dof * 5 * nsteps / (ms * 1e-3)}
+            del Q, R, f0, m
+            torch.cuda.empty_cache()
+        e64, v64 = case["fp64"]["l2_error_p"], case["fp64"]["value"]
+        for prec in ("fp32_3xbf16", "fp32", "fp32_tf32"):
+            case[prec]["ratio_to_fp64"] = case[prec]["l2_error_p"] / e64
+            case[prec]["equal_l2_error"] = bool(case[prec]["l2_error_p"] <= 1.05 * e64)
+            case[prec]["speedup_over_fp64"] = case[prec]["value"] / v64
+        case["dof"] = 4 * len(EToV) * (N + 1) * (N + 2) * (N + 3) // 6
+        out[f"n{n}_N{N}"] = case
+    eq = [k for k, c in out.items() if c["fp32_3xbf16"]["equal_l2_error"] and c["fp32"]["equal_l2_error"]]
+    if eq:
+        k = max(eq, key=lambda k: out[k]["dof"])
+        c = out[k]
+        out["headline"] = {"case": k, "fp64_value": c["fp64"]["value"], "mixed_value": c["fp32_3xbf16"]["value"],
+                           "speedup": c["fp32_3xbf16"]["speedup_over_fp64"],
+                           "fp64_l2_error_p": c["fp64"]["l2_error_p"],
+                           "mixed_l2_error_p": c["fp32_3xbf16"]["l2_error_p"],
+                           "error_ratio": c["fp32_3xbf16"]["ratio_to_fp64"]}
+    return out
+
+
 def algorithmic_form(N: int, S: int, s: int, form: str) -> int:
     """Algorithmic bytes per element and stage of a formulation: the strong
     form reads its 9 geometric factors at (max(N+1, 2N-1))^3 volume points and
@@ -521,32 +627,65 @@ def e2e_steps(W, m, Q, steps):
     return a.elapsed_time(b) / steps, nq, nq
 
 
+def _limit_blas_threads():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    try:
+        from threadpoolctl import threadpool_limits
+        return threadpool_limits(1)
+    except Exception:
+        return None
+
+
+SAMPLE_N = 16  # hexahedra per cube side in the oracle's sample (16^3 x 6 = 24,576 tets, 1/8 of the workload)
+
+
+def _sample_elements(EToV, part: int, nparts: int):
+    """Elements [k0, k1) of an equal split and their face neighbours (faces
+    matched by sorted vertex triples), in increasing global order, and the
+    positions of the owned ones in that list."""
+    K = len(EToV)
+    k0, k1 = part * K // nparts, (part + 1) * K // nparts
+    if nparts == 1:
+        return np.arange(K), np.arange(K)
+    faces = np.array(((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3)))
+    tri = np.sort(np.asarray(EToV)[:, faces], axis=2).reshape(-1, 3)
+    nv = int(np.max(EToV)) + 1
+    key = (tri[:, 0] * nv + tri[:, 1]) * nv + tri[:, 2]
+    own = np.zeros(K, dtype=bool)
+    own[k0:k1] = True
+    mine = np.isin(key, key[np.repeat(own, 4)])
+    ks = np.unique(np.nonzero(mine)[0] // 4)
+    return ks, np.nonzero((ks >= k0) & (ks < k1))[0]
+
+
 class OracleSample:
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the
-    same recipe (warped cube, N = 4, heterogeneous c^2) on a 16^3-hex cube
-    (24,576 tets, 1/8 of the workload); one stage = oracle RHS (strong-weak
-    terms + matrix-free weight-adjusted inverse) + LSRK update, single thread."""
+    same recipe (warped cube, N = 4, heterogeneous c^2, the workload's volume
+    rule) on a 16^3-hex cube (24,576 tets, 1/8 of the workload).  One stage =
+    oracle RHS (strong-weak terms + matrix-free weight-adjusted inverse) + LSRK
+    update, one thread.  part/nparts: the process owns an equal share of the
+    elements and evaluates them on the sub-mesh of those elements and their
+    face neighbours in increasing global order (every shared face keeps its
+    owner and its points, so an owned element's stage is the whole mesh's);
+    the neighbours' results are discarded.  nparts = 1: the whole sample."""
 
-    def __init__(self):
-        os.environ.setdefault("OMP_NUM_THREADS", "1")
-        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-        try:
-            from threadpoolctl import threadpool_limits
-            self._limit = threadpool_limits(1)
-        except Exception:
-            self._limit = None
+    def __init__(self, part: int = 0, nparts: int = 1):
+        self._limit = _limit_blas_threads()
         from oracle import wadg as OW
         from oracle.discretization import Mesh, RefTet
         from synthetic import warped_cube, c2_heterogeneous, random_fields
         self.OW = OW
-        n, N = 16, WORKLOAD["N"]
-        VXYZ, EToV, geom = warped_cube(n, N, WORKLOAD["warp"])
+        N = WORKLOAD["N"]
+        VXYZ, EToV, geom = warped_cube(SAMPLE_N, N, WORKLOAD["warp"])
+        ks, self.owned = _sample_elements(EToV, part, nparts)
         self.ref = RefTet(N, volume_rule=headline_rule())
-        self.mesh = Mesh(self.ref, VXYZ, EToV, geom)
+        self.mesh = Mesh(self.ref, VXYZ, EToV[ks], geom[ks])
         self.c2 = c2_heterogeneous(self.mesh.xq)
-        self.c = self.ref.to_modal(random_fields((4, self.mesh.K, self.ref.Np), 1))
+        self.c = self.ref.to_modal(random_fields((4, len(EToV), self.ref.Np), 1)[:, ks])
         self.res = np.zeros_like(self.c)
-        self.dof = 4 * self.mesh.K * self.ref.Np
+        self.K_sample = len(EToV)
+        self.dof = 4 * len(self.owned) * self.ref.Np
         self.s = 0
 
     def stage(self) -> float:
@@ -557,21 +696,84 @@ class OracleSample:
         self.s += 1
         return time.perf_counter() - t0
 
-    def describe(self, stages, seconds):
-        return (f"a sample of the workload: warped cube 16^3 x 6 = {self.mesh.K} tets, N={self.ref.N}, "
+    def describe(self, stages, seconds, cores=1):
+        return (f"a sample of the workload: warped cube {SAMPLE_N}^3 x 6 = {self.K_sample} tets, N={self.ref.N}, "
                 f"{self.ref.Nq}-point volume rule, heterogeneous c^2, FP64, {stages} stages in {seconds:.1f} s "
-                "(1 thread; DOF*stage/s over the sample's DOF)")
+                f"({cores} {'process' if cores == 1 else 'processes'} of one thread each; "
+                "DOF*stage/s over the sample's DOF)")
+
+
+def _oracle_part(part, nparts, nstages, barrier, queue):
+    """One process of the all-core oracle run: build its part (not timed),
+    one warm-up stage, then nstages stages between wall-clock stamps taken
+    after every process has reached the barrier."""
+    try:
+        o = OracleSample(part, nparts)
+        o.stage()
+        barrier.wait(timeout=300)
+        t0 = time.time()
+        for _ in range(nstages):
+            o.stage()
+        queue.put((part, t0, time.time(), o.dof, o.describe(nstages, 0.0, nparts), None))
+    except Exception as e:  # reported to the parent, which raises
+        queue.put((part, 0.0, 0.0, 0, "", repr(e)))
+
+
+def oracle_all_cores(nstages: int, cores: int | None = None):
+    """The oracle on `cores` host cores (default: every core this process may
+    run on), element-parallel over spawned processes: returns (DOF*stage/s
+    over the sample's DOF, wall seconds of the timed stages, cores, text)."""
+    import multiprocessing as mp
+    cores = cores or len(os.sched_getaffinity(0))
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(cores), ctx.Queue()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+    procs = [ctx.Process(target=_oracle_part, args=(p, cores, nstages, barrier, queue)) for p in range(cores)]
+    for pr in procs:
+        pr.start()
+    import queue as _q
+    out = []
+    try:
+        while len(out) < cores:
+            try:
+                out.append(queue.get(timeout=5))
+            except _q.Empty:
+                if not any(pr.is_alive() for pr in procs):
+                    raise RuntimeError("oracle processes exited without reporting")
+    finally:
+        for pr in procs:
+            pr.join(timeout=60)
+            if pr.is_alive():
+                pr.kill()
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    errs = [e for *_, e in out if e]
+    if errs:
+        raise RuntimeError(f"oracle process failed: {errs[0]}")
+    wall = max(o[2] for o in out) - min(o[1] for o in out)
+    dof = sum(o[3] for o in out)
+    text = out[0][4].replace(" in 0.0 s", f" in {wall:.1f} s")
+    return dof * nstages / wall, wall, cores, text
 
 
 def cpu_baseline(budget_s: float = 20.0):
+    """The oracle on every host core (element-parallel processes) and on one
+    core, on the 16^3 sample; the line's value is the all-core one."""
     o = OracleSample()
     o.stage()  # warm-up
     stages, t = 0, 0.0
     while t < budget_s and stages < 25:
         t += o.stage()
         stages += 1
-    return {"value": o.dof * stages / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": o.describe(stages, t)}
+    one = {"value": o.dof * stages / t, "cores": 1, "sample": o.describe(stages, t)}
+    del o
+    # about as much work per process as the single-core run did in total
+    v, wall, cores, text = oracle_all_cores(max(5, stages))
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text, "single_core": one}
 
 
 def max_over_ranks(ms: float, ws: int) -> float:
@@ -599,20 +801,22 @@ def dist_env():
 
 
 def run_reference(args):
-    """Reference arm: the oracle on the host cores, one stage per step."""
+    """Reference arm: the oracle on every host core (element-parallel
+    processes) on the 16^3 sample of the workload; one step = one LSRK step
+    (5 stages) of the sample."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    o = OracleSample()
-    for _ in range(args.warmup):
-        o.stage()
-    t = sum(o.stage() for _ in range(args.steps))
-    v = o.dof * args.steps / t
+    v, wall, cores, text = oracle_all_cores(5 * (args.warmup + args.steps))
+    steps = args.warmup + args.steps
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / steps,
             "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic", "vs_baseline": None,
             "config": headline_config(ws),
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": o.describe(args.steps, t), "value": v},
+            "reference_sample": (f"timed on the {SAMPLE_N}^3 x 6 = {6 * SAMPLE_N ** 3}-tet sample of the workload "
+                                 "(value normalised by the sample's DOF); ms_per_step is one LSRK step (5 stages) "
+                                 "of the sample on all host cores; the warm-up steps are timed with the others"),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": text, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -632,6 +836,8 @@ def main():
                     help="run only the formulation comparison on the headline mesh and print its JSON")
     ap.add_argument("--batch", action="store_true",
                     help="run only the uneven-batch study (12 meshes, N = 2..6, large and small) and print its JSON")
+    ap.add_argument("--equal-error", action="store_true",
+                    help="run only the equal-L2-error comparison (FP64 vs mixed precision, whole solves) and print it")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
     args = ap.parse_args()
@@ -655,6 +861,10 @@ def main():
     if args.forms:
         if rank == 0:
             print(json.dumps({"formulations": formulations(W, args.steps)}))
+        return
+    if args.equal_error:
+        if rank == 0:
+            print(json.dumps({"equal_error": equal_error(W)}))
         return
     if args.batch:
         if rank == 0:
@@ -753,6 +963,7 @@ def main():
         extras["uneven_batch"] = uneven_batch(W, max(2, args.steps))
         extras["uneven_batch_small"] = uneven_batch(W, max(2, args.steps), small=True)
         extras["accuracy"] = accuracy(W)
+        extras["equal_error"] = equal_error(W)
         extras["formulations"] = formulations(W, args.steps)
         extras["adjoint"] = adjoint_timing(W)
 

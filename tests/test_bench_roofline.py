@@ -61,8 +61,9 @@ def test_job_value_counts_every_rank():
 
 
 def test_both_arms_report_the_same_config():
-    """The reference arm (the oracle on a bounded sample, on the host) prints
-    the native arm's config; the sample is described in its cpu_baseline."""
+    """The reference arm (the oracle on a bounded sample, on every host core)
+    prints the native arm's config; the sample is named beside it and
+    described in its cpu_baseline."""
     import json
     import os
     import subprocess
@@ -79,3 +80,6 @@ def test_both_arms_report_the_same_config():
     assert line["metric"] == b.METRIC and line["unit"] == b.UNIT and line["higher_is_better"] is True
     assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and "sample" in line["cpu_baseline"]["sample"]
+    # every host core, element-parallel; the sample it times is named beside the config
+    assert line["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+    assert "16^3 x 6 = 24576-tet sample" in line["reference_sample"]
