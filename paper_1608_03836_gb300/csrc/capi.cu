@@ -881,7 +881,10 @@ cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p,
     P.err = m->d_err;
     P.vgeo_il = m->d_vgeo_il;
     P.fgeo_il = m->d_fgeo_il;
-    P.bulk_q = (p.ncols * m->ref.Np) % 4 == 0 && ((uintptr_t)p.Qin & 15) == 0;
+    // bulk copies and 16-byte accesses of the field tiles: every field range
+    // of a tile starts 16-byte aligned in every field array the stage touches
+    auto a16 = [](const void* q) { return ((uintptr_t)q & 15) == 0; };
+    P.bulk_q = (p.ncols * m->ref.Np) % 4 == 0 && a16(p.Qin) && a16(p.out) && a16(p.res) && a16(p.Qout);
     return launch_stage_tc(m->N, P, mode, m->tc_fmt, m->num_sms, st);
   }
   return launch_stage<float>(m->N, p, stage_mode(m, mode), st);

@@ -881,7 +881,53 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         if (n0 + j < NP) sTT[(grp * TILE + mrow) * NPS + n0 + j] = __uint_as_float(v[j]);
     }
     sync_check();
-    {
+    if (bulkq) {
+      // 16-byte accesses: the FP32 tile has the global row stride (NPS = NP)
+      // and every field range of the tile starts 16-byte aligned
+      constexpr int F4 = TILE * NP / 4, NIT4 = (4 * F4 + kThreads - 1) / kThreads;
+      const int nval4 = ncol_t * NP / 4;
+      const float4* sT4 = reinterpret_cast<const float4*>(sTT);
+      if (MODE == kRhs) {
+#pragma unroll 3
+        for (int it = 0; it < NIT4; ++it) {
+          const int i = tid + it * kThreads, f = i / F4, r4 = i - f * F4;
+          if (i < 4 * F4 && r4 < nval4)
+            reinterpret_cast<float4*>(p.out + f * fs + col0 * NP)[r4] = sT4[f * F4 + r4];
+        }
+      } else {
+        // LSRK (Sec. 5.2) as below, EB4 float4 loads of res and Q_in issued
+        // before their stores
+        constexpr int EB4 = 3;
+        const bool rd = p.rk_a != 0.f;
+        for (int i0 = 0; i0 < NIT4; i0 += EB4) {
+          float4 vv[EB4], rs[EB4], qi[EB4];
+          int64_t ix[EB4];
+#pragma unroll
+          for (int e = 0; e < EB4; ++e) {
+            const int i = tid + (i0 + e) * kThreads, f = i / F4, r4 = i - f * F4;
+            const bool ok = i0 + e < NIT4 && i < 4 * F4 && r4 < nval4;
+            ix[e] = ok ? (f * fs + col0 * NP) / 4 + r4 : -1;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            vv[e] = ok ? sT4[f * F4 + r4] : z;
+            rs[e] = ok && rd ? __ldg(reinterpret_cast<const float4*>(p.res) + ix[e]) : z;
+            qi[e] = ok ? __ldg(reinterpret_cast<const float4*>(p.Qin) + ix[e]) : z;
+          }
+#pragma unroll
+          for (int e = 0; e < EB4; ++e) {
+            if (ix[e] < 0) continue;
+            float4 rr;
+            rr.x = rd ? p.rk_a * rs[e].x + p.dt * vv[e].x : p.dt * vv[e].x;
+            rr.y = rd ? p.rk_a * rs[e].y + p.dt * vv[e].y : p.dt * vv[e].y;
+            rr.z = rd ? p.rk_a * rs[e].z + p.dt * vv[e].z : p.dt * vv[e].z;
+            rr.w = rd ? p.rk_a * rs[e].w + p.dt * vv[e].w : p.dt * vv[e].w;
+            reinterpret_cast<float4*>(p.res)[ix[e]] = rr;
+            reinterpret_cast<float4*>(p.Qout)[ix[e]] =
+                make_float4(qi[e].x + p.rk_b * rr.x, qi[e].y + p.rk_b * rr.y, qi[e].z + p.rk_b * rr.z,
+                            qi[e].w + p.rk_b * rr.w);
+          }
+        }
+      }
+    } else {
       const int nval = ncol_t * NP;
       if (MODE == kRhs) {
 #pragma unroll 4
