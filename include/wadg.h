@@ -65,14 +65,16 @@ enum wadg_precision {
     WADG_FP32 = 1,          /* FP32 fields, FP32 arithmetic (CUDA cores)      */
     WADG_FP32_TF32 = 2,     /* FP32 fields; the dense products of the stage on
                                the tensor cores in tf32 (one product, 10-bit
-                               mantissa operands, FP32 accumulation); N <= 4
+                               mantissa operands, FP32 accumulation); N <= 5
+                               (N = 5 on the collapsed 216-point volume rule)
                                and K * shots * Np < 2^31.  About 1e-3 relative
                                on the RHS.  Adjoint and diagnostics as
                                WADG_FP32. */
     WADG_FP32_3XBF16 = 3    /* FP32 fields; the dense products of the stage on
                                the tensor cores with split bf16 operands
                                (hi*hi + hi*lo + lo*hi, FP32 accumulation);
-                               N <= 4 and K * shots * Np < 2^31.  Adjoint
+                               N <= 5 (N = 5 on the collapsed 216-point
+                               volume rule) and K * shots * Np < 2^31.  Adjoint
                                and diagnostics as WADG_FP32. */
 };
 

@@ -149,6 +149,9 @@ struct TcStageParams {
 };
 cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
 bool pack_tc_ops(int N, const RefOps& o, int fmt, std::vector<uint8_t>& out);
+// N = 5 (stage_tc5.cu), the collapsed 216-point volume rule.
+cudaError_t launch_stage_tc5(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
+bool pack_tc5_ops(const RefOps& o, int fmt, std::vector<uint8_t>& out);
 cudaError_t launch_bounded_wait_selftest(int* err, uint32_t max_iters, cudaStream_t stream);
 
 // Batches of FP32 meshes (batch.cu).

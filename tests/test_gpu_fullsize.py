@@ -126,8 +126,9 @@ def test_c1_fewer_point_rule_sampled(W, precision):
     run_sampled(W, 32, 4, precision, seed=6, rule=fewer_point_rule(4))
 
 
-def test_c2_rhs_sampled(W):
-    run_sampled(W, 24, 5, "fp32", seed=3)
+@pytest.mark.parametrize("precision", ["fp32", "fp32_3xbf16", "fp32_tf32"])
+def test_c2_rhs_sampled(W, precision):
+    run_sampled(W, 24, 5, precision, seed=3)
 
 
 def test_c3_shots_sampled(W):
