@@ -294,6 +294,26 @@ int wadg_step_adjoint(wadg_mesh* mesh, void* lamQ, void* lamR, double dt, const 
  * receiver's column.  weights device [S][R] in the mesh precision. */
 int wadg_receivers_adjoint(wadg_mesh* mesh, const void* weights, void* lamQ, wadg_stream stream);
 
+/* The reverse of one checkpoint segment of nsteps steps in a single call:
+ * when ystore is given, the segment is first recomputed forward from its
+ * checkpoint as by wadg_step_record, recording every step's stage factors;
+ * then, for n = nsteps - 1 .. 0, the receiver adjoint of step n's weights
+ * (as wadg_receivers_adjoint) followed by the reverse of step n (as
+ * wadg_step_adjoint).  The same kernels in the same order as those calls.
+ *   Q, res   device [4][K][S][Np]: the state (Q, res) at t0 (the segment's
+ *            start); advanced to t0 + nsteps dt by the recompute.  Read only
+ *            when ystore is given (the adjoint of the linear steps does not
+ *            depend on the state); may then be NULL.
+ *   weights  device [nsteps][S][R] in the mesh precision, dJ/d(trace) of the
+ *            segment's steps, or NULL (no receiver terms).
+ *   lamQ, lamR  adjoints after the segment, replaced by those before it.
+ *   ystore   device [nsteps][5][K][S][Nq] scratch in the mesh precision, or
+ *            NULL; dc2 device [K][Nq] FP64 accumulator, NULL exactly when
+ *            ystore is NULL. */
+int wadg_segment_adjoint(wadg_mesh* mesh, void* Q, void* res, double t0, double dt, int nsteps,
+                         const void* weights, void* lamQ, void* lamR, void* ystore, double* dc2,
+                         wadg_stream stream);
+
 /* ---- Batches of meshes of uneven size and degree -------------------------
  * Not in the paper, which tunes the number of elements per work-group for
  * each kernel (Sec. 6.1) but steps one mesh at a time.  A batch steps several

@@ -50,6 +50,7 @@ from .api import (  # noqa: E402,F401
     wadg_set_formulation,
     wadg_set_conservation,
     FORMULATIONS,
+    wadg_segment_adjoint,
     wadg_step_adjoint,
     wadg_step_record,
     wadg_version,

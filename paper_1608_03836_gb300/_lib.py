@@ -40,6 +40,8 @@ SIGNATURES = {
     "wadg_step_record": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, c_void_p, c_void_p, c_void_p]),
     "wadg_step_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     "wadg_receivers_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wadg_segment_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_void_p]),
     "wadg_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p)]),
     "wadg_batch_info": (c_int, [c_void_p, P_int64]),
     "wadg_batch_set_grid": (c_int, [c_void_p, c_int]),

@@ -8,9 +8,10 @@ the library's discrete adjoint (wadg_step_adjoint, wadg_receivers_adjoint),
 giving exact gradients of any scalar function of the traces with respect to
 the nodal initial pressure and the c^2 values at the volume quadrature points.
 
-Memory: the forward pass keeps Q every ``checkpoint`` steps; the backward pass
-recomputes each segment forward once, recording the 5 stage factors of every
-step of the segment (5 K S Nq values per step), then reverses it step by step.
+Memory: the forward pass keeps Q every ``checkpoint`` steps; the
+backward pass makes one library call per segment (wadg_segment_adjoint),
+which recomputes the segment forward once, recording the 5 stage factors of
+every step (5 K S Nq values per step), then reverses it step by step.
 """
 from __future__ import annotations
 
@@ -53,13 +54,11 @@ class _ReceiverTraces(torch.autograd.Function):
         for seg in reversed(range(nseg)):
             n0, n1 = seg * cp, min(nsteps, (seg + 1) * cp)
             Q = ctx.checkpoints[seg].clone()
-            R = torch.zeros_like(Q)
+            R = torch.zeros_like(Q)  # a step's first stage (a_1 = 0) does not read res
             ys = torch.empty((n1 - n0, 5, mesh.K, mesh.S, mesh.Nq), dtype=mesh.dtype, device="cuda")
-            for n in range(n0, n1):
-                W.wadg_step_record(mesh, Q, R, t0 + n * dt, dt, ys[n - n0])
-            for n in reversed(range(n0, n1)):
-                W.wadg_receivers_adjoint(mesh, g[n], lamQ)
-                W.wadg_step_adjoint(mesh, lamQ, lamR, dt, ys[n - n0], dc2)
+            # one library call: recompute with recording, then the reverse steps
+            W.wadg_segment_adjoint(mesh, Q, R, t0 + n0 * dt, dt, n1 - n0, g[n0:n1] if mesh.R > 0 else None,
+                                   lamQ, lamR, ys, dc2)
             del ys
         grad_p0 = lamQ[0].clone()
         return grad_p0, dc2, None, None, None, None, None

@@ -298,6 +298,27 @@ def wadg_receivers_adjoint(mesh: MeshHandle, weights, lamQ, stream=None):
            mesh)
 
 
+def wadg_segment_adjoint(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, weights, lamQ, lamR,
+                         ystore=None, dc2=None, stream=None):
+    import torch
+    a = _check_field(mesh, lamQ, "lamQ")
+    b = _check_field(mesh, lamR, "lamR")
+    q = r = None
+    if ystore is not None:
+        q = _check_field(mesh, Q, "Q")
+        r = _check_field(mesh, res, "res")
+        if ystore.dtype != mesh.dtype or ystore.numel() != nsteps * 5 * mesh.K * mesh.S * mesh.Nq \
+                or not ystore.is_contiguous():
+            raise ValueError("ystore must hold nsteps*5*K*S*Nq contiguous values in the mesh precision")
+    if dc2 is not None and (dc2.dtype != torch.float64 or dc2.numel() != mesh.K * mesh.Nq):
+        raise ValueError("dc2 must be a float64 tensor of K*Nq values")
+    if weights is not None and (weights.dtype != mesh.dtype or weights.numel() != nsteps * mesh.S * mesh.R
+                                or not weights.is_contiguous()):
+        raise ValueError("weights must be a contiguous nsteps*S*R tensor in the mesh precision")
+    _check(load().wadg_segment_adjoint(mesh.handle, q, r, float(t0), float(dt), int(nsteps), _ptr(weights), a, b,
+                                       _ptr(ystore), _ptr(dc2), _stream(stream)), "wadg_segment_adjoint", mesh)
+
+
 class BatchHandle:
     """Owns a wadg_batch*; keeps its meshes alive."""
 

@@ -1276,9 +1276,56 @@ int step_adjoint_t(wadg_mesh* m, void* lamQ, void* lamR, double dt, const void* 
   return WADG_OK;
 }
 
+// The reverse of a checkpoint segment: the forward recompute that records
+// the stage factors (only when they are wanted), then, from the last step to
+// the first, the receiver adjoint of the step's trace weights and the reverse
+// LSRK step.
+template <typename T>
+int segment_adjoint_t(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, const void* weights,
+                      void* lamQ, void* lamR, void* ystore, double* dc2, cudaStream_t st) {
+  const size_t ny5 = (size_t)5 * m->K * m->S * m->ref.Nq;
+  if (ystore)
+    for (int n = 0; n < nsteps; ++n) {
+      const int r = step_record_t<T>(m, Q, res, t0 + n * dt, dt, (T*)ystore + n * ny5, nullptr, st);
+      if (r != WADG_OK) return r;
+    }
+  for (int n = nsteps - 1; n >= 0; --n) {
+    if (weights && m->R > 0) {
+      cudaError_t e = launch_receivers_adjoint<T>(m->S, m->R, m->ref.Np, (const T*)weights + (size_t)n * m->S * m->R,
+                                                  m->d_rec_col, (const T*)m->d_rec_vec, (T*)lamQ, st);
+      if (e != cudaSuccess) return cuda_fail(m, e, "receiver adjoint kernel");
+    }
+    const int r = step_adjoint_t<T>(m, lamQ, lamR, dt, ystore ? (const T*)ystore + n * ny5 : nullptr, dc2, st);
+    if (r != WADG_OK) return r;
+  }
+  return WADG_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int wadg_segment_adjoint(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, const void* weights,
+                         void* lamQ, void* lamR, void* ystore, double* dc2, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
+  if (!collapsed_size(m)) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the (N+1)^3-point volume rule");
+  if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "nsteps/dt/t0");
+  if (!lamQ || !lamR || lamQ == lamR || !aligned16(lamQ) || !aligned16(lamR))
+    return fail(m, WADG_EINVAL, "lambda_Q and lambda_res must be distinct 16-byte aligned device pointers");
+  if ((dc2 != nullptr) != (ystore != nullptr)) return fail(m, WADG_EINVAL, "ystore and dc2 go together");
+  if (ystore && (!Q || !res || Q == res || !aligned16(Q) || !aligned16(res) || Q == lamQ || Q == lamR ||
+                 res == lamQ || res == lamR))
+    return fail(m, WADG_EINVAL, "Q and res must be distinct 16-byte aligned device pointers, apart from the adjoints");
+  if (m->conservative && ystore)
+    return fail(m, WADG_EUNSUPPORTED, "the c^2 gradient is built for the pointwise update weights");
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->precision == WADG_FP64
+             ? segment_adjoint_t<double>(m, Q, res, t0, dt, nsteps, weights, lamQ, lamR, ystore, dc2, s)
+             : segment_adjoint_t<float>(m, Q, res, t0, dt, nsteps, weights, lamQ, lamR, ystore, dc2, s);
+}
 
 int wadg_rhs_adjoint(wadg_mesh* m, const void* lam, void* out, wadg_stream stream) {
   int st = check_ready(m);

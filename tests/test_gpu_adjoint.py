@@ -128,3 +128,43 @@ def test_misfit_gradients_match_finite_differences_on_gpu(W):
         eps = 1e-5
         fd = (misfit(p0.detach(), c2.detach() + eps * dc) - misfit(p0.detach(), c2.detach() - eps * dc)) / (2 * eps)
         assert abs(fd - float((gc * dc).sum())) < 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_segment_adjoint_equals_the_step_by_step_calls(W, precision):
+    """wadg_segment_adjoint (recompute with recording, then receiver adjoints
+    and reverse steps, one call) gives bit for bit what the per-step calls
+    give, with and without the c^2 record; without it the state is not read."""
+    import torch
+    N, ns, dt, t0 = 3, 5, 3e-3, 0.01
+    VXYZ, EToV, geom = make_mesh_inputs(2, N)
+    om = oracle_case(VXYZ, EToV, geom, N)
+    om._inputs = (VXYZ, EToV, geom)
+    m = _gpu_problem(W, precision, None, om, c2_perturbed_samples((om.K, om.ref.Nq)))
+    Q0 = to_torch(random_fields((4, m.K, 1, m.Np), 21), m.dtype)
+    g = to_torch(random_fields((ns, 1, 2), 22), m.dtype)
+    lq0 = to_torch(random_fields((4, m.K, 1, m.Np), 23), m.dtype)
+    lr0 = to_torch(random_fields((4, m.K, 1, m.Np), 24), m.dtype)
+    for record in (True, False):
+        # per-step reference
+        Q, R = Q0.clone(), torch.zeros_like(Q0)
+        ys = torch.empty((ns, 5, m.K, 1, m.Nq), dtype=m.dtype, device="cuda") if record else None
+        lq, lr = lq0.clone(), lr0.clone()
+        dc = torch.zeros((m.K, m.Nq), dtype=torch.float64, device="cuda") if record else None
+        if record:
+            for n in range(ns):
+                W.wadg_step_record(m, Q, R, t0 + n * dt, dt, ys[n])
+        for n in reversed(range(ns)):
+            W.wadg_receivers_adjoint(m, g[n], lq)
+            W.wadg_step_adjoint(m, lq, lr, dt, None if ys is None else ys[n], dc)
+        # one call
+        Q2, R2 = Q0.clone(), torch.zeros_like(Q0)
+        ys2 = torch.empty_like(ys) if record else None
+        lq2, lr2 = lq0.clone(), lr0.clone()
+        dc2 = torch.zeros_like(dc) if record else None
+        W.wadg_segment_adjoint(m, Q2 if record else None, R2 if record else None, t0, dt, ns, g, lq2, lr2, ys2, dc2)
+        torch.cuda.synchronize()
+        assert torch.equal(lq, lq2) and torch.equal(lr, lr2)
+        if record:
+            assert torch.equal(Q, Q2) and torch.equal(R, R2) and torch.equal(ys, ys2)
+            assert float((dc - dc2).abs().max()) <= 1e-14 * float(dc.abs().max())
