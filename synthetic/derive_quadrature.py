@@ -11,6 +11,7 @@ positive weights and interior points.  Prints the orbit table.
 
     python -m synthetic.derive_quadrature 9 0 1 1 2 3 3 3 3
     python -m synthetic.derive_quadrature 7 0 1 2 3 3
+    python -m synthetic.derive_quadrature 5 1 1 2
 """
 from __future__ import annotations
 
@@ -21,7 +22,7 @@ import numpy as np
 
 from .quadrature import orbit
 
-NPAR = {0: 0, 1: 1, 2: 1, 3: 2}
+NPAR = {0: 0, 1: 1, 2: 1, 3: 2, 4: 3}
 
 
 def _unpack(struct, x):
@@ -55,7 +56,7 @@ def derive(degree, struct, seed=0, max_tries=100000):
     from scipy.optimize import least_squares
     E, ex = _moments(degree)
     rng = np.random.default_rng(seed)
-    npts = sum(len(orbit(k, (0.1, 0.2)[:NPAR[k]])) for k in struct)
+    npts = sum(len(orbit(k, (0.1, 0.2, 0.3)[:NPAR[k]])) for k in struct)
     for _ in range(max_tries):
         x, lo, hi = [], [], []
         for kind in struct:
@@ -66,6 +67,9 @@ def derive(degree, struct, seed=0, max_tries=100000):
             elif kind == 3:
                 a = rng.uniform(0.01, 0.45)
                 x += [a, rng.uniform(0.01, max(0.02, 1 - 2 * a - 0.01))]; lo += [1e-9, 1e-9]; hi += [0.5, 1.0]
+            elif kind == 4:
+                b = rng.dirichlet(np.ones(4))
+                x += list(b[:3]); lo += [1e-9] * 3; hi += [1.0] * 3
             x += [rng.uniform(0.3, 1.5) / npts]; lo += [1e-12]; hi += [1.0]
         x = np.clip(x, np.array(lo) + 1e-12, np.array(hi) - 1e-12)
         r = least_squares(_residual, x, args=(struct, E, ex), bounds=(lo, hi), xtol=1e-15, ftol=1e-15, gtol=1e-15,

@@ -17,6 +17,7 @@ unit-measure simplex, summing to 1):
   kind 1: (a, a, a, 1 - 3a)             4 points
   kind 2: (a, a, 1/2 - a, 1/2 - a)      6 points
   kind 3: (a, a, b, 1 - 2a - b)        12 points
+  kind 4: (a, b, c, 1 - a - b - c)     24 points
 """
 from __future__ import annotations
 
@@ -26,6 +27,11 @@ import numpy as np
 
 # degree -> [(kind, params, weight)]
 SYMMETRIC_RULES = {
+    5: [  # 14 points
+        (1, (0.3108859192633007,), 0.11268792571801467),
+        (1, (0.09273525031089097,), 0.0734930431163615),
+        (2, (0.4544962958743488,), 0.04254602077708256),
+    ],
     7: [  # 35 points
         (0, (), 0.09548528946629624),
         (1, (0.315701149778696,), 0.04232958120934625),
@@ -55,6 +61,8 @@ def _representative(kind: int, p) -> tuple:
         return (p[0], p[0], 0.5 - p[0], 0.5 - p[0])
     if kind == 3:
         return (p[0], p[0], p[1], 1.0 - 2.0 * p[0] - p[1])
+    if kind == 4:
+        return (p[0], p[1], p[2], 1.0 - p[0] - p[1] - p[2])
     raise ValueError(kind)
 
 
@@ -81,6 +89,6 @@ def symmetric_rule(degree: int):
 
 
 def fewer_point_rule(N: int):
-    """The symmetric volume rule exact to degree 2N+1 for N = 3 (35 points) and
-    N = 4 (63 points)."""
+    """The symmetric volume rule exact to degree 2N+1 for N = 2 (14 points),
+    N = 3 (35 points) and N = 4 (63 points)."""
     return symmetric_rule(2 * N + 1)
