@@ -454,7 +454,7 @@ def equal_error(W, T=0.25):
     against the analytic solution by the volume rule.  'Equal' means within
     1.05x of the FP64 error.  Meshes (n^3 x 6 tets) and degrees where the
     discretisation error lies well above the FP32 rounding floor; the
-    fewer-point volume rules where tabulated (N = 3, 4), else the (N+1)^3
+    fewer-point volume rules where tabulated (N = 2, 3, 4), else the (N+1)^3
     rule.  'headline' names the case with the most DOF where every
     FP32-field path but TF32 keeps equal error."""
     import torch
@@ -462,7 +462,7 @@ def equal_error(W, T=0.25):
     out = {}
     for n, N in EQUAL_ERROR_CASES:
         VXYZ, EToV, geom = warped_cube(n, N, 0.1)
-        rule = fewer_point_rule(N) if N in (3, 4) else None
+        rule = fewer_point_rule(N) if N in (2, 3, 4) else None
         dt_max = 0.5 * (1.0 / n) / (N + 1) ** 2
         case = {"workload": f"warped cube {n}^3x6 = {len(EToV)} tets, N={N}, "
                             f"{'collapsed' if rule is None else str(len(rule[1])) + '-point'} volume rule, c^2=1, "
