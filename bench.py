@@ -82,9 +82,9 @@ def headline_config(ws: int) -> dict:
 
 def headline_rule():
     """The volume rule of the workload: the fewer-point symmetric rule exact
-    to degree 2N+1 where one is tabulated (N = 3, 4), else the collapsed rule."""
+    to degree 2N+1 where one is tabulated (N = 2, 3, 4), else the collapsed rule."""
     from synthetic import fewer_point_rule
-    return fewer_point_rule(WORKLOAD["N"]) if WORKLOAD["N"] in (3, 4) else None
+    return fewer_point_rule(WORKLOAD["N"]) if WORKLOAD["N"] in (2, 3, 4) else None
 
 
 TC_SOURCES = ("paper_1608_03836_gb300/csrc/stage_tc.cu", "paper_1608_03836_gb300/csrc/tc_ops.cuh",
@@ -849,8 +849,11 @@ def main():
                     help="run only the equal-L2-error comparison (FP64 vs mixed precision, whole solves) and print it")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
+    ap.add_argument("--N", type=int, default=WORKLOAD["N"],
+                    help="polynomial degree (default: the headline workload's 4; 5 runs the N = 5 tensor-core stage)")
     args = ap.parse_args()
     WORKLOAD["n"] = args.n
+    WORKLOAD["N"] = args.N
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
@@ -910,7 +913,7 @@ def main():
     lsrk_ms = ms_per_step / 5
     achieved_gbs = B * K / (lsrk_ms * 1e-3) / 1e9
     achieved_tf = F * K / (lsrk_ms * 1e-3) / 1e12
-    tpe = tc_traffic_per_element()
+    tpe = tc_traffic_per_element() if (WORKLOAD["N"], nq) == (4, 63) else None
     variants = {headline: {"value": value, "ms_per_step": ms_per_step, "stage_ms": lsrk_ms, "rhs_launch_ms": stage_ms,
                            "achieved_tflops": achieved_tf, "achieved_gbs": achieved_gbs,
                            "dtype": "f32 fields, bf16x3 tensor products", "volume_points": nq}}
@@ -987,7 +990,8 @@ def main():
                      "frac": achieved_gbs / hbm,
                      "traffic": None if tpe is None else tpe * K,
                      "peak_kind": peak_kind,
-                     "kernel": f"stage_tc_kernel<4,1,0,{nq}> (one launch = one LSRK stage over all elements)",
+                     "kernel": (f"stage_tc_kernel<{WORKLOAD['N']},1,0,{nq}>" if WORKLOAD["N"] <= 4 else
+                                f"stage_tc5_kernel<1,0,{nq}>") + " (one launch = one LSRK stage over all elements)",
                      "launch_ms": lsrk_ms,
                      "launch_ms_from": "the timed region: ms_per_step / 5 launches (CUDA events on the launching stream)",
                      "algorithmic_bytes_per_element": B,

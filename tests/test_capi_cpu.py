@@ -61,3 +61,22 @@ def test_status_strings(lib):
     import paper_1608_03836_gb300 as W
     assert W.wadg_status_string(0) == "ok"
     assert W.wadg_status_string(-4) == "invalid geometry"
+
+
+def test_mesh_create_rejects_bad_sizes_without_a_gpu(lib):
+    """Host-side checks before any device work: an empty mesh, degrees outside
+    1..6 and a volume rule whose point count no kernel is built for."""
+    import paper_1608_03836_gb300 as W
+    from synthetic import warped_cube
+    VXYZ, EToV, geom = warped_cube(1, 2, 0.1)
+    with pytest.raises(W.WadgError) as e:
+        W.wadg_mesh_create(2, VXYZ, EToV[:0], None)
+    assert e.value.status == -1
+    for N in (0, 7):
+        with pytest.raises(W.WadgError) as e:
+            W.wadg_mesh_create(N, VXYZ, EToV, None)
+        assert e.value.status == -8
+    rst = np.zeros((5, 3)) - 0.5
+    with pytest.raises(W.WadgError) as e:
+        W.wadg_mesh_create(2, VXYZ, EToV, geom, rule=(rst, np.full(5, 4.0 / 15)))
+    assert e.value.status == -8
