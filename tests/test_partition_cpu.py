@@ -59,6 +59,20 @@ def test_local_meshes_and_exchange_plan(part_mod, n, nparts):
             assert np.array_equal(rm.elems[idx], rms[s].elems[rms[s].recv[rm.rank]])
         for s, idx in rm.recv.items():
             assert np.all(part[rm.elems[idx]] == s)
+    # the trace plan: each message's (element, node) pairs agree on both
+    # sides, and name exactly the nodes of the faces shared across the cut
+    N = 3
+    fn = part_mod.face_node_indices(N)
+    assert all(len(f) == (N + 1) * (N + 2) // 2 for f in fn)
+    rmt = [part_mod.build_rank_mesh(EToV, part, r, N=N) for r in range(nparts)]
+    for rm in rmt:
+        for s, (p, nd) in rm.send_nodes.items():
+            q, nq = rmt[s].recv_nodes[rm.rank]
+            assert np.array_equal(rm.elems[p], rmt[s].elems[q]) and np.array_equal(nd, nq)
+            for g in np.unique(rm.elems[p]):
+                want = np.unique(np.concatenate([fn[f] for f in range(4) if E[g, f] >= 0 and part[E[g, f]] == s]))
+                assert np.array_equal(nd[rm.elems[p] == g], want)
+            assert len(p) < len(rm.send[s]) * (N + 1) * (N + 2) * (N + 3) // 6   # fewer values than whole columns
     # the slabs are slabs: owned centroids of rank r lie below those of rank r + 1
     cz = VXYZ[EToV, 2].mean(1)
     for r in range(nparts - 1):
@@ -109,12 +123,15 @@ def _rank_worker(rank, ws, port, nsteps, out):
     VXYZ, EToV, geom = warped_cube(3, N, 0.1)
     ref = RefTet(N)
     part = P.slab_partition(VXYZ, EToV, ws)
-    rm = P.build_rank_mesh(EToV, part, rank)
+    rm = P.build_rank_mesh(EToV, part, rank, N=N)
     sub = Mesh(ref, *P.local_inputs(VXYZ, EToV, geom, rm))
     c2q = c2_heterogeneous(sub.xq)
-    # this rank starts from its owned columns only; the ghosts come from the exchange
-    c0 = random_fields((4, len(EToV), ref.Np), 12)
-    q = torch.full((4, len(rm.elems), 1, ref.Np), float("nan"), dtype=torch.float64)
+    # nodal fields (the library's layout); this rank starts from its owned
+    # columns only; the ghosts' shared-face nodes come from the trace
+    # exchange, their other nodes stay 0 (the trace on a face depends only on
+    # the face's nodes)
+    c0 = ref.to_nodal(random_fields((4, len(EToV), ref.Np), 12))
+    q = torch.zeros((4, len(rm.elems), 1, ref.Np), dtype=torch.float64)
     q[:, rm.owned, 0] = torch.from_numpy(c0[:, rm.elems[rm.owned]])
     res = torch.zeros_like(q)
     dt, exchanges = 1e-3, 0
@@ -122,7 +139,7 @@ def _rank_worker(rank, ws, port, nsteps, out):
         for s in range(5):
             P.halo_exchange(q, rm)
             exchanges += 1
-            r = OW.rhs(sub, q[:, :, 0].numpy(), c2q=c2q)
+            r = ref.to_nodal(OW.rhs(sub, ref.to_modal(q[:, :, 0].numpy()), c2q=c2q))
             o = rm.owned
             res[:, o, 0] = float(OW.LSRK_A[s]) * res[:, o, 0] + dt * torch.from_numpy(r[:, o])
             q[:, o, 0] = q[:, o, 0] + float(OW.LSRK_B[s]) * res[:, o, 0]
@@ -131,9 +148,9 @@ def _rank_worker(rank, ws, port, nsteps, out):
 
 
 def test_two_gloo_ranks_step_like_the_whole_mesh(part_mod):
-    """Two ranks (gloo), two LSRK(5,4) steps with a halo exchange before each
-    stage, each rank starting from its owned columns only (ghosts NaN until
-    the first exchange): the owned columns gathered from both ranks equal the
+    """Two ranks (gloo), two LSRK(5,4) steps with a trace exchange (the
+    shared faces' node values) before each stage, each rank starting from its
+    owned columns only: the owned columns gathered from both ranks equal the
     same steps on the whole mesh to round-off."""
     import torch.multiprocessing as mp
     from oracle import wadg as OW
@@ -151,6 +168,7 @@ def test_two_gloo_ranks_step_like_the_whole_mesh(part_mod):
     r = np.zeros_like(c)
     for k in range(nsteps):
         c, r = OW.lsrk_step(lambda q, t: OW.rhs(full, q, c2q=c2q), c, r, k * 1e-3, 1e-3)
+    c = full.ref.to_nodal(c)
     got = np.full_like(c, np.nan)
     for rank in range(ws):
         ids, q, nex = res[rank]
