@@ -309,22 +309,26 @@ def shots_accuracy(W, S=4, nsteps=120, t_start=0.1):
     return out
 
 
-def uneven_batch(W, steps, small=False):
+def uneven_batch(W, steps, small=False, tensor_cores=False):
     """12 meshes of uneven size and degree (n_i = 4 + round(12 i/11) hexes per
     side, N_i = 2 + (i mod 5)) stepped by one persistent launch per stage
     (autotuned grid), against the same meshes stepped one after another.
     small=True: the same degrees on n_i = 2 + (i mod 4) (48 to 384 tets per
-    mesh), where the per-mesh launches dominate."""
+    mesh), where the per-mesh launches dominate.  tensor_cores=True: the same
+    sizes with N_i = 2 + (i mod 4) (the tensor-core stage is built for N <= 5)
+    in split bf16 on the fewer-point rules where tabulated, one combined
+    launch per degree class and stage against per-mesh tensor-core steps."""
     import torch
-    from synthetic import warped_cube, random_fields
+    from synthetic import warped_cube, random_fields, fewer_point_rule
     ms, Qs, Rs = [], [], []
     dof = 0
     for i in range(12):
         n = 2 + (i % 4) if small else 4 + int(round(12 * i / 11))
-        N = 2 + (i % 5)
+        N = 2 + (i % 4) if tensor_cores else 2 + (i % 5)
         VXYZ, EToV, geom = warped_cube(n, N, 0.1)
-        m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
-        W.wadg_set_operators(m, "fp32", 1, 1.0, 1.0, None)
+        rule = fewer_point_rule(N) if tensor_cores and N in (2, 3, 4) else None
+        m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
+        W.wadg_set_operators(m, "fp32_3xbf16" if tensor_cores else "fp32", 1, 1.0, 1.0, None)
         ms.append(m)
         Qs.append(torch.from_numpy(random_fields((4, m.K, 1, m.Np), 10 + i).astype(np.float32)).cuda() * 1e-3)
         Rs.append(torch.zeros_like(Qs[-1]))
@@ -349,10 +353,16 @@ def uneven_batch(W, steps, small=False):
     torch.cuda.synchronize()
     t_seq = e0.elapsed_time(e1) / steps
     info = W.wadg_batch_info(b)
-    return {"workload": "12 warped cubes, " + ("n = 2..5" if small else "n = 4..16") + ", N = 2..6, FP32",
+    for m in ms:
+        W.wadg_device_status(m)
+    classes = len({(m.N, m.Nq) for m in ms})
+    return {"workload": "12 warped cubes, " + ("n = 2..5" if small else "n = 4..16") +
+                        (", N = 2..5, split bf16 tensor cores (fewer-point rules at N = 2, 3, 4)" if tensor_cores
+                         else ", N = 2..6, FP32"),
             "dof": dof, "items": info["items"], "tile_rule": info["rule"],
             "grid": grid, "value": dof * 5 / (t_batch * 1e-3), "ms_per_step": t_batch,
-            "sequential_ms_per_step": t_seq, "launches_per_step": 5, "sequential_launches_per_step": 60}
+            "sequential_ms_per_step": t_seq, "speedup": t_seq / t_batch,
+            "launches_per_step": 5 * classes if tensor_cores else 5, "sequential_launches_per_step": 60}
 
 
 def adjoint_timing(W, nsteps=300, checkpoint=20):
@@ -881,7 +891,10 @@ def main():
     if args.batch:
         if rank == 0:
             print(json.dumps({"uneven_batch": uneven_batch(W, max(2, args.steps)),
-                              "uneven_batch_small": uneven_batch(W, max(2, args.steps), small=True)}))
+                              "uneven_batch_small": uneven_batch(W, max(2, args.steps), small=True),
+                              "uneven_batch_tc": uneven_batch(W, max(2, args.steps), tensor_cores=True),
+                              "uneven_batch_tc_small": uneven_batch(W, max(2, args.steps), small=True,
+                                                                    tensor_cores=True)}))
         return
 
     def barrier():
@@ -974,6 +987,8 @@ def main():
         extras["batched_shots"] = batched_shots(W, max(2, args.steps // 3))
         extras["uneven_batch"] = uneven_batch(W, max(2, args.steps))
         extras["uneven_batch_small"] = uneven_batch(W, max(2, args.steps), small=True)
+        extras["uneven_batch_tc"] = uneven_batch(W, max(2, args.steps), tensor_cores=True)
+        extras["uneven_batch_tc_small"] = uneven_batch(W, max(2, args.steps), small=True, tensor_cores=True)
         extras["accuracy"] = accuracy(W)
         extras["equal_error"] = equal_error(W)
         extras["formulations"] = formulations(W, args.steps)

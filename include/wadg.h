@@ -317,21 +317,36 @@ int wadg_segment_adjoint(wadg_mesh* mesh, void* Q, void* res, double t0, double 
 /* ---- Batches of meshes of uneven size and degree -------------------------
  * Not in the paper, which tunes the number of elements per work-group for
  * each kernel (Sec. 6.1) but steps one mesh at a time.  A batch steps several
- * WADG_FP32 meshes together: each LSRK stage is ONE persistent launch over a
- * work list of (mesh, tile) items, heaviest degree first, with exactly the
- * arithmetic of wadg_step per mesh (results are bitwise equal).  Point
- * sources and receivers of the meshes are not applied in batch stepping.
+ * meshes together, with exactly the arithmetic of wadg_step per mesh
+ * (results are bitwise equal):
+ *   - WADG_FP32 meshes: each LSRK stage is ONE persistent launch over a work
+ *     list of (mesh, tile) items, heaviest degree first;
+ *   - tensor-core meshes (all WADG_FP32_3XBF16 or all WADG_FP32_TF32, N <= 5):
+ *     the meshes of one class (same degree, volume rule, shots and
+ *     penalties) are stepped as one combined mesh (their elements in
+ *     sequence, the geometry copied into one interleaved table at creation),
+ *     one tensor-core launch per class and stage, so that tiles of small
+ *     meshes share the SMs; each step call copies the members' fields into
+ *     the combined buffers and back (device to device).  The geometry is
+ *     taken at creation: a batch made before a member's operators or
+ *     conservation setting change keeps the old ones.
+ * Point sources and receivers are not applied in batch stepping (a
+ * tensor-core batch refuses meshes that have them: WADG_ESTATE).
  * Q[i], res[i]: device [4][K_i][S_i][Np_i] float buffers of mesh i. */
 typedef struct wadg_batch wadg_batch;
 
-/* meshes: host array of `count` handles, each already set to WADG_FP32 on the
- * same device (WADG_ESTATE otherwise).  The batch keeps the handles (not
- * owned); destroy it before the meshes. */
+/* meshes: host array of `count` handles on the same device, all set to
+ * WADG_FP32 or all to the same tensor-core precision (WADG_ESTATE
+ * otherwise).  The batch keeps the handles (not owned); destroy it before
+ * the meshes.  A mesh whose precision or shots change afterwards makes the
+ * stepping calls return WADG_ESTATE. */
 int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out);
 
 /* info[0..4] = meshes, work items, persistent blocks in use, largest
  * resident grid (occupancy x SMs) for the tile rule in use, the tile rule in
- * use (0, 1 or 2; see wadg_batch_autotune). */
+ * use (0, 1 or 2; see wadg_batch_autotune).  Tensor-core batches: meshes,
+ * 128-column tiles over all classes, SMs, SMs, -1 (one schedule; the grid,
+ * rule and autotuner calls have no effect on them). */
 int wadg_batch_info(const wadg_batch* batch, int64_t info[5]);
 
 /* Number of persistent blocks (clamped to the number of work items). */

@@ -10,9 +10,28 @@
 
 using namespace wadg;
 
+// Tensor-core batches: the meshes of one class (same degree, volume rule,
+// shots and penalties) are stepped as one combined mesh, a library-internal
+// wadg_mesh whose elements are the members' in sequence (connectivity offset,
+// geometry repacked into one interleaved copy) and which borrows the first
+// member's operator tables; every tile of 128 columns of the combined mesh
+// may hold columns of several members.  The stage's arithmetic per column is
+// that of the member's own stage, so results are bitwise equal to stepping
+// the members one by one.
+struct TcClass {
+  wadg_mesh* cm = nullptr;
+  std::vector<int> members;
+  std::vector<int64_t> off;  // first element of each member in the combined mesh
+  float* dQ = nullptr;       // combined fields and residual [4][K][S][Np]
+  float* dR = nullptr;
+};
+
 struct wadg_batch {
   std::vector<wadg_mesh*> meshes;
   int device = 0;
+  bool tc = false;                 // tensor-core batch (classes) instead of the persistent FP32 launch
+  std::vector<TcClass> classes;
+  std::vector<int> prec0, S0;      // the members' precision and shots at creation
   // work lists of the tile rules (see batch.cu)
   int rule = 0;
   int nitems_r[kBatchRules] = {};
@@ -39,6 +58,18 @@ struct wadg_batch {
 };
 
 namespace {
+
+// Runs a body with the batch's device current, restoring the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
 
 int bfail(wadg_batch* b, int status, const std::string& msg) {
   if (b) b->last_error = msg;
@@ -103,9 +134,136 @@ int check_buffers(wadg_batch* b, void* const* Q, void* const* res) {
   for (size_t i = 0; i < b->meshes.size(); ++i) {
     if (!Q[i] || !res[i] || Q[i] == res[i] || ((uintptr_t)Q[i] & 15u) || ((uintptr_t)res[i] & 15u))
       return bfail(b, WADG_EINVAL, "each Q[i], res[i] must be distinct 16-byte aligned device pointers");
-    if (b->meshes[i]->precision != WADG_FP32)
-      return bfail(b, WADG_ESTATE, "every mesh of a batch must be set to WADG_FP32");
+    if (b->meshes[i]->precision != b->prec0[i] || b->meshes[i]->S != b->S0[i])
+      return bfail(b, WADG_ESTATE, "a mesh's precision or shots changed since the batch was created");
   }
+  return WADG_OK;
+}
+
+// Copies between the members' fields and a class's combined fields.
+int tc_copy(wadg_batch* b, const TcClass& c, void* const* Q, void* const* res, bool in, cudaStream_t st) {
+  const wadg_mesh* cm = c.cm;
+  const size_t col = (size_t)cm->S * cm->ref.Np;
+  for (size_t j = 0; j < c.members.size(); ++j) {
+    const int i = c.members[j];
+    const wadg_mesh* m = b->meshes[i];
+    const size_t n = (size_t)m->K * col * sizeof(float);
+    for (int f = 0; f < 4; ++f) {
+      float* gq = c.dQ + ((size_t)f * cm->K + c.off[j]) * col;
+      float* gr = c.dR + ((size_t)f * cm->K + c.off[j]) * col;
+      float* mq = (float*)Q[i] + (size_t)f * m->K * col;
+      float* mr = (float*)res[i] + (size_t)f * m->K * col;
+      cudaError_t e = in ? cudaMemcpyAsync(gq, mq, n, cudaMemcpyDeviceToDevice, st)
+                         : cudaMemcpyAsync(mq, gq, n, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = in ? cudaMemcpyAsync(gr, mr, n, cudaMemcpyDeviceToDevice, st)
+               : cudaMemcpyAsync(mr, gr, n, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return bfail(b, WADG_ECUDA, std::string("batch copy: ") + cudaGetErrorString(e));
+    }
+  }
+  return WADG_OK;
+}
+
+// Tensor-core batch: per class, the members' fields into the combined
+// buffers, nsteps LSRK steps of the combined mesh, and back.
+int enqueue_tc(wadg_batch* b, void* const* Q, void* const* res, double t0, double dt, int nsteps, cudaStream_t st) {
+  for (const TcClass& c : b->classes) {
+    int r = tc_copy(b, c, Q, res, true, st);
+    if (r != WADG_OK) return r;
+    r = wadg_step(c.cm, c.dQ, c.dR, t0, dt, nsteps, nullptr, (wadg_stream)st);
+    if (r != WADG_OK) return bfail(b, r, std::string("combined step: ") + c.cm->last_error);
+    r = tc_copy(b, c, Q, res, false, st);
+    if (r != WADG_OK) return r;
+  }
+  return WADG_OK;
+}
+
+void free_class(TcClass& c) {
+  if (c.cm) {
+    wadg_mesh* m = c.cm;
+    cudaFree(m->d_EToE);
+    cudaFree(m->d_fcode);
+    cudaFree(m->d_vgeo_il);
+    cudaFree(m->d_fgeo_il);
+    cudaFree(m->d_err);
+    cudaFree(m->d_Qtmp);
+    delete m;  // the operator tables are the first member's
+  }
+  cudaFree(c.dQ);
+  cudaFree(c.dR);
+  c = TcClass();
+}
+
+// The combined mesh of a class.  Interleaved geometry: element k's float4
+// (row, group) sits at ((k >> 7) * rows * groups + row * groups + group) * 128
+// + (k & 127) (see launch_geo_pack_il), repacked element by element.
+int build_class(wadg_batch* b, TcClass& c) {
+  const wadg_mesh* m0 = b->meshes[c.members[0]];
+  int64_t K = 0;
+  for (int i : c.members) {
+    c.off.push_back(K);
+    K += b->meshes[i]->K;
+  }
+  const int S = m0->S, Np = m0->ref.Np, Nq = m0->ref.Nq, Nfq = m0->ref.Nfq;
+  if (K * S * Np >= ((int64_t)1 << 31)) return bfail(b, WADG_EUNSUPPORTED, "a tensor-core class needs K * S * Np < 2^31");
+  wadg_mesh* cm = new (std::nothrow) wadg_mesh();
+  if (!cm) return WADG_ENOMEM;
+  c.cm = cm;
+  cm->device = m0->device;
+  cm->N = m0->N;
+  cm->K = K;
+  cm->ref = m0->ref;
+  cm->precision = m0->precision;
+  cm->S = S;
+  cm->tau_p = m0->tau_p;
+  cm->tau_u = m0->tau_u;
+  cm->ops32 = m0->ops32;
+  cm->d_tcops = m0->d_tcops;
+  cm->tc_fmt = m0->tc_fmt;
+  cm->num_sms = m0->num_sms;
+  std::vector<int32_t> E((size_t)K * 4);
+  std::vector<uint8_t> F((size_t)K * 4);
+  const int64_t nq4 = (Nq + 3) / 4, nf4 = (Nfq + 3) / 4, Kt = (K + 127) / 128;
+  std::vector<float> V((size_t)Kt * 128 * 11 * nq4 * 4, 0.f), G((size_t)Kt * 128 * 12 * nf4 * 4, 0.f);
+  for (size_t j = 0; j < c.members.size(); ++j) {
+    const wadg_mesh* m = b->meshes[c.members[j]];
+    const int64_t o = c.off[j], Km = m->K, Ktm = (Km + 127) / 128;
+    for (int64_t k = 0; k < Km * 4; ++k) {
+      const int32_t e = m->EToE[k];
+      E[o * 4 + k] = e >= 0 ? (int32_t)(e + o) : e;
+      F[o * 4 + k] = m->fcode[k];
+    }
+    std::vector<float> v((size_t)Ktm * 128 * 11 * nq4 * 4), g((size_t)Ktm * 128 * 12 * nf4 * 4);
+    BCUDA(b, cudaMemcpy(v.data(), m->d_vgeo_il, v.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    BCUDA(b, cudaMemcpy(g.data(), m->d_fgeo_il, g.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    auto repack = [&](const std::vector<float>& src, std::vector<float>& dst, int64_t rows_groups) {
+      for (int64_t k = 0; k < Km; ++k) {
+        const int64_t kc = k + o;
+        for (int64_t rg = 0; rg < rows_groups; ++rg) {
+          const size_t si = (size_t)(((k >> 7) * rows_groups + rg) * 128 + (k & 127)) * 4;
+          const size_t di = (size_t)(((kc >> 7) * rows_groups + rg) * 128 + (kc & 127)) * 4;
+          for (int x = 0; x < 4; ++x) dst[di + x] = src[si + x];
+        }
+      }
+    };
+    repack(v, V, 11 * nq4);
+    repack(g, G, 12 * nf4);
+  }
+  const size_t qbytes = (size_t)4 * K * S * Np * sizeof(float);
+  BCUDA(b, cudaMalloc((void**)&cm->d_EToE, E.size() * sizeof(int32_t)));
+  BCUDA(b, cudaMalloc((void**)&cm->d_fcode, F.size()));
+  BCUDA(b, cudaMalloc((void**)&cm->d_vgeo_il, V.size() * sizeof(float)));
+  BCUDA(b, cudaMalloc((void**)&cm->d_fgeo_il, G.size() * sizeof(float)));
+  BCUDA(b, cudaMalloc((void**)&cm->d_err, sizeof(int)));
+  BCUDA(b, cudaMalloc(&cm->d_Qtmp, qbytes));
+  BCUDA(b, cudaMalloc((void**)&c.dQ, qbytes));
+  BCUDA(b, cudaMalloc((void**)&c.dR, qbytes));
+  cm->qtmp_bytes = qbytes;
+  BCUDA(b, cudaMemset(cm->d_err, 0, sizeof(int)));
+  BCUDA(b, cudaMemcpy(cm->d_EToE, E.data(), E.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(cm->d_fcode, F.data(), F.size(), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(cm->d_vgeo_il, V.data(), V.size() * sizeof(float), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(cm->d_fgeo_il, G.data(), G.size() * sizeof(float), cudaMemcpyHostToDevice));
   return WADG_OK;
 }
 
@@ -143,6 +301,7 @@ void wadg_batch_destroy(wadg_batch* b) {
     cudaFree(b->d_item_mesh_r[r]);
     cudaFree(b->d_item_blk_r[r]);
   }
+  for (TcClass& c : b->classes) free_class(c);
   cudaFree(b->d_mesh_N);
   cudaFree(b->d_params);
   delete b;
@@ -154,6 +313,49 @@ int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
   wadg_batch* b = new (std::nothrow) wadg_batch();
   if (!b) return WADG_ENOMEM;
   b->meshes.assign(meshes, meshes + count);
+  for (int i = 0; i < count; ++i)
+    if (!meshes[i]) {
+      delete b;
+      return WADG_EINVAL;
+    }
+  for (int i = 0; i < count; ++i) {
+    b->prec0.push_back(meshes[i]->precision);
+    b->S0.push_back(meshes[i]->S);
+  }
+  const int p0 = meshes[0]->precision;
+  if (p0 == WADG_FP32_3XBF16 || p0 == WADG_FP32_TF32) {
+    // tensor-core batch: classes of (degree, rule, shots, penalties)
+    b->tc = true;
+    b->device = meshes[0]->device;
+    for (int i = 0; i < count; ++i) {
+      const wadg_mesh* m = meshes[i];
+      if (m->precision != p0 || m->form != 0 || m->device != b->device || m->nsrc > 0 || m->R > 0) {
+        delete b;
+        return WADG_ESTATE;
+      }
+      TcClass* c = nullptr;
+      for (TcClass& x : b->classes) {
+        const wadg_mesh* a = meshes[x.members[0]];
+        if (a->N == m->N && a->ref.Nq == m->ref.Nq && a->S == m->S && a->tau_p == m->tau_p && a->tau_u == m->tau_u)
+          c = &x;
+      }
+      if (!c) {
+        b->classes.emplace_back();
+        c = &b->classes.back();
+      }
+      c->members.push_back(i);
+    }
+    DeviceGuard g(b->device);
+    for (TcClass& c : b->classes) {
+      const int r = build_class(b, c);
+      if (r != WADG_OK) {
+        wadg_batch_destroy(b);
+        return r;
+      }
+    }
+    *out = b;
+    return WADG_OK;
+  }
   for (int i = 0; i < count; ++i) {
     const int n1 = meshes[i] ? meshes[i]->N + 1 : 0;
     if (!meshes[i] || meshes[i]->precision != WADG_FP32 || meshes[i]->form != 0 ||
@@ -204,6 +406,15 @@ int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
 
 int wadg_batch_info(const wadg_batch* b, int64_t info[5]) {
   if (!b || !info) return WADG_EINVAL;
+  if (b->tc) {
+    int64_t tiles = 0;
+    for (const TcClass& c : b->classes) tiles += (c.cm->K * c.cm->S + 127) / 128;
+    info[0] = (int64_t)b->meshes.size();
+    info[1] = tiles;
+    info[2] = info[3] = b->meshes[0]->num_sms;
+    info[4] = -1;
+    return WADG_OK;
+  }
   info[0] = (int64_t)b->meshes.size();
   info[1] = b->nitems();
   info[2] = b->grid;
@@ -214,6 +425,7 @@ int wadg_batch_info(const wadg_batch* b, int64_t info[5]) {
 
 int wadg_batch_set_rule(wadg_batch* b, int rule) {
   if (!b || rule < 0 || rule >= kBatchRules) return WADG_EINVAL;
+  if (b->tc) return WADG_OK;  // tensor-core batches have one schedule
   b->rule = rule;
   b->grid = std::min(b->grid, std::max(1, b->nitems()));
   return WADG_OK;
@@ -221,6 +433,7 @@ int wadg_batch_set_rule(wadg_batch* b, int rule) {
 
 int wadg_batch_set_grid(wadg_batch* b, int grid) {
   if (!b || grid < 1) return WADG_EINVAL;
+  if (b->tc) return WADG_OK;
   b->grid = std::min(grid, std::max(1, b->nitems()));
   return WADG_OK;
 }
@@ -231,6 +444,10 @@ int wadg_batch_step(wadg_batch* b, void* const* Q, void* const* res, double t0, 
   int st = check_buffers(b, Q, res);
   if (st != WADG_OK) return st;
   if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) return bfail(b, WADG_EINVAL, "nsteps/dt/t0");
+  if (b->tc) {
+    DeviceGuard g(b->device);
+    return enqueue_tc(b, Q, res, t0, dt, nsteps, (cudaStream_t)stream);
+  }
   st = ensure_tables(b, Q, res, dt);
   if (st != WADG_OK) return st;
   return enqueue_steps(b, Q, nsteps, (cudaStream_t)stream);
@@ -242,6 +459,10 @@ int wadg_batch_autotune(wadg_batch* b, void* const* Q, void* const* res, int* gr
   if (!b) return WADG_EINVAL;
   int st = check_buffers(b, Q, res);
   if (st != WADG_OK) return st;
+  if (b->tc) {  // one schedule: a persistent block per SM in every class's launch
+    if (grid_out) *grid_out = b->meshes[0]->num_sms;
+    return WADG_OK;
+  }
   st = ensure_tables(b, Q, res, b->key_dt == b->key_dt ? b->key_dt : 0.0);
   if (st != WADG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -302,8 +523,11 @@ int wadg_batch_solve(wadg_batch* b, void* const* Q, void* const* res, double t0,
   const int nsteps = std::max(1, (int)ratio);
   const double dt = T / nsteps;
   if (nsteps_out) *nsteps_out = nsteps;
-  st = ensure_tables(b, Q, res, dt);
-  if (st != WADG_OK) return st;
+  if (!b->tc) {
+    st = ensure_tables(b, Q, res, dt);
+    if (st != WADG_OK) return st;
+  }
+  DeviceGuard g(b->device);
   if (!b->stream) {
     BCUDA(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
     BCUDA(b, cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
@@ -321,7 +545,7 @@ int wadg_batch_solve(wadg_batch* b, void* const* Q, void* const* res, double t0,
     }
     cudaGraph_t graph = nullptr;
     BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_steps(b, Q, nsteps, b->stream);
+    int rc = b->tc ? enqueue_tc(b, Q, res, t0, dt, nsteps, b->stream) : enqueue_steps(b, Q, nsteps, b->stream);
     cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
     if (rc != WADG_OK) {
       if (graph) cudaGraphDestroy(graph);

@@ -119,3 +119,63 @@ def test_batch_rejects_other_precisions(W):
     with pytest.raises(W.WadgError) as e:
         W.wadg_batch_create([m])
     assert e.value.status == -5
+
+
+@pytest.mark.parametrize("precision", ["fp32_3xbf16", "fp32_tf32"])
+def test_tensor_core_batch_equals_per_mesh_steps(W, precision):
+    """Tensor-core batches: meshes of N = 2..5 (two of N = 4 on the collapsed
+    rule share a class, one on the 63-point rule and one with two shots are
+    classes of their own) stepped as combined meshes, bitwise equal to
+    per-mesh wadg_step, stepped and as a captured solve replayed twice; the
+    combined class also matches the oracle through the per-mesh equality."""
+    import torch
+    from synthetic import fewer_point_rule
+    spec = [(2, 2, 1, None), (3, 4, 1, None), (2, 4, 1, None), (2, 4, 1, 4), (1, 5, 1, None), (2, 3, 2, None),
+            (4, 4, 1, None)]
+    ms = []
+    for n, N, S, rule_N in spec:
+        VXYZ, EToV, geom = make_mesh_inputs(n, N)
+        rule = fewer_point_rule(rule_N) if rule_N else None
+        ms.append(library_mesh(VXYZ, EToV, geom, N, precision, shots=S, c2="heterogeneous", rule=rule))
+    Q0 = [to_torch(random_Q(m.K, m.S, m.Np, 90 + i), torch.float32) for i, m in enumerate(ms)]
+    dt, ns = 1e-3, 3
+    ref = []
+    for m, q in zip(ms, Q0):
+        Q, R = q.clone(), torch.zeros_like(q)
+        W.wadg_step(m, Q, R, 0.0, dt, ns)
+        ref.append((Q, R))
+    b = W.wadg_batch_create(ms)
+    info = W.wadg_batch_info(b)
+    assert info["meshes"] == len(ms) and info["rule"] == -1
+    classes = {}
+    for m in ms:
+        classes[(m.N, m.Nq, m.S)] = classes.get((m.N, m.Nq, m.S), 0) + m.K * m.S
+    assert len(classes) == 5 and info["items"] == sum((c + 127) // 128 for c in classes.values())
+    Qs = [q.clone() for q in Q0]
+    Rs = [torch.zeros_like(q) for q in Q0]
+    W.wadg_batch_step(b, Qs, Rs, 0.0, dt, ns)
+    torch.cuda.synchronize()
+    for m in ms:
+        W.wadg_device_status(m)
+    for (Qr, Rr), Q, R, q0 in zip(ref, Qs, Rs, Q0):
+        assert torch.equal(Qr, Q) and torch.equal(Rr, R)
+        assert not torch.equal(Q, q0)
+    for _ in range(2):
+        Qg = [q.clone() for q in Q0]
+        Rg = [torch.zeros_like(q) for q in Q0]
+        n = W.wadg_batch_solve(b, Qg, Rg, 0.0, dt * ns, dt)
+        torch.cuda.synchronize()
+        assert n == ns
+        for (Qr, Rr), Q, R in zip(ref, Qg, Rg):
+            assert torch.equal(Qr, Q) and torch.equal(Rr, R)
+    W.wadg_batch_destroy(b)
+
+
+def test_tensor_core_batch_refuses_mixed_precisions(W):
+    VXYZ, EToV, geom = make_mesh_inputs(1, 2)
+    a = library_mesh(VXYZ, EToV, geom, 2, "fp32_3xbf16")
+    c = library_mesh(VXYZ, EToV, geom, 2, "fp32")
+    for pair in ([a, c], [c, a]):
+        with pytest.raises(W.WadgError) as e:
+            W.wadg_batch_create(pair)
+        assert e.value.status == -5
