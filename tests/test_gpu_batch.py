@@ -126,8 +126,8 @@ def test_tensor_core_batch_equals_per_mesh_steps(W, precision):
     """Tensor-core batches: meshes of N = 2..5 (two of N = 4 on the collapsed
     rule share a class, one on the 63-point rule and one with two shots are
     classes of their own) stepped as combined meshes, bitwise equal to
-    per-mesh wadg_step, stepped and as a captured solve replayed twice; the
-    combined class also matches the oracle through the per-mesh equality."""
+    per-mesh wadg_step, stepped and as a captured solve replayed twice; every
+    member against the oracle's steps of that mesh alone."""
     import torch
     from synthetic import fewer_point_rule
     spec = [(2, 2, 1, None), (3, 4, 1, None), (2, 4, 1, None), (2, 4, 1, 4), (1, 5, 1, None), (2, 3, 2, None),
@@ -160,6 +160,20 @@ def test_tensor_core_batch_equals_per_mesh_steps(W, precision):
     for (Qr, Rr), Q, R, q0 in zip(ref, Qs, Rs, Q0):
         assert torch.equal(Qr, Q) and torch.equal(Rr, R)
         assert not torch.equal(Q, q0)
+    # each member against the FP64 oracle's steps of that mesh alone
+    from oracle import wadg as OW
+    for (n, N, S, rule_N), m, q0, Q in zip(spec, ms, Q0, Qs):
+        VXYZ, EToV, geom = make_mesh_inputs(n, N)
+        om = oracle_case(VXYZ, EToV, geom, N, rule=fewer_point_rule(rule_N) if rule_N else None)
+        c2o = oracle_c2(om, "heterogeneous")
+        q0n, got = q0.double().cpu().numpy(), Q.double().cpu().numpy()
+        for s in range(S):
+            c = om.ref.to_modal(q0n[:, :, s])
+            res = np.zeros_like(c)
+            for k in range(ns):
+                c, res = OW.lsrk_step(lambda q, t: OW.rhs(om, q, c2q=c2o), c, res, k * dt, dt)
+            l2, mx = rel_errors(got[:, :, s], om.ref.to_nodal(c))
+            assert l2 < TOL[precision] and mx < 10 * TOL[precision], (N, s, l2, mx)
     for _ in range(2):
         Qg = [q.clone() for q in Q0]
         Rg = [torch.zeros_like(q) for q in Q0]
