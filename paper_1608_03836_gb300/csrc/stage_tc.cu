@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   constexpr int NP = T::NP, NQ = T::NQ, NFP = T::NFP, NFQ = T::NFQ, KP = T::KP, QC = T::QC, NPS = T::NPS;
   constexpr int TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16, NCH = T::NCH;
   constexpr int NQ4 = (NQ + 3) / 4, NF4 = (NFQ + 3) / 4;  // groups of four points in the interleaved geometry
+  static_assert(NFP16 == 16, "the face gather maps 8 lanes x 2 nodes to the 16 padded face nodes");
   const StageParams<float>& p = P.s;
   const DevOps<float>& ops = p.ops;
 
@@ -385,45 +386,45 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     for (int f = 0; f < 4 && !failed; ++f) {
       const int q0 = 8 * grp;
       // (i) [p], {u}, [u] at the face nodes, owner's node order -> split A
-      // operands.  Sixteen lanes take the face nodes j of one column, so that
-      // the neighbour's values come from a few sectors of its row.
-      {
-        float qp[4][4], qm[4][4];
-        bool bnd[4];
+      // operands.  Eight lanes take the face nodes of one column, two
+      // adjacent nodes each (one packed store per part and combination), so
+      // that the neighbour's values come from a few sectors of its row.
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-          const int r = it * 32 + (tid >> 4), j = tid & 15;
-          const uint32_t cd = (sC4[r] >> (8 * f)) & 0xffu;
-          const int po = (int)(cd % 6), pn = (int)((cd / 6) % 6), fnb = (int)(cd / 36);
-          const uint4 o4 = sNB[r];
-          const uint32_t nbo = f == 0 ? o4.x : f == 1 ? o4.y : f == 2 ? o4.z : o4.w;
-          const int jj = j < NFP ? j : 0;
+      for (int it = 0; it < 2; ++it) {
+        const int r = it * 64 + (tid >> 3), j0 = 2 * (tid & 7);
+        const uint32_t cd = (sC4[r] >> (8 * f)) & 0xffu;
+        const int po = (int)(cd % 6), pn = (int)((cd / 6) % 6), fnb = (int)(cd / 36);
+        const uint4 o4 = sNB[r];
+        const uint32_t nbo = f == 0 ? o4.x : f == 1 ? o4.y : f == 2 ? o4.z : o4.w;
+        const bool bnd = (nbo & 0x80000000u) != 0;
+        float qp[2][4], qm[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int jj = j0 + h < NFP ? j0 + h : 0;
           const int64_t b = (int64_t)(nbo & 0x7fffffffu) + sGX[(fnb * 6 + pn) * NFP + jj];
           const int o = sGX[(f * 6 + po) * NFP + jj];
-          bnd[it] = (nbo & 0x80000000u) != 0;
 #pragma unroll
           for (int fl = 0; fl < 4; ++fl) {
-            qp[it][fl] = __ldg(p.Qin + fl * fs + b);
-            qm[it][fl] = sQS[(fl * TILE + r) * NPS + o];
+            qp[h][fl] = __ldg(p.Qin + fl * fs + b);
+            qm[h][fl] = sQS[(fl * TILE + r) * NPS + o];
           }
         }
+        float cv[7][2];
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-          const int r = it * 32 + (tid >> 4), j = tid & 15;
-          const bool on = j < NFP;
+        for (int h = 0; h < 2; ++h) {
+          const bool on = j0 + h < NFP;
           // Dirichlet ghost state on the boundary (Sec. 4.1): p+ = -p-, u+ = u-
-          const float pp = bnd[it] ? -qm[it][0] : qp[it][0];
-          float cv[7];
-          cv[0] = on ? pp - qm[it][0] : 0.f;
+          const float pp = bnd ? -qm[h][0] : qp[h][0];
+          cv[0][h] = on ? pp - qm[h][0] : 0.f;
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            const float up = bnd[it] ? qm[it][1 + i] : qp[it][1 + i];
-            cv[1 + i] = on ? 0.5f * (up + qm[it][1 + i]) : 0.f;
-            cv[4 + i] = on ? up - qm[it][1 + i] : 0.f;
+            const float up = bnd ? qm[h][1 + i] : qp[h][1 + i];
+            cv[1 + i][h] = on ? 0.5f * (up + qm[h][1 + i]) : 0.f;
+            cv[4 + i][h] = on ? up - qm[h][1 + i] : 0.f;
           }
-#pragma unroll
-          for (int c = 0; c < 7; ++c) OF::st1(sFA + (2 * c) * T::A_FN, T::A_FN, r, j, NFP16, cv[c]);
         }
+#pragma unroll
+        for (int c = 0; c < 7; ++c) OF::st2(sFA + (2 * c) * T::A_FN, T::A_FN, r, j0, NFP16, cv[c][0], cv[c][1]);
       }
       sync_check();
       if (failed) break;

@@ -121,6 +121,15 @@ struct OpFmt<0> {
     *reinterpret_cast<__nv_bfloat16*>(base + o) = h;
     *reinterpret_cast<__nv_bfloat16*>(base + part + o) = l;
   }
+  // values at k0, k0 + 1 (k0 even): one 4-byte store per part
+  __device__ static void st2(uint8_t* base, int part, int row, int k0, int K, float x0, float x1) {
+    const uint32_t o = tc::kmajor_offset(row, k0, K);
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    *reinterpret_cast<__nv_bfloat162*>(base + o) = hb;
+    *reinterpret_cast<__nv_bfloat162*>(base + part + o) = lb;
+  }
   template <int KE>
   __device__ static void chain(const Mma3& g) {
     mma3_chain<KE / 16>(g);
@@ -143,6 +152,10 @@ struct OpFmt<1> {
   }
   __device__ static void st1(uint8_t* base, int, int row, int k, int K, float x) {
     *reinterpret_cast<uint32_t*>(base + tc::kmajor_offset4(row, k, K)) = tc::to_tf32(x);
+  }
+  // values at k0, k0 + 1 (k0 even): one 8-byte store
+  __device__ static void st2(uint8_t* base, int, int row, int k0, int K, float x0, float x1) {
+    *reinterpret_cast<uint2*>(base + tc::kmajor_offset4(row, k0, K)) = make_uint2(tc::to_tf32(x0), tc::to_tf32(x1));
   }
   template <int KE>
   __device__ static void chain(const Mma3& g) {
