@@ -21,14 +21,16 @@ def W():
     return lib
 
 
+@pytest.mark.parametrize("N", [3, 5])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_3xbf16", "fp32_tf32"])
-def test_solve_graph_equals_steps(W, precision):
+def test_solve_graph_equals_steps(W, precision, N):
     """The captured graph replays exactly the launches of wadg_step: bitwise
-    equal results, also on a second (replayed) call, with sources/receivers."""
+    equal results, also on a second (replayed) call, with sources/receivers
+    (N = 5 runs the N = 5 tensor-core stage in the tensor-core precisions)."""
     import torch
     from synthetic import source_positions, receiver_positions
-    VXYZ, EToV, geom = make_mesh_inputs(2, 3)
-    m = library_mesh(VXYZ, EToV, geom, 3, precision, shots=2, c2="heterogeneous")
+    VXYZ, EToV, geom = make_mesh_inputs(2, N)
+    m = library_mesh(VXYZ, EToV, geom, N, precision, shots=2, c2="heterogeneous")
     W.wadg_set_sources(m, source_positions(2), 5.0, 0.05)
     W.wadg_set_receivers(m, receiver_positions(4).reshape(2, 2, 3))
     Q0 = to_torch(random_Q(m.K, 2, m.Np, 4), m.dtype)
