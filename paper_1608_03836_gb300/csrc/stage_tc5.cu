@@ -33,7 +33,7 @@ struct TcDims5 {
   static constexpr int N = 5;
   using D = Dims<5, NQX>;
   static constexpr int NP = D::NP, NQ = D::NQ, NFP = D::NFP, NFQ = D::NFQ;
-  static constexpr int KP = 64, NPS = NP | 1, QC = 16, NCH = (NQ + QC - 1) / QC, TILE = 128;
+  static constexpr int KP = 64, QC = 16, NCH = (NQ + QC - 1) / QC, TILE = 128;
   static constexpr int A_FIELD = TILE * KP * 2, SZ_AQ = 4 * 2 * A_FIELD;  // split field tiles (128 KB)
   static constexpr int A_CH = TILE * QC * 2, SZ_AX = 6 * 2 * A_CH;        // U^a, g_i of a chunk (48 KB)
   static constexpr int B_V = QC * KP * 2, B_P = KP * QC * 2;
@@ -69,7 +69,7 @@ struct TcDims5 {
                 "TMEM plan");
   static_assert(SZ_VA <= SZ_SLOT && SZ_VB <= SZ_SLOT && 2 * SZ_UA <= SZ_SLOT && 2 * SZ_UB <= SZ_SLOT, "slots");
   static_assert(OFF_FB + 3 * 2 * A_FN <= SZ_AQ && 3 * 2 * A_FQ <= SZ_AQ && 4 * NFP16 * TILE * 4 <= SZ_AQ &&
-                    4 * TILE * NPS * 4 <= SZ_AQ && 4 * 2 * A_UCH <= SZ_X && SZ_FOPS <= SZ_X,
+                    4 * TILE * NP * 4 <= SZ_AQ && 4 * 2 * A_UCH <= SZ_X && SZ_FOPS <= SZ_X,
                 "region plan");
   static_assert(SMEM <= 232448, "shared memory");
 };
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
   using OF = OpFmt<FMT>;
   using T = TcDims5<NQX>;
   constexpr int N = 5, NP = T::NP, NQ = T::NQ, NFP = T::NFP, NFQ = T::NFQ, KP = T::KP, QC = T::QC;
-  constexpr int NPS = T::NPS, TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16, NCH = T::NCH;
+  constexpr int TILE = T::TILE, NFP16 = T::NFP16, NFQ16 = T::NFQ16, NCH = T::NCH;
   constexpr int NQ4 = (NQ + 3) / 4, NF4 = (NFQ + 3) / 4;
   const StageParams<float>& p = P.s;
   const DevOps<float>& ops = p.ops;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
   uint8_t* sFA = smem;                                     // face combinations (pass A), then the fluxes
   uint8_t* sFB = smem + T::OFF_FB;                         // face combinations (pass B)
   float* sLS = reinterpret_cast<float*>(smem);             // lifted face values [4][NFP16][128]
-  float* sTT = reinterpret_cast<float*>(smem);             // output tile [4][128][NPS]
+  float* sTT = reinterpret_cast<float*>(smem);             // output tile [4][128][NP], global row stride
   uint8_t* sAX = smem + T::OFF_X;                          // chunk arrays; the face operators during faces
   uint8_t* sFT = smem + T::OFF_X;
   int16_t* sGI = reinterpret_cast<int16_t*>(smem + T::OFF_GI);
@@ -675,26 +675,71 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
     if (tid == 0 && tile + gridDim.x < ntiles) prefetch_volume();  // the slots are free
 
     // ---- epilogue: r -> FP32 tile -> coalesced dQ/dt, or the LSRK update (Sec. 5.2) ----
+    // The tile has the global row stride (NP = 56, a multiple of 8): each
+    // thread writes its row as float4s (two-way bank conflicts at stride 224 B)
 #pragma unroll
-    for (int n0 = 0; n0 < KP; n0 += 8) {
+    for (int n0 = 0; n0 < NP; n0 += 8) {
       uint32_t v[8];
       tc::tmem_ld8_nw(lane_base + T::TB + KP * grp + n0, v);
       tc::wait_ld();
       tc::pin8(v);
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (n0 + j < NP) sTT[(grp * TILE + mrow) * NPS + n0 + j] = __uint_as_float(v[j]);
+      float4* d = reinterpret_cast<float4*>(sTT + (grp * TILE + mrow) * NP + n0);
+      d[0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]), __uint_as_float(v[3]));
+      d[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]), __uint_as_float(v[7]));
     }
     sync_check();
-    {
+    if (aligned) {
+      // 16-byte global accesses: every field range of the tile starts 16-byte aligned
+      constexpr int F4 = TILE * NP / 4, NIT4 = (4 * F4 + kThreads - 1) / kThreads;
+      const int nval4 = ncol_t * NP / 4;
+      const float4* sT4 = reinterpret_cast<const float4*>(sTT);
+      if (MODE == kRhs) {
+#pragma unroll 7
+        for (int it = 0; it < NIT4; ++it) {
+          const int i = tid + it * kThreads, f = i / F4, r4 = i - f * F4;
+          if (i < 4 * F4 && r4 < nval4)
+            reinterpret_cast<float4*>(p.out + f * fs + col0 * NP)[r4] = sT4[f * F4 + r4];
+        }
+      } else {
+        // LSRK: res = a res + dt r, Q_out = Q_in + b res; the loads of EB4
+        // iterations are issued before their stores
+        constexpr int EB4 = 7;
+        const bool rd = p.rk_a != 0.f;
+        for (int i0 = 0; i0 < NIT4; i0 += EB4) {
+          float4 vv[EB4], rs[EB4], qi[EB4];
+          int64_t ix[EB4];
+#pragma unroll
+          for (int e = 0; e < EB4; ++e) {
+            const int i = tid + (i0 + e) * kThreads, f = i / F4, r4 = i - f * F4;
+            const bool ok = i0 + e < NIT4 && i < 4 * F4 && r4 < nval4;
+            ix[e] = ok ? (f * fs + col0 * NP) / 4 + r4 : -1;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            vv[e] = ok ? sT4[f * F4 + r4] : z;
+            rs[e] = ok && rd ? __ldg(reinterpret_cast<const float4*>(p.res) + ix[e]) : z;
+            qi[e] = ok ? __ldg(reinterpret_cast<const float4*>(p.Qin) + ix[e]) : z;
+          }
+#pragma unroll
+          for (int e = 0; e < EB4; ++e) {
+            if (ix[e] < 0) continue;
+            float4 rr;
+            rr.x = rd ? p.rk_a * rs[e].x + p.dt * vv[e].x : p.dt * vv[e].x;
+            rr.y = rd ? p.rk_a * rs[e].y + p.dt * vv[e].y : p.dt * vv[e].y;
+            rr.z = rd ? p.rk_a * rs[e].z + p.dt * vv[e].z : p.dt * vv[e].z;
+            rr.w = rd ? p.rk_a * rs[e].w + p.dt * vv[e].w : p.dt * vv[e].w;
+            reinterpret_cast<float4*>(p.res)[ix[e]] = rr;
+            reinterpret_cast<float4*>(p.Qout)[ix[e]] =
+                make_float4(qi[e].x + p.rk_b * rr.x, qi[e].y + p.rk_b * rr.y, qi[e].z + p.rk_b * rr.z,
+                            qi[e].w + p.rk_b * rr.w);
+          }
+        }
+      }
+    } else {
       const int nval = ncol_t * NP;
       if (MODE == kRhs) {
 #pragma unroll 4
         for (int i = tid; i < 4 * TILE * NP; i += kThreads) {
           const int f = i / (TILE * NP), r = i - f * (TILE * NP);
-          if (r >= nval) continue;
-          const int c = r / NP, n = r - c * NP;
-          p.out[f * fs + col0 * NP + r] = sTT[(f * TILE + c) * NPS + n];
+          if (r < nval) p.out[f * fs + col0 * NP + r] = sTT[i];
         }
       } else {
         constexpr int NIT = (4 * TILE * NP + kThreads - 1) / kThreads, EB = 7;
@@ -707,9 +752,8 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
             const int i = tid + (i0 + e) * kThreads;
             const int f = i / (TILE * NP), r = i - f * (TILE * NP);
             const bool ok = i0 + e < NIT && i < 4 * TILE * NP && r < nval;
-            const int c = r / NP, n = r - c * NP;
             ix[e] = ok ? f * fs + col0 * NP + r : -1;
-            vv[e] = ok ? sTT[(f * TILE + c) * NPS + n] : 0.f;
+            vv[e] = ok ? sTT[i] : 0.f;
             rs[e] = ok && rd ? __ldg(p.res + ix[e]) : 0.f;
             qi[e] = ok ? __ldg(p.Qin + ix[e]) : 0.f;
           }
