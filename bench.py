@@ -82,9 +82,9 @@ def headline_config(ws: int) -> dict:
 
 def headline_rule():
     """The volume rule of the workload: the fewer-point symmetric rule exact
-    to degree 2N+1 where one is tabulated (N = 2, 3, 4), else the collapsed rule."""
+    to degree 2N+1 where one is tabulated (N = 2..5), else the collapsed rule."""
     from synthetic import fewer_point_rule
-    return fewer_point_rule(WORKLOAD["N"]) if WORKLOAD["N"] in (2, 3, 4) else None
+    return fewer_point_rule(WORKLOAD["N"]) if WORKLOAD["N"] in (2, 3, 4, 5) else None
 
 
 TC_SOURCES = ("paper_1608_03836_gb300/csrc/stage_tc.cu", "paper_1608_03836_gb300/csrc/tc_ops.cuh",
@@ -326,7 +326,7 @@ def uneven_batch(W, steps, small=False, tensor_cores=False):
         n = 2 + (i % 4) if small else 4 + int(round(12 * i / 11))
         N = 2 + (i % 4) if tensor_cores else 2 + (i % 5)
         VXYZ, EToV, geom = warped_cube(n, N, 0.1)
-        rule = fewer_point_rule(N) if tensor_cores and N in (2, 3, 4) else None
+        rule = fewer_point_rule(N) if tensor_cores and N in (2, 3, 4, 5) else None
         m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
         W.wadg_set_operators(m, "fp32_3xbf16" if tensor_cores else "fp32", 1, 1.0, 1.0, None)
         ms.append(m)
@@ -472,7 +472,7 @@ def equal_error(W, T=0.25):
     out = {}
     for n, N in EQUAL_ERROR_CASES:
         VXYZ, EToV, geom = warped_cube(n, N, 0.1)
-        rule = fewer_point_rule(N) if N in (2, 3, 4) else None
+        rule = fewer_point_rule(N) if N in (2, 3, 4, 5) else None
         dt_max = 0.5 * (1.0 / n) / (N + 1) ** 2
         case = {"workload": f"warped cube {n}^3x6 = {len(EToV)} tets, N={N}, "
                             f"{'collapsed' if rule is None else str(len(rule[1])) + '-point'} volume rule, c^2=1, "
@@ -569,57 +569,62 @@ def formulations(W, steps):
 
 def c2_study(W):
     """The precision configuration: warped cube 24^3 x 6 = 82,944 tets, N = 5,
-    c^2 = 1, standing wave to T = 0.5.  For every precision (FP64, FP32 on the
-    CUDA cores, FP32 fields with split-bf16 or tf32 tensor-core products), the
-    L2 error of p against the analytic solution, the relative L2 difference of
-    the nodal p from the FP64 solution (the FP64 path equals the oracle's
-    discrete solution to 1e-11) and the throughput of the whole solve (one
-    captured graph; the FP32-field paths are timed on a second solve after an
-    untimed first one, the FP64 solve, about three minutes, once)."""
+    c^2 = 1, standing wave to T = 0.5, on the 96-point symmetric volume rule
+    and on the collapsed 216-point rule.  For every precision (FP64, FP32 on
+    the CUDA cores, FP32 fields with split-bf16 or tf32 tensor-core products),
+    the L2 error of p against the analytic solution, the relative L2
+    difference of the nodal p from the FP64 solution on the same rule (the
+    FP64 path equals the oracle's discrete solution to 1e-11) and the
+    throughput of the whole solve (one captured graph; the FP32-field paths
+    are timed on a second solve after an untimed first one, each FP64 solve,
+    one to three minutes, once)."""
     import torch
-    from synthetic import warped_cube, standing_wave
+    from synthetic import warped_cube, standing_wave, fewer_point_rule
     n, N, T = 24, 5, 0.5
     VXYZ, EToV, geom = warped_cube(n, N, 0.1)
     h = 2.0 / n
     dt_max = 0.5 * (h / 2) / (N + 1) ** 2
-    out = {"workload": f"warped cube {n}^3x6 = {len(EToV)} tets, N={N}, collapsed 216-point volume rule, c^2=1, "
+    out = {"workload": f"warped cube {n}^3x6 = {len(EToV)} tets, N={N}, c^2=1, "
                        f"standing wave to T={T}, dt_max={dt_max:.3e}"}
-    ref = None
-    for prec in ("fp64", "fp32", "fp32_3xbf16", "fp32_tf32"):
-        m = W.wadg_mesh_create(N, VXYZ, EToV, geom)
-        W.wadg_set_operators(m, prec, 1, 1.0, 1.0, None)
-        xq = W.wadg_volume_points(m)
-        f0 = torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda()
-        Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
-        R = torch.zeros_like(Q)
-        if prec != "fp64":
+    for rule_name, rule in (("96-point rule", fewer_point_rule(N)), ("collapsed 216-point rule", None)):
+        rows = {}
+        ref = None
+        for prec in ("fp64", "fp32", "fp32_3xbf16", "fp32_tf32"):
+            m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
+            W.wadg_set_operators(m, prec, 1, 1.0, 1.0, None)
+            xq = W.wadg_volume_points(m)
+            f0 = torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda()
+            Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
+            R = torch.zeros_like(Q)
+            if prec != "fp64":
+                W.wadg_project(m, f0, Q)
+                W.wadg_solve(m, Q, R, 0.0, T, dt_max)
+                R.zero_()
             W.wadg_project(m, f0, Q)
-            W.wadg_solve(m, Q, R, 0.0, T, dt_max)
-            R.zero_()
-        W.wadg_project(m, f0, Q)
-        stream = torch.cuda.current_stream()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        nsteps = W.wadg_solve(m, Q, R, 0.0, T, dt_max)
-        b.record(stream)
-        torch.cuda.synchronize()
-        W.wadg_device_status(m)
-        ms = a.elapsed_time(b)
-        err = W.wadg_l2_error(m, Q, torch.from_numpy(standing_wave(xq, T)[:, :, None, :]).cuda(), 1)
-        dof = 4 * m.K * m.Np
-        row = {"l2_error_p": err, "nsteps": nsteps, "solve_ms": ms,
-               "dof_stage_per_s": dof * 5 * nsteps / (ms * 1e-3)}
-        p = Q[0].double().cpu().numpy()
-        if ref is None:
-            ref = p
-        else:
-            row["rel_l2_diff_vs_fp64_nodal"] = float(np.linalg.norm(p - ref) / np.linalg.norm(ref))
-            row["ratio_to_fp64"] = err / out["fp64"]["l2_error_p"]
-            row["speedup_over_fp64"] = row["dof_stage_per_s"] / out["fp64"]["dof_stage_per_s"]
-        out[prec] = row
-        del Q, R, f0, m
-        torch.cuda.empty_cache()
+            stream = torch.cuda.current_stream()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            nsteps = W.wadg_solve(m, Q, R, 0.0, T, dt_max)
+            b.record(stream)
+            torch.cuda.synchronize()
+            W.wadg_device_status(m)
+            ms = a.elapsed_time(b)
+            err = W.wadg_l2_error(m, Q, torch.from_numpy(standing_wave(xq, T)[:, :, None, :]).cuda(), 1)
+            dof = 4 * m.K * m.Np
+            row = {"l2_error_p": err, "nsteps": nsteps, "solve_ms": ms, "volume_points": m.Nq,
+                   "dof_stage_per_s": dof * 5 * nsteps / (ms * 1e-3)}
+            p = Q[0].double().cpu().numpy()
+            if ref is None:
+                ref = p
+            else:
+                row["rel_l2_diff_vs_fp64_nodal"] = float(np.linalg.norm(p - ref) / np.linalg.norm(ref))
+                row["ratio_to_fp64"] = err / rows["fp64"]["l2_error_p"]
+                row["speedup_over_fp64"] = row["dof_stage_per_s"] / rows["fp64"]["dof_stage_per_s"]
+            rows[prec] = row
+            del Q, R, f0, m
+            torch.cuda.empty_cache()
+        out[rule_name] = rows
     return out
 
 

@@ -66,15 +66,17 @@ enum wadg_precision {
     WADG_FP32_TF32 = 2,     /* FP32 fields; the dense products of the stage on
                                the tensor cores in tf32 (one product, 10-bit
                                mantissa operands, FP32 accumulation); N <= 5
-                               (N = 5 on the collapsed 216-point volume rule)
-                               and K * shots * Np < 2^31.  About 1e-3 relative
+                               (N = 5 on the collapsed 216-point or the
+                               96-point volume rule) and
+                               K * shots * Np < 2^31.  About 1e-3 relative
                                on the RHS.  Adjoint and diagnostics as
                                WADG_FP32. */
     WADG_FP32_3XBF16 = 3    /* FP32 fields; the dense products of the stage on
                                the tensor cores with split bf16 operands
                                (hi*hi + hi*lo + lo*hi, FP32 accumulation);
-                               N <= 5 (N = 5 on the collapsed 216-point
-                               volume rule) and K * shots * Np < 2^31.  Adjoint
+                               N <= 5 (N = 5 on the collapsed 216-point or
+                               the 96-point volume rule) and
+                               K * shots * Np < 2^31.  Adjoint
                                and diagnostics as WADG_FP32. */
 };
 
@@ -107,9 +109,10 @@ int wadg_mesh_create(int N, int64_t Nv, const double* VXYZ, int64_t K, const int
  * collapsed one.  It must be exact to degree 2N (checked: P_q V_q = I,
  * WADG_EUNSUPPORTED otherwise) and should be exact to 2N+1 (Sec. 4, Sec. 6.2).
  * The stage kernels are built for nq = (N+1)^3 and for the fewer-point
- * symmetric rules with nq = 35 (N = 3) and 63 (N = 4); other sizes are
- * WADG_EUNSUPPORTED.  With the fewer-point sizes the strong formulations, the
- * adjoint and batches are not available (WADG_EUNSUPPORTED / WADG_ESTATE).
+ * symmetric rules with nq = 14 (N = 2), 35 (N = 3), 63 (N = 4) and 96
+ * (N = 5); other sizes are WADG_EUNSUPPORTED.  With the fewer-point sizes
+ * the strong formulations, the adjoint and WADG_FP32 batches are not
+ * available (WADG_EUNSUPPORTED / WADG_ESTATE); tensor-core batches are.
  * rule = NULL is wadg_mesh_create. */
 int wadg_mesh_create_rule(int N, int64_t Nv, const double* VXYZ, int64_t K, const int64_t* EToV,
                           const double* geom_xyz, int nq, const double* rule, wadg_mesh** out);

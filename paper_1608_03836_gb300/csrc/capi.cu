@@ -739,8 +739,9 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
     return fail(m, WADG_EUNSUPPORTED, "precision %d is not built", precision);
   const bool tensor = precision == WADG_FP32_3XBF16 || precision == WADG_FP32_TF32;
   if (tensor && m->N > 5) return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 5");
-  if (tensor && m->N == 5 && m->ref.Nq != 216)
-    return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage at N = 5 is built for the 216-point collapsed rule");
+  if (tensor && m->N == 5 && m->ref.Nq != 216 && m->ref.Nq != fewer_point_nq(5))
+    return fail(m, WADG_EUNSUPPORTED,
+                "the tensor-core stage at N = 5 is built for the 216-point collapsed rule and the fewer-point rule");
   if (tensor && m->form != 0)
     return fail(m, WADG_EUNSUPPORTED, "the tensor-core stage is built for the strong-weak formulation");
   if (shots < 1 || shots > (1 << 20)) return fail(m, WADG_EINVAL, "shots=%d", shots);

@@ -798,22 +798,35 @@ cudaError_t launch5(const TcStageParams& P, int grid, cudaStream_t stream) {
 
 }  // namespace
 
-// N = 5 on the collapsed (N+1)^3 = 216-point volume rule.
-cudaError_t launch_stage_tc5(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream) {
-  using T = TcDims5<>;
-  if (P.s.nq != T::NQ) return cudaErrorInvalidValue;
+template <int NQX>
+cudaError_t launch_stage_tc5_q(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream) {
+  using T = TcDims5<NQX>;
   const int64_t ntiles = (P.s.ncols + T::TILE - 1) / T::TILE;
   if (ntiles == 0) return cudaSuccess;
   const int g = (int)(ntiles < grid ? ntiles : grid);
-  if (mode == kRhs) return fmt == 0 ? launch5<kRhs, 0, T::NQ>(P, g, stream) : launch5<kRhs, 1, T::NQ>(P, g, stream);
-  return fmt == 0 ? launch5<kLsrk, 0, T::NQ>(P, g, stream) : launch5<kLsrk, 1, T::NQ>(P, g, stream);
+  if (mode == kRhs) return fmt == 0 ? launch5<kRhs, 0, NQX>(P, g, stream) : launch5<kRhs, 1, NQX>(P, g, stream);
+  return fmt == 0 ? launch5<kLsrk, 0, NQX>(P, g, stream) : launch5<kLsrk, 1, NQX>(P, g, stream);
+}
+
+// N = 5 on the collapsed (N+1)^3 = 216-point volume rule or on the
+// fewer-point symmetric rule exact to degree 11.
+cudaError_t launch_stage_tc5(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream) {
+  if (P.s.nq == 216) return launch_stage_tc5_q<216>(P, mode, fmt, grid, stream);
+  if (P.s.nq == fewer_point_nq(5)) return launch_stage_tc5_q<fewer_point_nq(5)>(P, mode, fmt, grid, stream);
+  return cudaErrorInvalidValue;
 }
 
 bool pack_tc5_ops(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
-  using T = TcDims5<>;
-  if (o.Nq != T::NQ || !face_nodes_match<5>(o)) return false;
-  pack_dims<T>(o, fmt, out);
-  return true;
+  if (!face_nodes_match<5>(o)) return false;
+  if (o.Nq == 216) {
+    pack_dims<TcDims5<216>>(o, fmt, out);
+    return true;
+  }
+  if (o.Nq == fewer_point_nq(5)) {
+    pack_dims<TcDims5<fewer_point_nq(5)>>(o, fmt, out);
+    return true;
+  }
+  return false;
 }
 
 }  // namespace wadg

@@ -54,9 +54,11 @@ enum StageMode {
 };
 
 // Points of the fewer-point symmetric volume rules the stage kernels are
-// built for (exact to degree 2N+1): 14 at N = 2, 35 at N = 3, 63 at N = 4;
-// 0: none.
-constexpr int fewer_point_nq(int N) { return N == 2 ? 14 : (N == 3 ? 35 : (N == 4 ? 63 : 0)); }
+// built for (exact to degree 2N+1): 14 at N = 2, 35 at N = 3, 63 at N = 4,
+// 96 at N = 5; 0: none.
+constexpr int fewer_point_nq(int N) {
+  return N == 2 ? 14 : (N == 3 ? 35 : (N == 4 ? 63 : (N == 5 ? 96 : 0)));
+}
 
 // Sizes of the strong-form stage for degree N and formulation FORM (1: the
 // energy-stable rules, 2: the degree 2N+1 rules).  The volume terms walk the

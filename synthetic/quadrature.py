@@ -49,6 +49,21 @@ SYMMETRIC_RULES = {
         (3, (0.031904877425252984, 0.7186038497123036), 0.009405679271801907),
         (3, (0.45903648723540347, 0.0023447430466212007), 0.008103754794817194),
     ],
+    11: [  # 96 points (node elimination, seed 100; two orbits at the 1e-3 coordinate bound)
+        (1, (0.11804884106967635,), 0.016865718825243983),
+        (1, (0.3261574903033582,), 0.01217401352789134),
+        (1, (0.06378982468749753,), 0.00700752014248011),
+        (1, (0.2931439460454494,), 0.022889376166740832),
+        (1, (0.1898897187337074,), 0.0235347681957092),
+        (2, (0.10148308055102657,), 0.024818904562489367),
+        (3, (0.1334760764817837, 0.001), 0.0038388762804312786),
+        (3, (0.013388986005848574, 0.8280685599040966), 0.001794978837598775),
+        (3, (0.21750416078041412, 0.04034730197691247), 0.01859369075436357),
+        (3, (0.4410289816644533, 0.0028897837578749025), 0.0061188001373923785),
+        (2, (0.001,), 0.0012466022509926321),
+        (3, (0.04335010420207233, 0.6323945671172728), 0.012033132370589441),
+        (1, (0.022818137544555552,), 0.0012919077805852474),
+    ],
 }
 
 
@@ -90,5 +105,5 @@ def symmetric_rule(degree: int):
 
 def fewer_point_rule(N: int):
     """The symmetric volume rule exact to degree 2N+1 for N = 2 (14 points),
-    N = 3 (35 points) and N = 4 (63 points)."""
+    N = 3 (35 points), N = 4 (63 points) and N = 5 (96 points)."""
     return symmetric_rule(2 * N + 1)

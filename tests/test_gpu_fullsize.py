@@ -8,7 +8,8 @@ one from each element's neighbourhood:
     strong form and the conservative
     weights in FP32; one LSRK step (tensor cores and CUDA cores) against five
     RHS launches composed on the device;
-  * 24^3 x 6 = 82,944 tets, N = 5, FP32;
+  * 24^3 x 6 = 82,944 tets, N = 5: FP32, split bf16 and TF32 on the collapsed
+    rule, and FP64 and both tensor precisions on the 96-point rule;
   * 16^3 x 6 = 24,576 tets, N = 4, 64 shots as columns, split bf16;
   * 16^3 x 6 tets, N = 3, FP32, c^2 perturbed by 10 % per point.
 """
@@ -129,6 +130,12 @@ def test_c1_fewer_point_rule_sampled(W, precision):
 @pytest.mark.parametrize("precision", ["fp32", "fp32_3xbf16", "fp32_tf32"])
 def test_c2_rhs_sampled(W, precision):
     run_sampled(W, 24, 5, precision, seed=3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_3xbf16", "fp32_tf32"])
+def test_c2_fewer_point_rule_sampled(W, precision):
+    from synthetic import fewer_point_rule
+    run_sampled(W, 24, 5, precision, seed=8, rule=fewer_point_rule(5))
 
 
 def test_c3_shots_sampled(W):

@@ -1,6 +1,6 @@
 """The fewer-point symmetric volume rules (14 points at N = 2, 35 at N = 3,
-63 at N = 4, exact to degree 2N+1) on every stage path against the oracle on
-the same rule."""
+63 at N = 4, 96 at N = 5, exact to degree 2N+1) on every stage path against
+the oracle on the same rule."""
 import numpy as np
 import pytest
 
@@ -20,7 +20,7 @@ def W():
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
-@pytest.mark.parametrize("N,n", [(2, 3), (3, 2), (4, 2), (4, 3)])
+@pytest.mark.parametrize("N,n", [(2, 3), (3, 2), (4, 2), (4, 3), (5, 2)])
 def test_fewer_point_rhs_matches_oracle(W, precision, N, n):
     """Element by element against the oracle on the same rule (curved,
     heterogeneous c^2 at the rule's points)."""

@@ -2,7 +2,8 @@
 accumulator, single-buffered volume operators) against the FP64 oracle:
 more 128-column tiles than resident blocks with a ragged last tile and
 several shots, LSRK steps, point sources with receivers, an element whose
-four faces are all on the boundary; split bf16 and tf32 operands."""
+four faces are all on the boundary; split bf16 and tf32 operands; on the
+collapsed 216-point rule and on the 96-point symmetric rule."""
 import numpy as np
 import pytest
 
@@ -128,4 +129,44 @@ def test_tc5_single_element_all_boundary(W, precision):
     Q = random_Q(1, 1, m.Np, seed=53)
     from oracle import wadg as OW
     l2, mx = rel_errors(_gpu_rhs(W, m, Q)[:, :, 0], OW.rhs_nodal(om, Q[:, :, 0]))
+    assert l2 < TOL[precision] and mx < 10 * TOL[precision], (l2, mx)
+
+
+@pytest.mark.parametrize("precision", TC)
+def test_tc5_fewer_point_rule_matches_oracle(W, precision):
+    """The 96-point symmetric rule (six volume and six update chunks of 16
+    points): 6,000 tets x 2 shots (93.75 tiles, the last ragged) against the
+    oracle on the same rule, heterogeneous c^2; then three LSRK steps with
+    penalties (1, 0.5) on 48 tets."""
+    import torch
+    from oracle import wadg as OW
+    from synthetic import fewer_point_rule
+    N, S = 5, 2
+    rule = fewer_point_rule(N)
+    VXYZ, EToV, geom = make_mesh_inputs(10, N)
+    om = oracle_case(VXYZ, EToV, geom, N, rule=rule)
+    m = library_mesh(VXYZ, EToV, geom, N, precision, shots=S, c2="heterogeneous", rule=rule)
+    assert m.Nq == 96
+    Q = random_Q(m.K, S, m.Np, seed=54)
+    got = _gpu_rhs(W, m, Q)
+    c2q = oracle_c2(om, "heterogeneous")
+    for s in range(S):
+        l2, mx = rel_errors(got[:, :, s], OW.rhs_nodal(om, Q[:, :, s], c2q=c2q))
+        print(f"N=5 96-point rule {precision} shot {s}: rel L2 {l2:.3e}, max {mx:.3e}")
+        assert l2 < TOL[precision] and mx < 10 * TOL[precision], (s, l2, mx)
+    VXYZ, EToV, geom = make_mesh_inputs(2, N)
+    om = oracle_case(VXYZ, EToV, geom, N, rule=rule)
+    m = library_mesh(VXYZ, EToV, geom, N, precision, c2="heterogeneous", tau=(1.0, 0.5), rule=rule)
+    c2o = oracle_c2(om, "heterogeneous")
+    Q0 = random_Q(m.K, 1, m.Np, seed=55)
+    dt, nsteps = 1e-3, 3
+    c = om.ref.to_modal(Q0[:, :, 0].astype(np.float32).astype(np.float64))
+    res = np.zeros_like(c)
+    for k in range(nsteps):
+        c, res = OW.lsrk_step(lambda q, t: OW.rhs(om, q, c2q=c2o, tau_u=0.5), c, res, k * dt, dt)
+    Qt = to_torch(Q0, m.dtype)
+    Rt = torch.zeros_like(Qt)
+    W.wadg_step(m, Qt, Rt, 0.0, dt, nsteps)
+    W.wadg_device_status(m)
+    l2, mx = rel_errors(Qt.double().cpu().numpy()[:, :, 0], om.ref.to_nodal(c))
     assert l2 < TOL[precision] and mx < 10 * TOL[precision], (l2, mx)

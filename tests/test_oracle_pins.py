@@ -749,7 +749,7 @@ def test_rhs_conservative_flag_reaches_the_update():
 # Fewer-point symmetric volume rules (tabulated inputs)
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("N,npts", [(2, 14), (3, 35), (4, 63)])
+@pytest.mark.parametrize("N,npts", [(2, 14), (3, 35), (4, 63), (5, 96)])
 def test_fewer_point_rules_exact_to_2N_plus_1_and_not_beyond(N, npts):
     """Every monomial of degree <= 2N+1 integrates exactly (closed form), some
     of degree 2N+2 do not; positive weights, interior points."""
@@ -771,7 +771,7 @@ def test_fewer_point_rules_exact_to_2N_plus_1_and_not_beyond(N, npts):
     assert worst < 1e-12 and beyond > 1e-9
 
 
-@pytest.mark.parametrize("degree", [5, 7, 9])
+@pytest.mark.parametrize("degree", [5, 7, 9, 11])
 def test_fewer_point_rules_are_symmetric(degree):
     """The point set with its weights is invariant under the 24 vertex
     permutations of the tetrahedron."""
@@ -785,7 +785,7 @@ def test_fewer_point_rules_are_symmetric(degree):
             assert abs(key[tuple(np.round(l[list(perm)], 12))] - wi) < 1e-15
 
 
-@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
 def test_fewer_point_rule_rhs_equals_collapsed_rule_on_affine_elements(N):
     """On affine elements with c^2 = 1 every integrand of the right-hand side
     and of the update is a polynomial of degree <= 2N, which both rules
