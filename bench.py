@@ -357,7 +357,7 @@ def uneven_batch(W, steps, small=False, tensor_cores=False):
         W.wadg_device_status(m)
     classes = len({(m.N, m.Nq) for m in ms})
     return {"workload": "12 warped cubes, " + ("n = 2..5" if small else "n = 4..16") +
-                        (", N = 2..5, split bf16 tensor cores (fewer-point rules at N = 2, 3, 4)" if tensor_cores
+                        (", N = 2..5, split bf16 tensor cores (fewer-point rules at N = 2..5)" if tensor_cores
                          else ", N = 2..6, FP32"),
             "dof": dof, "items": info["items"], "tile_rule": info["rule"],
             "grid": grid, "value": dof * 5 / (t_batch * 1e-3), "ms_per_step": t_batch,
