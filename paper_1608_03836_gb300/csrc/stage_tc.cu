@@ -87,9 +87,10 @@ struct TcDims {
   static constexpr int SZ_GI = (4 * 6 * NP * 2 + 15) / 16 * 16;
   static constexpr int OFF_GX = OFF_GI + SZ_GI;
   static constexpr int SZ_GX = (4 * 6 * NFP * 2 + 15) / 16 * 16;
-  // per tile column: offset of each face's neighbour column (4 x uint32, top bit: boundary), face codes
+  // per tile column: offset of each face's neighbour column (4 x uint32, top bit: boundary), face codes,
+  // the neighbour's row in the tile (4 x uint8, 0xff: outside the tile)
   static constexpr int OFF_NB = OFF_GX + SZ_GX;
-  static constexpr int OFF_BAR = OFF_NB + TILE * 20;
+  static constexpr int OFF_BAR = OFF_NB + TILE * 24;
   static constexpr int SMEM = OFF_BAR + 128;
   // TMEM columns
   static constexpr int T1 = 96;                    // volume chunk outputs, two buffers at 0 and T1
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   int16_t* sGX = reinterpret_cast<int16_t*>(smem + T::OFF_GX);  // gidx [4][6][NFP]
   uint4* sNB = reinterpret_cast<uint4*>(smem + T::OFF_NB);                     // [128] neighbour offsets
   uint32_t* sC4 = reinterpret_cast<uint32_t*>(smem + T::OFF_NB + TILE * 16);   // [128] face codes
+  uint32_t* sIT = reinterpret_cast<uint32_t*>(smem + T::OFF_NB + TILE * 20);   // [128] neighbour rows in the tile
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + T::OFF_BAR);
   // bars: 0-3 operator slots, 4-5 first products of a chunk, 6 second products, 7 faces, 8 drain, 9 fields
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + T::OFF_BAR + 80);
@@ -281,6 +283,11 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
       };
       sNB[mrow] = make_uint4(nbo(e4.x), nbo(e4.y), nbo(e4.z), nbo(e4.w));
       sC4[mrow] = code4;
+      auto row = [&](int kn) {  // the neighbour column's row when this tile holds it (its values are in sQS)
+        const int64_t c = (int64_t)kn * S + sh - col0;
+        return kn >= 0 && c >= 0 && c < ncol_t ? (uint32_t)c : 0xffu;
+      };
+      sIT[mrow] = row(e4.x) | row(e4.y) << 8 | row(e4.z) << 16 | row(e4.w) << 24;
     }
 
     // ---- fields -> FP32 tile in shared memory (coalesced; or the bulk copies issued one tile ahead) ----
@@ -397,15 +404,19 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         const uint4 o4 = sNB[r];
         const uint32_t nbo = f == 0 ? o4.x : f == 1 ? o4.y : f == 2 ? o4.z : o4.w;
         const bool bnd = (nbo & 0x80000000u) != 0;
+        // a neighbour inside this tile (most neighbours within the same hexahedron or row) is read
+        // from the FP32 tile, the others from global memory (L2)
+        const uint32_t nrow = (sIT[r] >> (8 * f)) & 0xffu;
         float qp[2][4], qm[2][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int jj = j0 + h < NFP ? j0 + h : 0;
-          const int64_t b = (int64_t)(nbo & 0x7fffffffu) + sGX[(fnb * 6 + pn) * NFP + jj];
+          const int nn = sGX[(fnb * 6 + pn) * NFP + jj];
+          const int64_t b = (int64_t)(nbo & 0x7fffffffu) + nn;
           const int o = sGX[(f * 6 + po) * NFP + jj];
 #pragma unroll
           for (int fl = 0; fl < 4; ++fl) {
-            qp[h][fl] = __ldg(p.Qin + fl * fs + b);
+            qp[h][fl] = nrow != 0xffu ? sQS[(fl * TILE + nrow) * NPS + nn] : __ldg(p.Qin + fl * fs + b);
             qm[h][fl] = sQS[(fl * TILE + r) * NPS + o];
           }
         }
