@@ -180,6 +180,17 @@ cudaError_t launch_to_precision(int64_t n, const double* in, T* out, cudaStream_
 template cudaError_t launch_to_precision<float>(int64_t, const double*, float*, cudaStream_t);
 template cudaError_t launch_to_precision<double>(int64_t, const double*, double*, cudaStream_t);
 
+__global__ void fill_kernel(int64_t n, double v, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = v;
+}
+
+cudaError_t launch_fill(int64_t n, double v, double* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  fill_kernel<<<2048, 256, 0, st>>>(n, v, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_geo_pack_il(int64_t K, int Nq, int Nfq, const double* J, const double* G, const double* c2,
                                const double* Wpu, const double* nJ, float* vgeo_il, float* fgeo_il, cudaStream_t st) {
   geo_pack_il_kernel<<<2048, 256, 0, st>>>(K, Nq, Nfq, J, G, c2, Wpu, nJ, vgeo_il, fgeo_il);

@@ -24,6 +24,8 @@ cudaError_t launch_geo_conservative(int64_t K, int Np, int Nq, const double* J, 
 // out[i] = (T) in[i], i < n.
 template <typename T>
 cudaError_t launch_to_precision(int64_t n, const double* in, T* out, cudaStream_t st);
+// out[i] = v, i < n.
+cudaError_t launch_fill(int64_t n, double v, double* out, cudaStream_t st);
 template <typename T>
 cudaError_t launch_project(int64_t ncols, int S, int Np, int Nq, const double* fq, const double* J, const double* Vq,
                            const double* Pq, T* Q, cudaStream_t st);

@@ -185,6 +185,7 @@ void free_class(TcClass& c) {
     cudaFree(m->d_fcode);
     cudaFree(m->d_vgeo_il);
     cudaFree(m->d_fgeo_il);
+    cudaFree(m->d_meanc);
     cudaFree(m->d_err);
     cudaFree(m->d_Qtmp);
     delete m;  // the operator tables are the first member's
@@ -264,6 +265,17 @@ int build_class(wadg_batch* b, TcClass& c) {
   BCUDA(b, cudaMemcpy(cm->d_fcode, F.data(), F.size(), cudaMemcpyHostToDevice));
   BCUDA(b, cudaMemcpy(cm->d_vgeo_il, V.data(), V.size() * sizeof(float), cudaMemcpyHostToDevice));
   BCUDA(b, cudaMemcpy(cm->d_fgeo_il, G.data(), G.size() * sizeof(float), cudaMemcpyHostToDevice));
+  // the members' mean corrections, element by element in the combined order
+  cm->meanc_stride = (K + 3) / 4 * 4 * Np;
+  BCUDA(b, cudaMalloc((void**)&cm->d_meanc, (size_t)3 * cm->meanc_stride * sizeof(float)));
+  BCUDA(b, cudaMemset(cm->d_meanc, 0, (size_t)3 * cm->meanc_stride * sizeof(float)));
+  for (size_t j = 0; j < c.members.size(); ++j) {
+    const wadg_mesh* m = b->meshes[c.members[j]];
+    if (!m->d_meanc) return bfail(b, WADG_ESTATE, "a tensor-core member has no mean correction");
+    for (int i = 0; i < 3; ++i)
+      BCUDA(b, cudaMemcpy(cm->d_meanc + i * cm->meanc_stride + c.off[j] * Np, m->d_meanc + i * m->meanc_stride,
+                          (size_t)m->K * Np * sizeof(float), cudaMemcpyDeviceToDevice));
+  }
   return WADG_OK;
 }
 

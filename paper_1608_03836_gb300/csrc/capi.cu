@@ -444,6 +444,9 @@ int set_points(wadg_mesh* m, int count, const double* xyz, int64_t* elem_out, st
   return WADG_OK;
 }
 
+// The tensor-core stage's mean correction (defined with the stage launch helpers below).
+int mean_correction(wadg_mesh* m);
+
 }  // namespace
 
 extern "C" {
@@ -512,6 +515,7 @@ void wadg_mesh_destroy(wadg_mesh* m) {
   dfree(m->d_red);
   dfree(m->d_tcops);
   dfree(m->d_vgeo_il);
+  dfree(m->d_meanc);
   dfree(m->d_hostQ);
   dfree(m->d_hostR);
   dfree(m->d_fgeo_il);
@@ -799,6 +803,8 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
       if (!m->d_vgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_vgeo_il, (size_t)Kt * 128 * 11 * nq4 * 4 * sizeof(float)));
       if (!m->d_fgeo_il) WADG_CUDA(m, cudaMalloc((void**)&m->d_fgeo_il, (size_t)Kt * 128 * 12 * nf4 * 4 * sizeof(float)));
       WADG_CUDA(m, launch_geo_pack_il(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, Wpu, m->d_nJ, m->d_vgeo_il, m->d_fgeo_il, 0));
+      const int st = mean_correction(m);
+      if (st != WADG_OK) return st;
     }
   }
   if (!m->d_err) {
@@ -859,6 +865,58 @@ StageParams<T> base_params(const wadg_mesh* m) {
   return p;
 }
 
+// The tensor-core stage forms its products from each column's fields less
+// their element means (the derivatives of smooth fields and the nearly
+// cancelling volume and face terms of the p equation are then products of
+// small operands, so the rounding of the split operands stays small beside
+// the result) and adds back in FP32 the term of the element-constant
+// velocity: with p = 0 and u = e_i on every element, {u} = e_i on every face
+// and every jump vanishes, so r_p of that state is element k's own term D_i,
+// and r_p(Q) = r_p(Q - Qbar) + sum_i ubar_i D_i (the mean of p drops out:
+// p enters only through derivatives and jumps).  The FP64 CUDA-core stage
+// evaluates D_1..3 whenever the operators or update weights change.
+int mean_correction(wadg_mesh* m) {
+  const int64_t K = m->K;
+  const int Np = m->ref.Np, Nq = m->ref.Nq, Nfq = m->ref.Nfq;
+  const int64_t stride = (K + 3) / 4 * 4 * Np;
+  if (!m->d_meanc) {
+    WADG_CUDA(m, cudaMalloc((void**)&m->d_meanc, (size_t)3 * stride * sizeof(float)));
+    WADG_CUDA(m, cudaMemset(m->d_meanc, 0, (size_t)3 * stride * sizeof(float)));
+  }
+  m->meanc_stride = stride;
+  if (!m->ops64.base) {
+    const int st = upload_ops<double>(m, m->ops64);
+    if (st != WADG_OK) return st;
+  }
+  double *vg = nullptr, *fg = nullptr, *Q = nullptr, *out = nullptr;
+  const int64_t nf = K * Np;
+  cudaError_t e = cudaMalloc((void**)&vg, (size_t)K * 11 * Nq * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&fg, (size_t)K * 12 * Nfq * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&Q, (size_t)4 * nf * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&out, (size_t)4 * nf * sizeof(double));
+  const double* Wpu = m->conservative ? m->d_Wpu : nullptr;
+  if (e == cudaSuccess) e = launch_geo_pack<double>(K, Nq, Nfq, m->d_J, m->d_G, m->d_c2, Wpu, m->d_nJ, vg, fg, 0);
+  StageParams<double> p = base_params<double>(m);
+  p.vgeo = vg;
+  p.fgeo = fg;
+  p.ncols = K;
+  p.S = 1;
+  p.Qin = Q;
+  p.out = out;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = cudaMemset(Q, 0, (size_t)4 * nf * sizeof(double));
+    if (e == cudaSuccess) e = launch_fill(nf, 1.0, Q + (1 + i) * nf, 0);
+    if (e == cudaSuccess) e = launch_stage<double>(m->N, p, kRhs, 0);
+    if (e == cudaSuccess) e = launch_to_precision<float>(nf, out, m->d_meanc + i * stride, 0);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(vg);
+  cudaFree(fg);
+  cudaFree(Q);
+  cudaFree(out);
+  return e == cudaSuccess ? WADG_OK : cuda_fail(m, e, "the tensor-core stage's mean correction");
+}
+
 // Stage launch for the mesh's precision: RHS and LSRK stages of
 // WADG_FP32_3XBF16 and WADG_FP32_TF32 run on the tensor cores, everything
 // else on CUDA cores.
@@ -884,6 +942,8 @@ cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p,
     P.err = m->d_err;
     P.vgeo_il = m->d_vgeo_il;
     P.fgeo_il = m->d_fgeo_il;
+    P.meanc = m->d_meanc;
+    P.meanc_stride = m->meanc_stride;
     // bulk copies and 16-byte accesses of the field tiles: every field range
     // of a tile starts 16-byte aligned in every field array the stage touches
     auto a16 = [](const void* q) { return ((uintptr_t)q & 15) == 0; };
@@ -1030,6 +1090,9 @@ int wadg_set_conservation(wadg_mesh* m, int on) {
         e = launch_geo_pack_il(m->K, o.Nq, o.Nfq, m->d_J, m->d_G, m->d_c2, Wpu, m->d_nJ, m->d_vgeo_il, m->d_fgeo_il, 0);
       if (e == cudaSuccess) e = cudaDeviceSynchronize();
       if (e != cudaSuccess) st = cuda_fail(m, e, "repacking the update weights");
+      // the tensor-core stage's mean correction carries the update weights
+      if (st == WADG_OK && (m->precision == WADG_FP32_3XBF16 || m->precision == WADG_FP32_TF32))
+        st = mean_correction(m);
     }
     if (st != WADG_OK) {
       const std::string msg = m->last_error;

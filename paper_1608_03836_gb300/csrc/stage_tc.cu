@@ -63,7 +63,8 @@ struct TcDims {
   static constexpr int A_UCH = TILE * UQC * 2;    // one part of a [128 x 32] update chunk array
   static constexpr int B_UV = UQC * KP * 2;       // one part of a [32 x KP] operator chunk
   static constexpr int B_UP = KP * UQC * 2;       // one part of a [KP x 32] operator chunk
-  static constexpr int SZ_VA = 8 * B_V, SZ_VB = 8 * B_P, SZ_UA = 2 * B_UV, SZ_UB = 2 * B_UP;
+  // the update operators in three bf16 parts (the fourth product of mma4_chain)
+  static constexpr int SZ_VA = 8 * B_V, SZ_VB = 8 * B_P, SZ_UA = 3 * B_UV, SZ_UB = 3 * B_UP;
   static constexpr int SZ_OPV = SZ_VA + SZ_VB, SZ_OPU = SZ_UA + SZ_UB;
   static constexpr int SZ_OPS = NCH * SZ_OPV + UNCH * SZ_OPU;  // packed chunks before the face operators
   static constexpr int SZ_SLOT = SZ_VA > SZ_VB ? (SZ_VA > SZ_UA ? SZ_VA : SZ_UA) : (SZ_VB > SZ_UA ? SZ_VB : SZ_UA);
@@ -90,7 +91,8 @@ struct TcDims {
   // per tile column: offset of each face's neighbour column (4 x uint32, top bit: boundary), face codes,
   // the neighbour's row in the tile (4 x uint8, 0xff: outside the tile)
   static constexpr int OFF_NB = OFF_GX + SZ_GX;
-  static constexpr int OFF_BAR = OFF_NB + TILE * 24;
+  static constexpr int OFF_MEAN = OFF_NB + TILE * 24;  // element means of the tile's columns [4][128]
+  static constexpr int OFF_BAR = OFF_MEAN + 4 * TILE * 4;
   static constexpr int SMEM = OFF_BAR + 128;
   // TMEM columns
   static constexpr int T1 = 96;                    // volume chunk outputs, two buffers at 0 and T1
@@ -128,6 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
   uint4* sNB = reinterpret_cast<uint4*>(smem + T::OFF_NB);                     // [128] neighbour offsets
   uint32_t* sC4 = reinterpret_cast<uint32_t*>(smem + T::OFF_NB + TILE * 16);   // [128] face codes
   uint32_t* sIT = reinterpret_cast<uint32_t*>(smem + T::OFF_NB + TILE * 20);   // [128] neighbour rows in the tile
+  float* sMean = reinterpret_cast<float*>(smem + T::OFF_MEAN);                  // [4][128] element means
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + T::OFF_BAR);
   // bars: 0-3 operator slots, 4-5 first products of a chunk, 6 second products, 7 faces, 8 drain, 9 fields
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + T::OFF_BAR + 80);
@@ -238,15 +241,15 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     const uint32_t sl = slot_addr(c & 1), d = tmem + (uint32_t)((c & 1) * T::T1U);
     const int f = w - 8;
     if (f >= 0 && f < 4)
-      OF::template chain<KP>(mk_mma3(d + T::UQC * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP,
-                                     sl, sl + T::B_UV, sbo_KP, OF::idesc(128, T::UQC), false));
+      OF::template chain4<KP>(mk_mma4(d + T::UQC * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP,
+                                      sl, sl + T::B_UV, sl + 2 * T::B_UV, sbo_KP, OF::idesc(128, T::UQC), false));
   };
   auto issue_U2 = [&](int c, int f) {  // r += P_q (W ...) per field (N = KP, K = 32)
     if (!live()) return;
     const uint32_t sl = slot_addr(2 + (c & 1)), sbo_32 = OF::sbo(T::UQC);
     if (f < 4)
-      OF::template chain<T::UQC>(mk_mma3(tmem + T::TB + KP * f, ax + (2 * f) * T::A_UCH, ax + (2 * f + 1) * T::A_UCH,
-                                         sbo_32, sl, sl + T::B_UP, sbo_32, OF::idesc(128, KP), c > 0));
+      OF::template chain4<T::UQC>(mk_mma4(tmem + T::TB + KP * f, ax + (2 * f) * T::A_UCH, ax + (2 * f + 1) * T::A_UCH,
+                                          sbo_32, sl, sl + T::B_UP, sl + 2 * T::B_UP, sbo_32, OF::idesc(128, KP), c > 0));
   };
 
   // fields of a tile by bulk copies (when the FP32 tile has the global row
@@ -291,10 +294,19 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     }
 
     // ---- fields -> FP32 tile in shared memory (coalesced; or the bulk copies issued one tile ahead) ----
+    // the element mean of this thread's field and column
+    auto field_mean = [&]() {
+      float a[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int n = 0; n < NP; ++n) a[n % 5] += sQS[(grp * TILE + mrow) * NPS + n];
+      sMean[grp * TILE + mrow] = P.meanc ? ((a[0] + a[1]) + (a[2] + a[3]) + a[4]) * (1.f / NP) : 0.f;
+    };
     if (bulkq) {
-      wait_all(9, par_q);
+      wait_all(9, par_q);  // the copied tile is visible to every waiting thread
       par_q ^= 1u;
       pend &= ~16u;
+      field_mean();
+      __syncthreads();
     } else {
       const int nval = ncol_t * NP;
 #pragma unroll 5
@@ -303,8 +315,10 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         const int c = r / NP, n = r - c * NP;
         sQS[(f * TILE + c) * NPS + n] = r < nval ? __ldg(p.Qin + f * fs + col0 * NP + r) : 0.f;
       }
+      __syncthreads();
+      field_mean();
+      __syncthreads();
     }
-    __syncthreads();
 
     // ---- surface terms (Sec. 4.1, Sec. 6.4), face by face; the lifted terms
     // are gathered at this thread's volume nodes and summed in the b
@@ -407,6 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         // a neighbour inside this tile (most neighbours within the same hexahedron or row) is read
         // from the FP32 tile, the others from global memory (L2)
         const uint32_t nrow = (sIT[r] >> (8 * f)) & 0xffu;
+        const float ub[3] = {sMean[TILE + r], sMean[2 * TILE + r], sMean[3 * TILE + r]};
         float qp[2][4], qm[2][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -430,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
             const float up = bnd ? qm[h][1 + i] : qp[h][1 + i];
-            cv[1 + i][h] = on ? 0.5f * (up + qm[h][1 + i]) : 0.f;
+            cv[1 + i][h] = on ? 0.5f * (up + qm[h][1 + i]) - ub[i] : 0.f;  // {u} less the element mean
             cv[4 + i][h] = on ? up - qm[h][1 + i] : 0.f;
           }
         }
@@ -503,14 +518,15 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     if (failed) break;
     scatter(3);
 
-    // ---- field grp -> split A operand (over the lifted-value scratch: every
-    // thread has finished with it) ----
+    // ---- field grp less its element mean -> split A operand (over the
+    // lifted-value scratch: every thread has finished with it) ----
     __syncthreads();
+    const float fmean = sMean[grp * TILE + mrow];
 #pragma unroll
     for (int n0 = 0; n0 < KP; n0 += 8) {
       float x[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) x[j] = n0 + j < NP ? sQS[(grp * TILE + mrow) * NPS + n0 + j] : 0.f;
+      for (int j = 0; j < 8; ++j) x[j] = n0 + j < NP ? sQS[(grp * TILE + mrow) * NPS + n0 + j] - fmean : 0.f;
       OF::st8(sAQ + (2 * grp) * T::A_FIELD, T::A_FIELD, mrow, n0, KP, x);
     }
     sync_check();
@@ -610,13 +626,17 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     wait_all(6, par_m2);
     par_m2 ^= 1u;
     if (tid == 0) {  // update operators of chunks 0 and 1
-      if (MODE == kLsrk && bulkq) {
-        // the epilogue's reads of Q_in and res for this tile, into L2 while the update runs
+      if (bulkq) {
+        // the epilogue's reads of Q_in and res (and of the mean correction
+        // when a column is one element) for this tile, into L2 while the update runs
         const uint32_t bytes = (uint32_t)(ncol_t * NP * 4);
-        for (int f = 0; f < 4; ++f) {
-          tc::bulk_prefetch_l2(p.Qin + f * fs + col0 * NP, bytes);
-          if (p.rk_a != 0.f) tc::bulk_prefetch_l2(p.res + f * fs + col0 * NP, bytes);
-        }
+        if (MODE == kLsrk)
+          for (int f = 0; f < 4; ++f) {
+            tc::bulk_prefetch_l2(p.Qin + f * fs + col0 * NP, bytes);
+            if (p.rk_a != 0.f) tc::bulk_prefetch_l2(p.res + f * fs + col0 * NP, bytes);
+          }
+        if (P.meanc && S == 1)
+          for (int i = 0; i < 3; ++i) tc::bulk_prefetch_l2(P.meanc + i * P.meanc_stride + col0 * NP, bytes);
       }
       load_slot(0, upd_ops, T::SZ_UA);
       load_slot(2, upd_ops + T::SZ_UA, T::SZ_UB);
@@ -736,6 +756,26 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
     }
 
     // ---- epilogue: r -> FP32 tile -> coalesced dQ/dt, or the LSRK update (Sec. 5.2) ----
+    // With 16-byte accesses and one element per column, the mean correction
+    // of the p-field float4 entries r4 = tid + e kThreads that this thread
+    // takes below is loaded before the TMEM reads (its latency overlaps them)
+    // and added to the FP32 tile by the same thread.
+    constexpr int F4P = TILE * NP / 4, NEP = (F4P + kThreads - 1) / kThreads;
+    const bool dpre = bulkq && S == 1 && P.meanc != nullptr;
+    const int nvalp4 = ncol_t * NP / 4;
+    float4 dA[NEP], dB[NEP], dC[NEP];
+    if constexpr (NPS == NP) {
+#pragma unroll
+      for (int e = 0; e < NEP; ++e) {
+        const int r4 = tid + e * kThreads;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = dpre && r4 < nvalp4;
+        const float4* d = reinterpret_cast<const float4*>(P.meanc + col0 * NP) + r4;
+        dA[e] = ok ? __ldg(d) : z;
+        dB[e] = ok ? __ldg(d + P.meanc_stride / 4) : z;
+        dC[e] = ok ? __ldg(d + P.meanc_stride / 2) : z;
+      }
+    }
 #pragma unroll
     for (int n0 = 0; n0 < KP; n0 += 8) {
       uint32_t v[8];
@@ -747,18 +787,79 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         if (n0 + j < NP) sTT[(grp * TILE + mrow) * NPS + n0 + j] = __uint_as_float(v[j]);
     }
     sync_check();
+    if constexpr (NPS == NP) {
+      if (dpre) {
+        float4* sT4w = reinterpret_cast<float4*>(sTT);
+#pragma unroll
+        for (int e = 0; e < NEP; ++e) {
+          const int r4 = tid + e * kThreads;
+          if (r4 >= nvalp4) continue;
+          const float da[4] = {dA[e].x, dA[e].y, dA[e].z, dA[e].w}, db[4] = {dB[e].x, dB[e].y, dB[e].z, dB[e].w},
+                      dc[4] = {dC[e].x, dC[e].y, dC[e].z, dC[e].w};
+          const int c0 = 4 * r4 / NP, n0 = 4 * r4 - c0 * NP;
+          float o[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int c = c0 + (n0 + t >= NP ? 1 : 0);
+            o[t] = sMean[TILE + c] * da[t] + sMean[2 * TILE + c] * db[t] + sMean[3 * TILE + c] * dc[t];
+          }
+          float4 v = sT4w[r4];
+          v.x += o[0];
+          v.y += o[1];
+          v.z += o[2];
+          v.w += o[3];
+          sT4w[r4] = v;
+        }
+      }
+    }
+    // r_p += sum_i ubar_i D_i (the element-constant velocity's term, in FP32)
+    // at entry r = c NP + n of the tile's p field
+    const int64_t mst = P.meanc_stride;
+    auto corr1 = [&](int r) -> float {
+      if (!P.meanc) return 0.f;
+      const int c = r / NP, n = r - c * NP;
+      const float* d = P.meanc + ((col0 + c) / S) * NP + n;
+      return sMean[TILE + c] * __ldg(d) + sMean[2 * TILE + c] * __ldg(d + mst) +
+             sMean[3 * TILE + c] * __ldg(d + 2 * mst);
+    };
     if (bulkq) {
       // 16-byte accesses: the FP32 tile has the global row stride (NPS = NP)
       // and every field range of the tile starts 16-byte aligned
       constexpr int F4 = TILE * NP / 4, NIT4 = (4 * F4 + kThreads - 1) / kThreads;
       const int nval4 = ncol_t * NP / 4;
       const float4* sT4 = reinterpret_cast<const float4*>(sTT);
+      auto corr4 = [&](int r4) -> float4 {
+        float o[4];
+        if (P.meanc && S == 1) {  // one element per column: D has the field's layout
+          const float4* d = reinterpret_cast<const float4*>(P.meanc + col0 * NP) + r4;
+          const float4 a = __ldg(d), b = __ldg(d + mst / 4), c = __ldg(d + mst / 2);
+          const float da[4] = {a.x, a.y, a.z, a.w}, db[4] = {b.x, b.y, b.z, b.w}, dc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int cc = (4 * r4 + t) / NP;
+            o[t] = sMean[TILE + cc] * da[t] + sMean[2 * TILE + cc] * db[t] + sMean[3 * TILE + cc] * dc[t];
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) o[t] = corr1(4 * r4 + t);
+        }
+        return make_float4(o[0], o[1], o[2], o[3]);
+      };
       if (MODE == kRhs) {
 #pragma unroll 3
         for (int it = 0; it < NIT4; ++it) {
           const int i = tid + it * kThreads, f = i / F4, r4 = i - f * F4;
-          if (i < 4 * F4 && r4 < nval4)
-            reinterpret_cast<float4*>(p.out + f * fs + col0 * NP)[r4] = sT4[f * F4 + r4];
+          if (i < 4 * F4 && r4 < nval4) {
+            float4 v = sT4[f * F4 + r4];
+            if (f == 0 && !dpre) {
+              const float4 c = corr4(r4);
+              v.x += c.x;
+              v.y += c.y;
+              v.z += c.z;
+              v.w += c.w;
+            }
+            reinterpret_cast<float4*>(p.out + f * fs + col0 * NP)[r4] = v;
+          }
         }
       } else {
         // LSRK (Sec. 5.2) as below, EB4 float4 loads of res and Q_in issued
@@ -775,6 +876,13 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
             ix[e] = ok ? (f * fs + col0 * NP) / 4 + r4 : -1;
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             vv[e] = ok ? sT4[f * F4 + r4] : z;
+            if (ok && f == 0 && !dpre) {
+              const float4 c = corr4(r4);
+              vv[e].x += c.x;
+              vv[e].y += c.y;
+              vv[e].z += c.z;
+              vv[e].w += c.w;
+            }
             rs[e] = ok && rd ? __ldg(reinterpret_cast<const float4*>(p.res) + ix[e]) : z;
             qi[e] = ok ? __ldg(reinterpret_cast<const float4*>(p.Qin) + ix[e]) : z;
           }
@@ -801,7 +909,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
           const int f = i / (TILE * NP), r = i - f * (TILE * NP);
           if (r >= nval) continue;
           const int c = r / NP, n = r - c * NP;
-          p.out[f * fs + col0 * NP + r] = sTT[(f * TILE + c) * NPS + n];
+          p.out[f * fs + col0 * NP + r] = sTT[(f * TILE + c) * NPS + n] + (f == 0 ? corr1(r) : 0.f);
         }
       } else {
         // LSRK (Sec. 5.2): res = a res + dt r, Q_out = Q_in + b res.  The loads of
@@ -819,7 +927,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
             const bool ok = i0 + e < NIT && i < 4 * TILE * NP && r < nval;
             const int c = r / NP, n = r - c * NP;
             ix[e] = ok ? f * fs + col0 * NP + r : -1;
-            vv[e] = ok ? sTT[(f * TILE + c) * NPS + n] : 0.f;
+            vv[e] = ok ? sTT[(f * TILE + c) * NPS + n] + (f == 0 ? corr1(r) : 0.f) : 0.f;
             rs[e] = ok && rd ? __ldg(p.res + ix[e]) : 0.f;
             qi[e] = ok ? __ldg(p.Qin + ix[e]) : 0.f;
           }

@@ -39,7 +39,8 @@ struct TcDims5 {
   static constexpr int B_V = QC * KP * 2, B_P = KP * QC * 2;
   static constexpr int UQC = 16, UNCH = (NQ + UQC - 1) / UQC;
   static constexpr int A_UCH = TILE * UQC * 2, B_UV = UQC * KP * 2, B_UP = KP * UQC * 2;
-  static constexpr int SZ_VA = 8 * B_V, SZ_VB = 8 * B_P, SZ_UA = 2 * B_UV, SZ_UB = 2 * B_UP;
+  // the update operators in three bf16 parts (the fourth product of mma4_chain)
+  static constexpr int SZ_VA = 8 * B_V, SZ_VB = 8 * B_P, SZ_UA = 3 * B_UV, SZ_UB = 3 * B_UP;
   static constexpr int SZ_OPV = SZ_VA + SZ_VB, SZ_OPU = SZ_UA + SZ_UB;
   static constexpr int SZ_OPS = NCH * SZ_OPV + UNCH * SZ_OPU;
   static constexpr int NFP16 = 32, NFQ16 = 48;
@@ -55,7 +56,8 @@ struct TcDims5 {
   static constexpr int SZ_X = SZ_AX;
   static constexpr int OFF_GI = OFF_X + SZ_X, SZ_GI = (4 * 6 * NP * 2 + 15) / 16 * 16;
   static constexpr int OFF_GX = OFF_GI + SZ_GI, SZ_GX = (4 * 6 * NFP * 2 + 15) / 16 * 16;
-  static constexpr int OFF_NB = OFF_GX + SZ_GX, OFF_BAR = OFF_NB + TILE * 20, SMEM = OFF_BAR + 128;
+  static constexpr int OFF_NB = OFF_GX + SZ_GX, OFF_MEAN = OFF_NB + TILE * 20;  // element means [4][128]
+  static constexpr int OFF_BAR = OFF_MEAN + 4 * TILE * 4, SMEM = OFF_BAR + 128;
   // TMEM columns
   static constexpr int TB = 256;        // b accumulators of the four fields, 64 each; then r
   static constexpr int T1 = 96;         // volume chunk outputs (u_i: 3 x 16, dp/dx^_a: 48), buffers at 0, 96
@@ -98,6 +100,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
   int16_t* sGX = reinterpret_cast<int16_t*>(smem + T::OFF_GX);
   uint4* sNB = reinterpret_cast<uint4*>(smem + T::OFF_NB);
   uint32_t* sC4 = reinterpret_cast<uint32_t*>(smem + T::OFF_NB + TILE * 16);
+  float* sMean = reinterpret_cast<float*>(smem + T::OFF_MEAN);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + T::OFF_BAR);
   // bars: 0-3 operator slots, 4-5 first products of a chunk, 6 second products, 7 faces, 8 drain
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + T::OFF_BAR + 80);
@@ -206,15 +209,15 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
     const uint32_t sl = slot_addr(ua_slot(c)), d = tmem + (uint32_t)((c & 1) * T::T1U);
     const int f = w - 8;
     if (f >= 0 && f < 4)
-      OF::template chain<KP>(mk_mma3(d + T::UQC * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP,
-                                     sl, sl + T::B_UV, sbo_KP, OF::idesc(128, T::UQC), false));
+      OF::template chain4<KP>(mk_mma4(d + T::UQC * f, aq + (2 * f) * T::A_FIELD, aq + (2 * f + 1) * T::A_FIELD, sbo_KP,
+                                      sl, sl + T::B_UV, sl + 2 * T::B_UV, sbo_KP, OF::idesc(128, T::UQC), false));
   };
   auto issue_U2 = [&](int c, int f) {  // r += P_q (W ...) per field (N = 64, K = 16), warps 0-3
     if (!live()) return;
     const uint32_t sl = slot_addr(ub_slot(c));
     if (f < 4)
-      OF::template chain<T::UQC>(mk_mma3(tmem + T::TB + KP * f, ax + (2 * f) * T::A_UCH, ax + (2 * f + 1) * T::A_UCH,
-                                         sbo_16, sl, sl + T::B_UP, sbo_16, OF::idesc(128, KP), c > 0));
+      OF::template chain4<T::UQC>(mk_mma4(tmem + T::TB + KP * f, ax + (2 * f) * T::A_UCH, ax + (2 * f + 1) * T::A_UCH,
+                                          sbo_16, sl, sl + T::B_UP, sl + 2 * T::B_UP, sbo_16, OF::idesc(128, KP), c > 0));
   };
   // the tile's field ranges are 16-byte aligned (L2 prefetch of the epilogue's reads)
   const bool aligned = P.bulk_q != 0;
@@ -239,6 +242,21 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
     }
     // face operators into region X (the previous tile's chunk arrays are free)
     stage_copy(sFT, P.ops + (size_t)T::SZ_OPS, T::SZ_FOPS);
+    {  // the element mean of this thread's field and column (from global memory)
+      float a = 0.f;
+      const float* q = p.Qin + grp * fs + cm * NP;
+      if (aligned) {
+#pragma unroll
+        for (int n4 = 0; n4 < NP / 4; ++n4) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(q) + n4);
+          a += (v.x + v.y) + (v.z + v.w);
+        }
+      } else {
+#pragma unroll 8
+        for (int n = 0; n < NP; ++n) a += __ldg(q + n);
+      }
+      sMean[grp * TILE + mrow] = P.meanc ? a * (1.f / NP) : 0.f;
+    }
     __syncthreads();
 
     // ---- surface terms (Sec. 4.1, Sec. 6.4), face by face, two passes ----
@@ -300,7 +318,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
             const float up = bnd[it] ? qm[it][1 + i] : qp[it][1 + i];
-            OF::st1(sFA + (2 * (1 + i)) * T::A_FN, T::A_FN, r, j, NFP16, on ? 0.5f * (up + qm[it][1 + i]) : 0.f);
+            // {u} less the element mean
+            OF::st1(sFA + (2 * (1 + i)) * T::A_FN, T::A_FN, r, j, NFP16,
+                    on ? 0.5f * (up + qm[it][1 + i]) - sMean[(1 + i) * TILE + r] : 0.f);
             OF::st1(sFB + (2 * i) * T::A_FN, T::A_FN, r, j, NFP16, on ? up - qm[it][1 + i] : 0.f);
           }
         }
@@ -460,16 +480,18 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
     }
     if (failed) break;
 
-    // ---- field grp of this thread's column -> split A operand (from global memory) ----
+    // ---- field grp of this thread's column less its element mean -> split A
+    // operand (from global memory) ----
     {
       const float4* q4 = reinterpret_cast<const float4*>(p.Qin + grp * fs + cm * NP);
+      const float mu = sMean[grp * TILE + mrow];
 #pragma unroll
       for (int n0 = 0; n0 < KP; n0 += 8) {
         float x[8];
         if (n0 + 8 <= NP) {
           const float4 a = __ldg(q4 + n0 / 4), b = __ldg(q4 + n0 / 4 + 1);
-          x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-          x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+          x[0] = a.x - mu; x[1] = a.y - mu; x[2] = a.z - mu; x[3] = a.w - mu;
+          x[4] = b.x - mu; x[5] = b.y - mu; x[6] = b.z - mu; x[7] = b.w - mu;
         } else {
 #pragma unroll
           for (int j = 0; j < 8; ++j) x[j] = 0.f;
@@ -562,12 +584,17 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
     wait_all(6, par_m2);
     par_m2 ^= 1u;
     if (tid == 0) {  // update operators of chunks 0 and 1
-      if (MODE == kLsrk && aligned) {
+      if (aligned) {
+        // the epilogue's reads of Q_in and res (and of the mean correction
+        // when a column is one element) for this tile, into L2 while the update runs
         const uint32_t bytes = (uint32_t)(ncol_t * NP * 4);
-        for (int f = 0; f < 4; ++f) {
-          tc::bulk_prefetch_l2(p.Qin + f * fs + col0 * NP, bytes);
-          if (p.rk_a != 0.f) tc::bulk_prefetch_l2(p.res + f * fs + col0 * NP, bytes);
-        }
+        if (MODE == kLsrk)
+          for (int f = 0; f < 4; ++f) {
+            tc::bulk_prefetch_l2(p.Qin + f * fs + col0 * NP, bytes);
+            if (p.rk_a != 0.f) tc::bulk_prefetch_l2(p.res + f * fs + col0 * NP, bytes);
+          }
+        if (P.meanc && S == 1)
+          for (int i = 0; i < 3; ++i) tc::bulk_prefetch_l2(P.meanc + i * P.meanc_stride + col0 * NP, bytes);
       }
       load_slot(ua_slot(0), upd_ops, T::SZ_UA);
       load_slot(ub_slot(0), upd_ops + T::SZ_UA, T::SZ_UB);
@@ -688,6 +715,26 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
       d[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]), __uint_as_float(v[7]));
     }
     sync_check();
+    // r_p += sum_i ubar_i D_i (the element-constant velocity's term, in FP32)
+    // at entry r = c NP + n of the tile's p field
+    const int64_t mst = P.meanc_stride;
+    auto corr1 = [&](int r) -> float {
+      if (!P.meanc) return 0.f;
+      const int c = r / NP, n = r - c * NP;
+      const float* d = P.meanc + ((col0 + c) / S) * NP + n;
+      return sMean[TILE + c] * __ldg(d) + sMean[2 * TILE + c] * __ldg(d + mst) +
+             sMean[3 * TILE + c] * __ldg(d + 2 * mst);
+    };
+    // four entries of one column (NP is a multiple of 4)
+    auto corr4 = [&](int r4) -> float4 {
+      if (!P.meanc) return make_float4(0.f, 0.f, 0.f, 0.f);
+      const int c = 4 * r4 / NP, n = 4 * r4 - c * NP;
+      const float4* d = reinterpret_cast<const float4*>(P.meanc + ((col0 + c) / S) * NP + n);
+      const float4 a = __ldg(d), b = __ldg(d + mst / 4), e = __ldg(d + mst / 2);
+      const float m1 = sMean[TILE + c], m2 = sMean[2 * TILE + c], m3 = sMean[3 * TILE + c];
+      return make_float4(m1 * a.x + m2 * b.x + m3 * e.x, m1 * a.y + m2 * b.y + m3 * e.y,
+                         m1 * a.z + m2 * b.z + m3 * e.z, m1 * a.w + m2 * b.w + m3 * e.w);
+    };
     if (aligned) {
       // 16-byte global accesses: every field range of the tile starts 16-byte aligned
       constexpr int F4 = TILE * NP / 4, NIT4 = (4 * F4 + kThreads - 1) / kThreads;
@@ -697,8 +744,17 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
 #pragma unroll 7
         for (int it = 0; it < NIT4; ++it) {
           const int i = tid + it * kThreads, f = i / F4, r4 = i - f * F4;
-          if (i < 4 * F4 && r4 < nval4)
-            reinterpret_cast<float4*>(p.out + f * fs + col0 * NP)[r4] = sT4[f * F4 + r4];
+          if (i < 4 * F4 && r4 < nval4) {
+            float4 v = sT4[f * F4 + r4];
+            if (f == 0) {
+              const float4 c = corr4(r4);
+              v.x += c.x;
+              v.y += c.y;
+              v.z += c.z;
+              v.w += c.w;
+            }
+            reinterpret_cast<float4*>(p.out + f * fs + col0 * NP)[r4] = v;
+          }
         }
       } else {
         // LSRK: res = a res + dt r, Q_out = Q_in + b res; the loads of EB4
@@ -715,6 +771,13 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
             ix[e] = ok ? (f * fs + col0 * NP) / 4 + r4 : -1;
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             vv[e] = ok ? sT4[f * F4 + r4] : z;
+            if (ok && f == 0) {
+              const float4 c = corr4(r4);
+              vv[e].x += c.x;
+              vv[e].y += c.y;
+              vv[e].z += c.z;
+              vv[e].w += c.w;
+            }
             rs[e] = ok && rd ? __ldg(reinterpret_cast<const float4*>(p.res) + ix[e]) : z;
             qi[e] = ok ? __ldg(reinterpret_cast<const float4*>(p.Qin) + ix[e]) : z;
           }
@@ -739,7 +802,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
 #pragma unroll 4
         for (int i = tid; i < 4 * TILE * NP; i += kThreads) {
           const int f = i / (TILE * NP), r = i - f * (TILE * NP);
-          if (r < nval) p.out[f * fs + col0 * NP + r] = sTT[i];
+          if (r < nval) p.out[f * fs + col0 * NP + r] = sTT[i] + (f == 0 ? corr1(r) : 0.f);
         }
       } else {
         constexpr int NIT = (4 * TILE * NP + kThreads - 1) / kThreads, EB = 7;
@@ -753,7 +816,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc5_kernel(const TcStagePar
             const int f = i / (TILE * NP), r = i - f * (TILE * NP);
             const bool ok = i0 + e < NIT && i < 4 * TILE * NP && r < nval;
             ix[e] = ok ? f * fs + col0 * NP + r : -1;
-            vv[e] = ok ? sTT[i] : 0.f;
+            vv[e] = ok ? sTT[i] + (f == 0 ? corr1(r) : 0.f) : 0.f;
             rs[e] = ok && rd ? __ldg(p.res + ix[e]) : 0.f;
             qi[e] = ok ? __ldg(p.Qin + ix[e]) : 0.f;
           }

@@ -93,6 +93,35 @@ __device__ __forceinline__ void mma3_chain(const Mma3& g) {
   }
 }
 
+// The same with the B operand in three bf16 parts b = bh + bl + b3 (the
+// residual of the two-part split in a third part) and a fourth product
+// ah*b3 per K step: the operator's rounding drops from 2^-18 to 2^-27 of its
+// entries, and what remains of the product's rounding (the A operand's
+// split, the dropped al*bl) changes with the data instead of being the same
+// perturbation of the operator at every stage.
+struct Mma4 {
+  Mma3 g;
+  uint64_t b3;
+};
+
+__device__ __forceinline__ Mma4 mk_mma4(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t a_sbo, uint32_t b_hi,
+                                        uint32_t b_lo, uint32_t b_3, uint32_t b_sbo, uint32_t idesc, bool acc) {
+  return Mma4{mk_mma3(d, a_hi, a_lo, a_sbo, b_hi, b_lo, b_sbo, idesc, acc), tc::smem_desc(b_3, 128, b_sbo)};
+}
+
+template <int KS>
+__device__ __forceinline__ void mma4_chain(const Mma4& m) {
+  const Mma3& g = m.g;
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    const uint64_t o = (uint64_t)(16 * ks);
+    tc::mma_bf16(g.d, g.ah + o, g.bh + o, g.idesc, (g.acc || ks > 0) ? 1u : 0u);
+    tc::mma_bf16(g.d, g.ah + o, g.bl + o, g.idesc, 1u);
+    tc::mma_bf16(g.d, g.al + o, g.bh + o, g.idesc, 1u);
+    tc::mma_bf16(g.d, g.ah + o, m.b3 + o, g.idesc, 1u);
+  }
+}
+
 // Operand formats.  A tile of R rows by K values takes R K 4 bytes in both:
 // format 0 holds the bf16 hi part at the tile base and the lo part `part`
 // bytes after it (three products per K step of 16); format 1 holds tf32
@@ -131,6 +160,10 @@ struct OpFmt<0> {
     *reinterpret_cast<__nv_bfloat162*>(base + part + o) = lb;
   }
   template <int KE>
+  __device__ static void chain4(const Mma4& m) {
+    mma4_chain<KE / 16>(m);
+  }
+  template <int KE>
   __device__ static void chain(const Mma3& g) {
     mma3_chain<KE / 16>(g);
   }
@@ -164,6 +197,11 @@ struct OpFmt<1> {
       const uint64_t o = (uint64_t)(16 * ks);
       tc::mma_tf32(g.d, g.ah + o, g.bh + o, g.idesc, (g.acc || ks > 0) ? 1u : 0u);
     }
+  }
+  // tf32 operators are one part
+  template <int KE>
+  __device__ static void chain4(const Mma4& m) {
+    chain<KE>(m.g);
   }
 };
 
@@ -221,6 +259,23 @@ void put_tile(int fmt, uint8_t* dst, size_t part_bytes, int R, int K, F value) {
     }
 }
 
+// As put_tile, with the residual of the two-part bf16 split in a third part
+// at dst + 2 part_bytes (format 0); format 1 as put_tile.
+template <typename F>
+void put_tile3(int fmt, uint8_t* dst, size_t part_bytes, int R, int K, F value) {
+  put_tile(fmt, dst, part_bytes, R, K, value);
+  if (fmt != 0) return;
+  for (int r = 0; r < R; ++r)
+    for (int k = 0; k < K; ++k) {
+      const double x = value(r, k);
+      const uint16_t h = bf16_bits_rne((float)x);
+      const double rh = x - (double)bf16_bits_to_float(h);
+      const uint16_t l = bf16_bits_rne((float)rh);
+      const uint16_t t = bf16_bits_rne((float)(rh - (double)bf16_bits_to_float(l)));
+      std::memcpy(dst + 2 * part_bytes + host_kmajor_offset(r, k, K), &t, 2);
+    }
+}
+
 // The packed operators of a tensor-core stage with dimensions T, chunk by
 // chunk in the order the kernel stages them: per volume chunk of QC points
 // the A part (V_q, V_q^a) and the B part ((V_q^a)^T diag(w), V_q^T diag(w)),
@@ -253,11 +308,11 @@ void pack_dims(const RefOps& o, int fmt, std::vector<uint8_t>& out) {
   for (int ch = 0; ch < T::UNCH; ++ch) {
     auto qn = [&](int r) { return ch * T::UQC + r; };
     uint8_t* u = out.data() + (size_t)T::NCH * T::SZ_OPV + (size_t)ch * T::SZ_OPU;
-    put_tile(fmt, u, T::B_UV, T::UQC, KP, [&](int r, int n) {
+    put_tile3(fmt, u, T::B_UV, T::UQC, KP, [&](int r, int n) {
       const int q = qn(r);
       return (q < Nq && n < Np) ? o.Vtilde[q * Np + n] : 0.0;
     });
-    put_tile(fmt, u + 2 * T::B_UV, T::B_UP, KP, T::UQC, [&](int n, int k) {
+    put_tile3(fmt, u + T::SZ_UA, T::B_UP, KP, T::UQC, [&](int n, int k) {
       const int q = qn(k);
       return (q < Nq && n < Np) ? o.Pq[n * Nq + q] : 0.0;
     });

@@ -149,6 +149,11 @@ struct TcStageParams {
   const float* vgeo_il = nullptr;  // column-interleaved geometric factors (see aux_kernels.cu)
   const float* fgeo_il = nullptr;
   int bulk_q = 0;  // fields may be loaded by bulk copies (16-byte aligned tiles, row stride = Np)
+  // r_p of the stage for the element-constant velocity e_i (p = 0), [3][stride]
+  // with element k's Np values at k * Np: the products run on each column's
+  // fields less their element means, and the epilogue adds sum_i ubar_i D_i
+  const float* meanc = nullptr;
+  int64_t meanc_stride = 0;
 };
 cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
 bool pack_tc_ops(int N, const RefOps& o, int fmt, std::vector<uint8_t>& out);
@@ -223,6 +228,8 @@ struct wadg_mesh {
   size_t host_io_bytes = 0;
   float* d_vgeo_il = nullptr;  // column-interleaved geometry for the tensor-core stage
   float* d_fgeo_il = nullptr;
+  float* d_meanc = nullptr;     // the tensor-core stage's mean correction [3][Kp][Np], Kp = K rounded up to 4
+  int64_t meanc_stride = 0;
   int* d_err = nullptr;        // device error flag (bounded waits)
   int num_sms = 0;
   void* d_Qtmp = nullptr;      // ping-pong buffer for LSRK stages

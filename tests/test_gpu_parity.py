@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import (TOL, library_mesh, make_mesh_inputs, oracle_c2, oracle_case, random_Q, rel_errors,
+from gpu_util import (TOL, TRACE_FACTOR, library_mesh, make_mesh_inputs, oracle_c2, oracle_case, random_Q, rel_errors,
                       to_torch)
 from synthetic import kuhn_cube, geometry_nodes, standing_wave
 
@@ -55,6 +55,35 @@ def test_rhs_matches_oracle(W, precision, N, n):
     l2, mx = rel_errors(got, want)
     print(f"N={N} {precision}: rel L2 {l2:.3e}, rel max {mx:.3e}")
     assert l2 < TOL[precision] and mx < 10 * TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_3xbf16"])
+@pytest.mark.parametrize("N,n", [(2, 8), (4, 8)])
+def test_smooth_fields_rhs_matches_oracle(W, precision, N, n):
+    """The standing wave at t = 0.3 projected by the oracle (smooth in every
+    element), on the fewer-point rule: the RHS of smooth fields is a small
+    difference of large volume and face terms and a derivative of nearly
+    constant data, which amplifies the rounding of the operands (by about 1/h
+    for element means left in).  Split bf16 with the element means taken out
+    of its products stays at 4-7e-5 here (3.4e-4 and 2e-4 with them in, at
+    N = 4 and 2 on 3,072 tets); the bar is 1.2e-4, and 4e-5 for FP32 (its
+    p field reaches 1.5e-5)."""
+    from oracle import wadg as OW
+    from synthetic import standing_wave, fewer_point_rule
+    rule = fewer_point_rule(N)
+    VXYZ, EToV, geom = make_mesh_inputs(n, N)
+    om = oracle_case(VXYZ, EToV, geom, N, rule=rule)
+    c = OW.wadg_projection(om, standing_wave(om.xq, 0.3))
+    Q = om.ref.to_nodal(c)[:, :, None, :]
+    m = library_mesh(VXYZ, EToV, geom, N, precision, rule=rule)
+    got = _gpu_rhs(W, m, Q)[:, :, 0]
+    W.wadg_device_status(m)
+    want = _oracle_rhs(om, Q[:, :, 0])
+    bar = {"fp32": 4e-5, "fp32_3xbf16": 1.2e-4}[precision]
+    for f in range(4):
+        l2, _ = rel_errors(got[f], want[f])
+        print(f"smooth N={N} n={n} {precision} field {f}: rel L2 {l2:.3e}")
+        assert l2 < bar, (f, l2)
 
 
 def test_volume_points_match_oracle_geometry(W):
@@ -243,7 +272,7 @@ def test_sources_and_receivers_match_oracle(W, precision):
             want_tr.append(OS.sample(c[0], rec, np.arange(s * R, (s + 1) * R)))
         l2, _ = rel_errors(got_Q[:, :, s], om.ref.to_nodal(c))
         l2t, _ = rel_errors(got_tr[:, s], np.array(want_tr))
-        assert l2 < TOL[precision] and l2t < TOL[precision], (s, l2, l2t)
+        assert l2 < TOL[precision] and l2t < TRACE_FACTOR * TOL[precision], (s, l2, l2t)
 
 
 def test_bounded_wait_expiry_is_reported(W):

@@ -7,7 +7,7 @@ collapsed 216-point rule and on the 96-point symmetric rule."""
 import numpy as np
 import pytest
 
-from gpu_util import (TOL, library_mesh, make_mesh_inputs, oracle_c2, oracle_case, random_Q, rel_errors,
+from gpu_util import (TOL, TRACE_FACTOR, library_mesh, make_mesh_inputs, oracle_c2, oracle_case, random_Q, rel_errors,
                       to_torch)
 from synthetic import geometry_nodes
 
@@ -115,7 +115,7 @@ def test_tc5_sources_and_receivers_match_oracle(W, precision):
             want_tr.append(OS.sample(c[0], rec, np.arange(s * R, (s + 1) * R)))
         l2, _ = rel_errors(got_Q[:, :, s], om.ref.to_nodal(c))
         l2t, _ = rel_errors(got_tr[:, s], np.array(want_tr))
-        assert l2 < TOL[precision] and l2t < TOL[precision], (s, l2, l2t)
+        assert l2 < TOL[precision] and l2t < TRACE_FACTOR * TOL[precision], (s, l2, l2t)
 
 
 @pytest.mark.parametrize("precision", TC)
