@@ -421,7 +421,6 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
         // a neighbour inside this tile (most neighbours within the same hexahedron or row) is read
         // from the FP32 tile, the others from global memory (L2)
         const uint32_t nrow = (sIT[r] >> (8 * f)) & 0xffu;
-        const float ub[3] = {sMean[TILE + r], sMean[2 * TILE + r], sMean[3 * TILE + r]};
         float qp[2][4], qm[2][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -445,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
             const float up = bnd ? qm[h][1 + i] : qp[h][1 + i];
-            cv[1 + i][h] = on ? 0.5f * (up + qm[h][1 + i]) - ub[i] : 0.f;  // {u} less the element mean
+            cv[1 + i][h] = on ? 0.5f * (up + qm[h][1 + i]) - sMean[(1 + i) * TILE + r] : 0.f;  // {u} less the element mean
             cv[4 + i][h] = on ? up - qm[h][1 + i] : 0.f;
           }
         }
