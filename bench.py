@@ -1015,8 +1015,12 @@ def main():
                      "launch_ms": lsrk_ms,
                      "launch_ms_from": "the timed region: ms_per_step / 5 launches (CUDA events on the launching stream)",
                      "algorithmic_bytes_per_element": B,
+                     # the tensor-core stage's mean correction, 3 x Np FP32 values per element read in
+                     # the epilogue: part of the traffic, not of the method's algorithmic bytes
+                     "mean_correction_bytes_per_element": 12 * (WORKLOAD["N"] + 1) * (WORKLOAD["N"] + 2) * (WORKLOAD["N"] + 3) // 6,
                      "tensor": {"achieved_fp32_equiv_tflops": achieved_tf,
-                                "note": "flops counted once per product; each runs as three bf16 MMAs"}},
+                                "note": "flops counted once per product; each runs as three bf16 MMAs "
+                                        "(four in the update, whose operators carry a third part)"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
