@@ -464,9 +464,11 @@ def equal_error(W, T=0.25):
     against the analytic solution by the volume rule.  'Equal' means within
     1.05x of the FP64 error.  Meshes (n^3 x 6 tets) and degrees where the
     discretisation error lies well above the FP32 rounding floor; the
-    fewer-point volume rules where tabulated (N = 2, 3, 4), else the (N+1)^3
-    rule.  'headline' names the case with the most DOF where every
-    FP32-field path but TF32 keeps equal error."""
+    fewer-point volume rules where tabulated (N = 2..5), else the (N+1)^3
+    rule.  The FP32-field paths run with plain FP32 state updates and, in
+    the '_compensated' rows, with compensated summation of the state
+    (wadg_set_compensation).  'headline' names the case with the most DOF
+    where the plain split-bf16 and FP32 paths keep equal error."""
     import torch
     from synthetic import warped_cube, standing_wave, fewer_point_rule
     out = {}
@@ -477,9 +479,12 @@ def equal_error(W, T=0.25):
         case = {"workload": f"warped cube {n}^3x6 = {len(EToV)} tets, N={N}, "
                             f"{'collapsed' if rule is None else str(len(rule[1])) + '-point'} volume rule, c^2=1, "
                             f"standing wave to T={T}, dt_max={dt_max:.3e}"}
-        for prec in ("fp64", "fp32_3xbf16", "fp32", "fp32_tf32"):
+        for name in ("fp64", "fp32_3xbf16", "fp32", "fp32_tf32", "fp32_3xbf16_compensated", "fp32_compensated"):
+            prec = name.replace("_compensated", "")
             m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
             W.wadg_set_operators(m, prec, 1, 1.0, 1.0, None)
+            if name.endswith("_compensated"):
+                W.wadg_set_compensation(m, True)
             xq = W.wadg_volume_points(m)
             f0 = torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda()
             Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
@@ -498,12 +503,12 @@ def equal_error(W, T=0.25):
             ms = a.elapsed_time(b)
             err = W.wadg_l2_error(m, Q, torch.from_numpy(standing_wave(xq, T)[:, :, None, :]).cuda(), 1)
             dof = 4 * m.K * m.Np
-            case[prec] = {"l2_error_p": err, "nsteps": nsteps, "solve_ms": ms,
+            case[name] = {"l2_error_p": err, "nsteps": nsteps, "solve_ms": ms,
                           "value": dof * 5 * nsteps / (ms * 1e-3)}
             del Q, R, f0, m
             torch.cuda.empty_cache()
         e64, v64 = case["fp64"]["l2_error_p"], case["fp64"]["value"]
-        for prec in ("fp32_3xbf16", "fp32", "fp32_tf32"):
+        for prec in ("fp32_3xbf16", "fp32", "fp32_tf32", "fp32_3xbf16_compensated", "fp32_compensated"):
             case[prec]["ratio_to_fp64"] = case[prec]["l2_error_p"] / e64
             case[prec]["equal_l2_error"] = bool(case[prec]["l2_error_p"] <= 1.05 * e64)
             case[prec]["speedup_over_fp64"] = case[prec]["value"] / v64

@@ -207,6 +207,18 @@ int wadg_set_formulation(wadg_mesh* mesh, int form);
  * is built for the pointwise weights: WADG_EUNSUPPORTED under 1. */
 int wadg_set_conservation(wadg_mesh* mesh, int on);
 
+/* Compensated summation of the state in the LSRK steps (FP32 fields; not in
+ * the paper): 1 = each stage adds b res to Q together with the rounding
+ * error carried from the previous stages (Fast2Sum into a mesh-owned buffer
+ * like Q, cleared at the start of every wadg_step / wadg_solve /
+ * wadg_step_host call), so the FP32 state no longer loses 2^-24 of its
+ * value per stage; 0 = plain FP32 updates (the default).  The stage's
+ * right-hand side reads Q only.  Costs one read and one write of a
+ * [4][K][S][Np] float array per stage.  WADG_EUNSUPPORTED for WADG_FP64
+ * (wadg_set_operators with WADG_FP64 turns it off); mesh batches and the
+ * adjoint entry points refuse compensated meshes (WADG_ESTATE). */
+int wadg_set_compensation(wadg_mesh* mesh, int on);
+
 /* wadg_step on host fields: Q and res are HOST [4][K][S][Np] arrays in the
  * mesh precision (pinned memory gives the fastest copies).  Q is copied to a
  * device buffer owned by the mesh, stepped nsteps times, and Q and res are

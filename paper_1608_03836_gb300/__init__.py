@@ -49,6 +49,7 @@ from .api import (  # noqa: E402,F401
     wadg_step_host,
     wadg_set_formulation,
     wadg_set_conservation,
+    wadg_set_compensation,
     FORMULATIONS,
     wadg_segment_adjoint,
     wadg_step_adjoint,

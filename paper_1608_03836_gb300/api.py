@@ -186,6 +186,12 @@ def wadg_set_conservation(mesh: MeshHandle, on: bool):
     _check(load().wadg_set_conservation(mesh.handle, 1 if on else 0), "wadg_set_conservation", mesh)
 
 
+def wadg_set_compensation(mesh: MeshHandle, on: bool):
+    """Compensated summation of the FP32 state in the LSRK steps (True) or
+    plain FP32 updates (False, the default); see include/wadg.h."""
+    _check(load().wadg_set_compensation(mesh.handle, 1 if on else 0), "wadg_set_compensation", mesh)
+
+
 def wadg_step_host(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, stream=None):
     """wadg_step on host tensors (CPU, contiguous, the mesh precision; pinned
     memory gives the fastest copies): Q copied in, stepped, Q and res copied

@@ -333,6 +333,10 @@ int wadg_batch_create(wadg_mesh* const* meshes, int count, wadg_batch** out) {
   for (int i = 0; i < count; ++i) {
     b->prec0.push_back(meshes[i]->precision);
     b->S0.push_back(meshes[i]->S);
+    if (meshes[i]->compensate) {  // batches step without compensation
+      delete b;
+      return WADG_ESTATE;
+    }
   }
   const int p0 = meshes[0]->precision;
   if (p0 == WADG_FP32_3XBF16 || p0 == WADG_FP32_TF32) {

@@ -516,6 +516,7 @@ void wadg_mesh_destroy(wadg_mesh* m) {
   dfree(m->d_tcops);
   dfree(m->d_vgeo_il);
   dfree(m->d_meanc);
+  dfree(m->d_Qlo);
   dfree(m->d_hostQ);
   dfree(m->d_hostR);
   dfree(m->d_fgeo_il);
@@ -818,6 +819,13 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
     WADG_CUDA(m, cudaMalloc(&m->d_Qtmp, qbytes));
     WADG_CUDA(m, cudaMalloc((void**)&m->d_red, ((size_t)K * shots + 1) * 8));
     m->qtmp_bytes = qbytes;
+    dfree(m->d_Qlo);
+  }
+  if (precision == WADG_FP64) {
+    m->compensate = 0;
+    dfree(m->d_Qlo);
+  } else if (m->compensate && !m->d_Qlo) {
+    WADG_CUDA(m, cudaMalloc(&m->d_Qlo, qbytes));
   }
   if (shots != m->S || precision != m->precision) {
     // sources and receivers depend on the shot count and precision
@@ -989,6 +997,12 @@ int step_t(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, v
   T* cur = (T*)Q;
   T* other = (T*)m->d_Qtmp;
   const size_t bytes = (size_t)4 * m->K * m->S * m->ref.Np * sizeof(T);
+  if (sizeof(T) == 4 && m->compensate && m->d_Qlo) {
+    // compensated summation of the state over this call's stages
+    cudaError_t e = cudaMemsetAsync(m->d_Qlo, 0, bytes, st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "clearing the compensation");
+    p.qlo = (T*)m->d_Qlo;
+  }
   for (int n = 0; n < nsteps; ++n) {
     const double t = t0 + n * dt;
     for (int s = 0; s < 5; ++s) {
@@ -1103,6 +1117,19 @@ int wadg_set_conservation(wadg_mesh* m, int on) {
     }
   }
   if (on != prev) ++m->generation;
+  return WADG_OK;
+}
+
+int wadg_set_compensation(wadg_mesh* m, int on) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (on != 0 && on != 1) return fail(m, WADG_EINVAL, "compensation %d (0 off, 1 on)", on);
+  if (on && m->precision == WADG_FP64) return fail(m, WADG_EUNSUPPORTED, "compensation is for FP32 fields");
+  DeviceGuard g(m->device);
+  if (on && !m->d_Qlo) WADG_CUDA(m, cudaMalloc(&m->d_Qlo, m->qtmp_bytes));
+  if (!on) dfree(m->d_Qlo);
+  if (on != m->compensate) ++m->generation;
+  m->compensate = on;
   return WADG_OK;
 }
 
@@ -1373,6 +1400,7 @@ int wadg_segment_adjoint(wadg_mesh* m, void* Q, void* res, double t0, double dt,
                          void* lamQ, void* lamR, void* ystore, double* dc2, wadg_stream stream) {
   int st = check_ready(m);
   if (st != WADG_OK) return st;
+  if (m->compensate) return fail(m, WADG_ESTATE, "the adjoint recomputes uncompensated steps: turn compensation off");
   if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
   if (!collapsed_size(m)) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the (N+1)^3-point volume rule");
   if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) return fail(m, WADG_EINVAL, "nsteps/dt/t0");
@@ -1407,6 +1435,7 @@ int wadg_step_record(wadg_mesh* m, void* Q, void* res, double t0, double dt, voi
                      wadg_stream stream) {
   int st = check_ready(m);
   if (st != WADG_OK) return st;
+  if (m->compensate) return fail(m, WADG_ESTATE, "the adjoint recomputes uncompensated steps: turn compensation off");
   if (m->form != 0) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the strong-weak formulation");
   if (!collapsed_size(m)) return fail(m, WADG_EUNSUPPORTED, "the adjoint is built for the (N+1)^3-point volume rule");
   if (m->conservative && ystore)

@@ -588,7 +588,15 @@ __device__ __forceinline__ void stage_tile(const StageParams<T>& p, int64_t blk,
             const int64_t idx = fld * fs + c * NP + m;
             const T rr = rd ? p.rk_a * rs[r][e] + p.dt * acc[r][e] : p.dt * acc[r][e];
             p.res[idx] = rr;
-            p.Qout[idx] = sQ[(fld * NP + m) * E + g * 4 + e] + p.rk_b * rr;
+            const T qi = sQ[(fld * NP + m) * E + g * 4 + e];
+            if (p.qlo) {  // compensated sum (Fast2Sum, |Q| >= |b res + carried error|)
+              const T y = p.rk_b * rr + p.qlo[idx];
+              const T q = qi + y;
+              p.qlo[idx] = (qi - q) + y;
+              p.Qout[idx] = q;
+            } else {
+              p.Qout[idx] = qi + p.rk_b * rr;
+            }
           }
         }
       }

@@ -894,9 +894,17 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
             rr.z = rd ? p.rk_a * rs[e].z + p.dt * vv[e].z : p.dt * vv[e].z;
             rr.w = rd ? p.rk_a * rs[e].w + p.dt * vv[e].w : p.dt * vv[e].w;
             reinterpret_cast<float4*>(p.res)[ix[e]] = rr;
-            reinterpret_cast<float4*>(p.Qout)[ix[e]] =
-                make_float4(qi[e].x + p.rk_b * rr.x, qi[e].y + p.rk_b * rr.y, qi[e].z + p.rk_b * rr.z,
-                            qi[e].w + p.rk_b * rr.w);
+            if (p.qlo) {
+              float4 l = reinterpret_cast<const float4*>(p.qlo)[ix[e]];
+              reinterpret_cast<float4*>(p.Qout)[ix[e]] =
+                  make_float4(lsrk_comp(qi[e].x, p.rk_b, rr.x, l.x), lsrk_comp(qi[e].y, p.rk_b, rr.y, l.y),
+                              lsrk_comp(qi[e].z, p.rk_b, rr.z, l.z), lsrk_comp(qi[e].w, p.rk_b, rr.w, l.w));
+              reinterpret_cast<float4*>(p.qlo)[ix[e]] = l;
+            } else {
+              reinterpret_cast<float4*>(p.Qout)[ix[e]] =
+                  make_float4(qi[e].x + p.rk_b * rr.x, qi[e].y + p.rk_b * rr.y, qi[e].z + p.rk_b * rr.z,
+                              qi[e].w + p.rk_b * rr.w);
+            }
           }
         }
       }
@@ -935,7 +943,13 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const TcStagePara
             if (ix[e] < 0) continue;
             const float rr = rd ? p.rk_a * rs[e] + p.dt * vv[e] : p.dt * vv[e];
             p.res[ix[e]] = rr;
-            p.Qout[ix[e]] = qi[e] + p.rk_b * rr;
+            if (p.qlo) {
+              float l = p.qlo[ix[e]];
+              p.Qout[ix[e]] = lsrk_comp(qi[e], p.rk_b, rr, l);
+              p.qlo[ix[e]] = l;
+            } else {
+              p.Qout[ix[e]] = qi[e] + p.rk_b * rr;
+            }
           }
         }
       }

@@ -58,6 +58,16 @@ constexpr uint32_t kWaitIters = 1u << 22;
 constexpr int kThreads = 512;      // four threads per column of a 128-column tile
 constexpr uint32_t kIssuers = 16;  // threads issuing tensor-core products (lane 0 of each warp)
 
+// LSRK state update with compensated summation: q = qi + (b rr + lo) and
+// the new lo = the rounding error of that sum (Fast2Sum, exact for
+// |qi| >= |b rr + lo|, which holds for a stage increment).
+__device__ __forceinline__ float lsrk_comp(float qi, float b, float rr, float& lo) {
+  const float y = fmaf(b, rr, lo);
+  const float q = qi + y;
+  lo = (qi - q) + y;
+  return q;
+}
+
 // Cooperative copy of `bytes` (multiple of 16) from global to shared memory.
 __device__ __forceinline__ void stage_copy(uint8_t* dst, const uint8_t* __restrict__ src, int bytes) {
   const uint4* s = reinterpret_cast<const uint4*>(src);

@@ -103,6 +103,9 @@ struct StageParams {
   const T* Qin = nullptr;   // [4][ncols][Np]
   T* Qout = nullptr;        // LSRK: Q + b res; may not alias Qin
   T* res = nullptr;         // LSRK: residual, read and written in place
+  // LSRK with compensated summation: the rounding error of Q_out carried to
+  // the next stage, [4][ncols][Np], read and written in place (nullptr: none)
+  T* qlo = nullptr;
   T* out = nullptr;         // RHS mode: dQ/dt
   const T* vgeo = nullptr;  // [K][11][Nq]: G_ai (a-major, 9), c^2/J, 1/J
   const T* fgeo = nullptr;  // [K][3][4 Nfq]: n J^f at the owner face points
@@ -233,6 +236,8 @@ struct wadg_mesh {
   int* d_err = nullptr;        // device error flag (bounded waits)
   int num_sms = 0;
   void* d_Qtmp = nullptr;      // ping-pong buffer for LSRK stages
+  int compensate = 0;          // 1: LSRK steps with compensated summation of the state (FP32 fields)
+  void* d_Qlo = nullptr;       // the carried rounding error of the state, like Q
   size_t qtmp_bytes = 0;
   double* d_red = nullptr;     // reduction scratch
   // sources and receivers
