@@ -87,8 +87,8 @@ def headline_rule():
     return fewer_point_rule(WORKLOAD["N"]) if WORKLOAD["N"] in (2, 3, 4, 5) else None
 
 
-TC_SOURCES = ("paper_1608_03836_gb300/csrc/stage_tc.cu", "paper_1608_03836_gb300/csrc/tc_ops.cuh",
-              "paper_1608_03836_gb300/csrc/tc_stage_common.cuh")
+TC_SOURCES = ("paper_1608_03836_gb300/csrc/stage_tc.cu", "paper_1608_03836_gb300/csrc/stage_tc_kernel.cuh",
+              "paper_1608_03836_gb300/csrc/tc_ops.cuh", "paper_1608_03836_gb300/csrc/tc_stage_common.cuh")
 TC_PROFILE = "profiles/stage_tc_kernel_63pt_n20_full.md"
 
 
@@ -572,6 +572,47 @@ def formulations(W, steps):
     return out
 
 
+def planar_study(W, steps):
+    """Planar and curved tiles in separate kernels (Sec. 6) on the headline
+    workload's tensor-core stage (N = 4, split bf16, 63-point rule,
+    heterogeneous c^2): cubes warped for z < 0 (half the elements affine,
+    half the tiles planar) and for z < -0.75 (7/8 of the tiles planar), and
+    the affine cube (every tile planar), each with the split as planned, with every all-affine tile on
+    the planar kernel, and off.  LSRK step time and one LSRK launch
+    (step / 5)."""
+    import torch
+    from synthetic import warped_cube, c2_heterogeneous, standing_wave
+    n, N = WORKLOAD["n"], WORKLOAD["N"]
+    out = {}
+    for name, planar_from, amp in (("half_planar", 0.0, WORKLOAD["warp"]),
+                                   ("mostly_planar", -0.75, WORKLOAD["warp"]), ("affine", None, 0.0)):
+        VXYZ, EToV, geom = warped_cube(n, N, amp, planar_from=planar_from)
+        m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=headline_rule())
+        xq = W.wadg_volume_points(m)
+        W.wadg_set_operators(m, "fp32_3xbf16", 1, 1.0, 1.0, c2_heterogeneous(xq))
+        fq = torch.from_numpy(standing_wave(xq, 0.0)[:, :, None, :]).cuda()
+        Q = torch.empty((4, m.K, 1, m.Np), dtype=m.dtype, device="cuda")
+        W.wadg_project(m, fq, Q)
+        del fq
+        rows = {}
+        dof = 4 * m.K * m.Np
+        for mode in ("planned", "all", "off"):
+            W.wadg_set_planar_split(m, mode)
+            tot, st = time_steps(W, m, Q, steps, 3)
+            rows[mode] = {"value": dof * 5 / (tot / steps * 1e-3), "ms_per_step": tot / steps,
+                          "stage_ms": tot / steps / 5, "rhs_launch_ms": st, "info": W.wadg_planar_info(m)}
+        W.wadg_device_status(m)
+        for mode in ("planned", "all"):
+            rows[f"time_{mode}_vs_off"] = rows[mode]["ms_per_step"] / rows["off"]["ms_per_step"]
+        out[name] = rows
+        del Q, m
+        torch.cuda.empty_cache()
+    out["workload"] = (f"Kuhn cube {n}^3x6, N={N}, fp32_3xbf16, the fewer-point rule, heterogeneous c^2; half_planar: "
+                       "warp times (z/1)^2 for z < 0, none beyond; mostly_planar: warp times ((z + 0.75)/0.25)^2 for "
+                       "z < -0.75, none beyond; affine: no warp")
+    return out
+
+
 def c2_study(W):
     """The precision configuration: warped cube 24^3 x 6 = 82,944 tets, N = 5,
     c^2 = 1, standing wave to T = 0.5, on the 96-point symmetric volume rule
@@ -867,6 +908,8 @@ def main():
                     help="run only the uneven-batch study (12 meshes, N = 2..6, large and small) and print its JSON")
     ap.add_argument("--equal-error", action="store_true",
                     help="run only the equal-L2-error comparison (FP64 vs mixed precision, whole solves) and print it")
+    ap.add_argument("--planar", action="store_true",
+                    help="run only the planar/curved kernel split study (half-planar and affine cubes) and print it")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"],
@@ -893,6 +936,10 @@ def main():
     if args.forms:
         if rank == 0:
             print(json.dumps({"formulations": formulations(W, args.steps)}))
+        return
+    if args.planar:
+        if rank == 0:
+            print(json.dumps({"planar_split": planar_study(W, max(2, args.steps))}))
         return
     if args.equal_error:
         if rank == 0:

@@ -219,6 +219,29 @@ int wadg_set_conservation(wadg_mesh* mesh, int on);
  * adjoint entry points refuse compensated meshes (WADG_ESTATE). */
 int wadg_set_compensation(wadg_mesh* mesh, int on);
 
+/* Planar and curved elements in separate tensor-core kernels (Sec. 6: planar
+ * elements admit a cheaper implementation; N <= 4): an element is affine when
+ * its geometry nodes are its vertices' affine lattice map (to 1e-13 of its
+ * extent; every element when wadg_mesh_create got no nodes).  A tile of 128
+ * columns whose elements are all affine may run a kernel that reads each
+ * element's constant geometric factors and normals once instead of at every
+ * quadrature point (the update weights c^2/J stay per point); the curved
+ * kernel runs the other tiles, one launch after the other in the stage.
+ * on = 1 (the default) plans the split from the tile counts: the planar
+ * launch takes the all-affine tiles less those that would open a partial
+ * round of its CTAs, and only when the rounds saved outweigh a second
+ * launch (so meshes of fewer tiles than SMs stay on one launch); on = 2 runs
+ * every all-affine tile on the planar kernel; on = 0 runs every tile on the
+ * curved kernel.  Results equal the curved kernel's to rounding.  The lists
+ * are built by wadg_set_operators (tensor-core precisions).  WADG_EINVAL for
+ * other values of on. */
+int wadg_set_planar_split(wadg_mesh* mesh, int on);
+
+/* info[0..3] = affine elements, tiles of affine elements, tiles, tiles the
+ * planar kernel runs (the last three are 0 until wadg_set_operators selects
+ * a tensor-core precision with N <= 4 and some tile is all affine). */
+int wadg_planar_info(const wadg_mesh* mesh, int64_t info[4]);
+
 /* wadg_step on host fields: Q and res are HOST [4][K][S][Np] arrays in the
  * mesh precision (pinned memory gives the fastest copies).  Q is copied to a
  * device buffer owned by the mesh, stepped nsteps times, and Q and res are

@@ -50,6 +50,8 @@ from .api import (  # noqa: E402,F401
     wadg_set_formulation,
     wadg_set_conservation,
     wadg_set_compensation,
+    wadg_set_planar_split,
+    wadg_planar_info,
     FORMULATIONS,
     wadg_segment_adjoint,
     wadg_step_adjoint,

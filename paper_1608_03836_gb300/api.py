@@ -192,6 +192,24 @@ def wadg_set_compensation(mesh: MeshHandle, on: bool):
     _check(load().wadg_set_compensation(mesh.handle, 1 if on else 0), "wadg_set_compensation", mesh)
 
 
+PLANAR_SPLIT = {False: 0, True: 1, "off": 0, "planned": 1, "all": 2}
+
+
+def wadg_set_planar_split(mesh: MeshHandle, on=True):
+    """Tiles of affine elements on the planar tensor-core kernel: True or
+    "planned" (the default: as the tile counts pay), "all" (every all-affine
+    tile), False or "off" (every tile on the curved kernel); see
+    include/wadg.h."""
+    mode = PLANAR_SPLIT[on] if isinstance(on, (bool, str)) else int(on)
+    _check(load().wadg_set_planar_split(mesh.handle, mode), "wadg_set_planar_split", mesh)
+
+
+def wadg_planar_info(mesh: MeshHandle) -> dict:
+    info = (ctypes.c_int64 * 4)()
+    _check(load().wadg_planar_info(mesh.handle, info), "wadg_planar_info", mesh)
+    return {"affine_elements": info[0], "planar_tiles": info[1], "tiles": info[2], "planar_launch_tiles": info[3]}
+
+
 def wadg_step_host(mesh: MeshHandle, Q, res, t0: float, dt: float, nsteps: int, stream=None):
     """wadg_step on host tensors (CPU, contiguous, the mesh precision; pinned
     memory gives the fastest copies): Q copied in, stepped, Q and res copied

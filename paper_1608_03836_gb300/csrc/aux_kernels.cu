@@ -180,6 +180,29 @@ cudaError_t launch_to_precision(int64_t n, const double* in, T* out, cudaStream_
 template cudaError_t launch_to_precision<float>(int64_t, const double*, float*, cudaStream_t);
 template cudaError_t launch_to_precision<double>(int64_t, const double*, double*, cudaStream_t);
 
+// Compact geometry of affine elements (constant G and n J^f): the values at
+// the first volume and face point, interleaved over 128 elements,
+// gP[(k >> 7) * 9 + a i][k & 127], nP[(k >> 7) * 12 + d * 4 + f][k & 127].
+__global__ void geo_planar_pack_kernel(int64_t K, int Nq, int Nfq, const double* __restrict__ G,
+                                       const double* __restrict__ nJ, float* __restrict__ gP, float* __restrict__ nP) {
+  const int64_t Kt = (K + 127) / 128;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < Kt * 128 * 21;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int kl = (int)(it & 127);
+    const int64_t rest = it >> 7;
+    const int row = (int)(rest % 21);
+    const int64_t k = (rest / 21) * 128 + kl;
+    if (row < 9) gP[((k >> 7) * 9 + row) * 128 + kl] = k < K ? (float)G[(k * 9 + row) * Nq] : 0.f;
+    else nP[((k >> 7) * 12 + row - 9) * 128 + kl] = k < K ? (float)nJ[k * 12 * Nfq + (row - 9) * Nfq] : 0.f;
+  }
+}
+
+cudaError_t launch_geo_planar_pack(int64_t K, int Nq, int Nfq, const double* G, const double* nJ, float* gP, float* nP,
+                                   cudaStream_t st) {
+  geo_planar_pack_kernel<<<1024, 256, 0, st>>>(K, Nq, Nfq, G, nJ, gP, nP);
+  return cudaGetLastError();
+}
+
 __global__ void fill_kernel(int64_t n, double v, double* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = v;

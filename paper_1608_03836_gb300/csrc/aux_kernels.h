@@ -26,6 +26,10 @@ template <typename T>
 cudaError_t launch_to_precision(int64_t n, const double* in, T* out, cudaStream_t st);
 // out[i] = v, i < n.
 cudaError_t launch_fill(int64_t n, double v, double* out, cudaStream_t st);
+// Constant G [K][9][Nq] and n J^f [K][12][Nfq] of affine elements, compact and
+// interleaved over 128 elements: gP [Kt][9][128], nP [Kt][12][128].
+cudaError_t launch_geo_planar_pack(int64_t K, int Nq, int Nfq, const double* G, const double* nJ, float* gP, float* nP,
+                                   cudaStream_t st);
 template <typename T>
 cudaError_t launch_project(int64_t ncols, int S, int Np, int Nq, const double* fq, const double* J, const double* Vq,
                            const double* Pq, T* Q, cudaStream_t st);

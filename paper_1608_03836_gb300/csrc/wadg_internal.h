@@ -157,8 +157,17 @@ struct TcStageParams {
   // fields less their element means, and the epilogue adds sum_i ubar_i D_i
   const float* meanc = nullptr;
   int64_t meanc_stride = 0;
+  // the tiles to walk (nullptr: all): the list of tiles whose elements are
+  // all affine, or of the others; compact geometry of the affine elements,
+  // interleaved over 128 elements: G [Kt][9][128], n J^f [Kt][12][128]
+  const int32_t* tiles = nullptr;
+  int64_t ntiles_list = 0;
+  const float* gP = nullptr;
+  const float* nP = nullptr;
 };
 cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
+// The same over the tiles of P.tiles whose elements are all affine (N <= 4).
+cudaError_t launch_stage_tc_planar(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
 bool pack_tc_ops(int N, const RefOps& o, int fmt, std::vector<uint8_t>& out);
 // N = 5 (stage_tc5.cu), the collapsed 216-point volume rule.
 cudaError_t launch_stage_tc5(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
@@ -194,6 +203,14 @@ struct wadg_mesh {
   std::vector<uint8_t> fcode;  // [K][4]
   std::vector<uint8_t> owner;  // [K][4] 1 if this element owns the face
   std::vector<double> geom;    // [K][Np][3]
+  std::vector<uint8_t> affine;  // [K] 1: the element's geometry nodes are its vertices' affine map
+  int64_t n_affine = 0;
+  int planar_split = 1;          // 0 off, 1 planned (the default), 2 every all-affine tile (wadg_set_planar_split)
+  int32_t* d_tlist = nullptr;    // the planar tiles, then the others (tensor-core stage, N <= 4)
+  int64_t n_planar_tiles = 0, n_curved_tiles = 0;
+  float* d_gP = nullptr;         // compact geometry of the affine elements (see TcStageParams)
+  float* d_nP = nullptr;
+  int64_t n_planar_launch = 0;   // tiles the planar kernel runs (the head of d_tlist)
   // device geometry (FP64)
   double* d_X = nullptr;       // [K][Np][3]
   double* d_J = nullptr;       // [K][Nq]

@@ -108,21 +108,31 @@ def warp_displacement(x: np.ndarray, amplitude: float) -> np.ndarray:
     return d
 
 
-def geometry_nodes(VXYZ, EToV, N: int, amplitude: float) -> np.ndarray:
-    """Physical coordinates of each element's equispaced lattice, warped; (K, Np, 3)."""
+def geometry_nodes(VXYZ, EToV, N: int, amplitude: float, planar_from: float | None = None) -> np.ndarray:
+    """Physical coordinates of each element's equispaced lattice, warped; (K, Np, 3).
+
+    planar_from = z0: the warp is multiplied by ((z0 - z) / (1 + z0))^2 for
+    z < z0 and by 0 beyond (C^1 across z = z0), so that the elements with
+    z >= z0 stay affine: a mesh of curved and planar elements.  z is the
+    slowest axis of the element order, so the affine elements come last."""
     rst = lattice_tet(N)
     lam = np.stack([-(1.0 + rst.sum(1)) / 2, (1 + rst[:, 0]) / 2,
                     (1 + rst[:, 1]) / 2, (1 + rst[:, 2]) / 2], axis=1)  # (Np, 4)
     x = np.einsum("nv,kvd->knd", lam, VXYZ[EToV])
     if amplitude != 0.0:
-        x = x + warp_displacement(x, amplitude)
+        d = warp_displacement(x, amplitude)
+        if planar_from is not None:
+            x0 = float(planar_from)
+            d = d * (np.minimum(x[..., 2] - x0, 0.0) / (1.0 + x0))[..., None] ** 2
+        x = x + d
     return np.ascontiguousarray(x)
 
 
-def warped_cube(n: int, N: int, amplitude: float = 0.1):
-    """(VXYZ, EToV, geom_xyz) of the warped Kuhn cube."""
+def warped_cube(n: int, N: int, amplitude: float = 0.1, planar_from: float | None = None):
+    """(VXYZ, EToV, geom_xyz) of the warped Kuhn cube; planar_from: see
+    geometry_nodes (a cube curved for z < z0 and planar beyond)."""
     VXYZ, EToV = kuhn_cube(n)
-    return VXYZ, EToV, geometry_nodes(VXYZ, EToV, N, amplitude)
+    return VXYZ, EToV, geometry_nodes(VXYZ, EToV, N, amplitude, planar_from)
 
 
 def standing_wave(x: np.ndarray, t: float):
