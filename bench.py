@@ -572,7 +572,7 @@ def formulations(W, steps):
     return out
 
 
-def planar_study(W, steps):
+def planar_study(W, steps, meshes=("half_planar", "mostly_planar", "affine")):
     """Planar and curved tiles in separate kernels (Sec. 6) on the headline
     workload's tensor-core stage (N = 4, split bf16, 63-point rule,
     heterogeneous c^2): cubes warped for z < 0 (half the elements affine,
@@ -586,6 +586,8 @@ def planar_study(W, steps):
     out = {}
     for name, planar_from, amp in (("half_planar", 0.0, WORKLOAD["warp"]),
                                    ("mostly_planar", -0.75, WORKLOAD["warp"]), ("affine", None, 0.0)):
+        if name not in meshes:
+            continue
         VXYZ, EToV, geom = warped_cube(n, N, amp, planar_from=planar_from)
         m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=headline_rule())
         xq = W.wadg_volume_points(m)
@@ -910,6 +912,8 @@ def main():
                     help="run only the equal-L2-error comparison (FP64 vs mixed precision, whole solves) and print it")
     ap.add_argument("--planar", action="store_true",
                     help="run only the planar/curved kernel split study (half-planar and affine cubes) and print it")
+    ap.add_argument("--planar-meshes", default="half_planar,mostly_planar,affine",
+                    help="meshes of the planar study (comma-separated subset of half_planar, mostly_planar, affine)")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="hexahedra per cube side (default: the headline workload; smaller for profiling)")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"],
@@ -939,7 +943,7 @@ def main():
         return
     if args.planar:
         if rank == 0:
-            print(json.dumps({"planar_split": planar_study(W, max(2, args.steps))}))
+            print(json.dumps({"planar_split": planar_study(W, max(2, args.steps), args.planar_meshes.split(","))}))
         return
     if args.equal_error:
         if rank == 0:
