@@ -160,3 +160,87 @@ def test_split_steps_match_oracle_and_replay(W):
         l2, mx = rel_errors(Qt.double().cpu().numpy()[:, :, s], om.ref.to_nodal(c))
         assert l2 < TOL["fp32_3xbf16"] and mx < 10 * TOL["fp32_3xbf16"], (s, l2, mx)
 
+
+
+def test_split_with_sources_receivers_and_compensation_matches_oracle(W):
+    """Two shots on the half-planar cube, one Ricker point source in an
+    affine element (z > 0) and one in a curved element, three receivers per
+    shot, compensated state updates, every affine tile on the planar kernel:
+    four LSRK steps from rest against the oracle's."""
+    import torch
+    from gpu_util import TRACE_FACTOR
+    from oracle import sources as OS
+    from oracle import wadg as OW
+    from synthetic import ricker, receiver_positions
+    N, S, R = 3, 2, 3
+    VXYZ, EToV, geom = _half_planar(4, N)
+    om = oracle_case(VXYZ, EToV, geom, N)
+    m = library_mesh(VXYZ, EToV, geom, N, "fp32_3xbf16", shots=S)
+    W.wadg_set_planar_split(m, "all")
+    W.wadg_set_compensation(m, True)
+    assert W.wadg_planar_info(m)["planar_launch_tiles"] > 0
+    xs = np.array([[0.11, -0.23, 0.42], [-0.31, 0.17, -0.46]])
+    xr = receiver_positions(S * R).reshape(S, R, 3)
+    f0, t0 = 5.0, 0.05
+    W.wadg_set_sources(m, xs, f0, t0)
+    W.wadg_set_receivers(m, xr)
+    dt, nsteps = 2e-3, 4
+    Q = torch.zeros((4, m.K, S, m.Np), dtype=m.dtype, device="cuda")
+    Rt = torch.zeros_like(Q)
+    traces = torch.zeros((nsteps, S, R), dtype=m.dtype, device="cuda")
+    W.wadg_step(m, Q, Rt, 0.0, dt, nsteps, traces)
+    W.wadg_device_status(m)
+    got_Q = Q.double().cpu().numpy()
+    got_tr = traces.double().cpu().numpy()
+    src = OS.PointSet(om, xs)
+    rec = OS.PointSet(om, xr.reshape(-1, 3))
+    for s in range(S):
+        c = np.zeros((4, om.K, om.ref.Np))
+        res = np.zeros_like(c)
+        want_tr = []
+        L = lambda q, t: OW.wadg_apply(om, OW.a_h(om, q) + OS.source_load(om, src, float(ricker(t, f0, t0)), s))
+        for n in range(nsteps):
+            c, res = OW.lsrk_step(L, c, res, n * dt, dt)
+            want_tr.append(OS.sample(c[0], rec, np.arange(s * R, (s + 1) * R)))
+        l2, _ = rel_errors(got_Q[:, :, s], om.ref.to_nodal(c))
+        l2t, _ = rel_errors(got_tr[:, s], np.array(want_tr))
+        assert l2 < TOL["fp32_3xbf16"] and l2t < TRACE_FACTOR * TOL["fp32_3xbf16"], (s, l2, l2t)
+
+
+def test_planned_split_full_size_sampled(W):
+    """The headline size with 7/8 of its tiles affine: 196,608 tets curved
+    for z < -0.75, N = 4, the 63-point rule, heterogeneous c^2, split bf16,
+    the planned split (1,232 tiles on the planar kernel on 152 SMs); 48
+    sampled columns (the first and last element, boundary elements, random
+    ones, and elements of the planar launch, of the moved affine tiles and
+    at the curved/affine interface) against the oracle's RHS evaluated on
+    each column's neighbourhood."""
+    import torch
+    from gpu_util import sample_columns, sampled_oracle_rhs
+    from synthetic import c2_heterogeneous, fewer_point_rule, random_fields
+    N = 4
+    rule = fewer_point_rule(N)
+    VXYZ, EToV, geom = warped_cube(32, N, 0.1, planar_from=-0.75)
+    m = W.wadg_mesh_create(N, VXYZ, EToV, geom, rule=rule)
+    W.wadg_set_operators(m, "fp32_3xbf16", 1, 1.0, 1.0, c2_heterogeneous(W.wadg_volume_points(m)))
+    info = W.wadg_planar_info(m)
+    nc = info["tiles"] - info["planar_tiles"]
+    npl = info["planar_launch_tiles"]
+    assert npl > 0 and info["planar_tiles"] == 1344, info
+    Q = random_fields((4, m.K, 1, m.Np), 777)
+    Qt = to_torch(Q, m.dtype)
+    out = torch.empty_like(Qt)
+    W.wadg_rhs(m, Qt, out)
+    W.wadg_device_status(m)
+    got = out.double().cpu().numpy()
+    cols = sample_columns(EToV, 1, 32, 17)
+    rng = np.random.default_rng(18)
+    # planar launch: tiles [nc, nc + npl); moved affine tiles: [nc + npl, tiles); interface: tile nc
+    extra = list(rng.integers(nc * 128, (nc + npl) * 128, 6)) + list(rng.integers((nc + npl) * 128, m.K, 4))
+    extra += list(range(nc * 128 - 3, nc * 128 + 3))
+    cols += [(int(k), 0) for k in extra]
+    want = sampled_oracle_rhs(VXYZ, EToV, geom, N, Q, cols, c2fun=c2_heterogeneous, rule=rule)
+    g = np.stack([got[:, k, s] for k, s in cols], 1)
+    l2, mx = rel_errors(g, want)
+    print(f"planned split at full size: {len(cols)} sampled columns, rel L2 {l2:.3e}, max {mx:.3e}")
+    assert l2 < TOL["fp32_3xbf16"] and mx < 10 * TOL["fp32_3xbf16"]
