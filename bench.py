@@ -456,6 +456,18 @@ def accuracy(W):
 EQUAL_ERROR_CASES = ((32, 2), (16, 3), (24, 3), (8, 4), (12, 4))
 
 
+def best_at_equal_error(case):
+    """The fastest FP32-field path of one equal-error case that keeps the
+    FP64 error (within 1.05x), with its speed-up over FP64; None when no path
+    does."""
+    ok = [(v["speedup_over_fp64"], k) for k, v in case.items()
+          if isinstance(v, dict) and v.get("equal_l2_error")]
+    if not ok:
+        return None
+    sp, k = max(ok)
+    return {"variant": k, "speedup_over_fp64": sp, "ratio_to_fp64": case[k]["ratio_to_fp64"]}
+
+
 def equal_error(W, T=0.25):
     """The headline comparison: plain FP64 against the mixed-precision paths
     on the same mesh, N, data (standing wave, c^2 = 1), dt and number of
@@ -513,6 +525,7 @@ def equal_error(W, T=0.25):
             case[prec]["equal_l2_error"] = bool(case[prec]["l2_error_p"] <= 1.05 * e64)
             case[prec]["speedup_over_fp64"] = case[prec]["value"] / v64
         case["dof"] = 4 * len(EToV) * (N + 1) * (N + 2) * (N + 3) // 6
+        case["best_at_equal_error"] = best_at_equal_error(case)
         out[f"n{n}_N{N}"] = case
     eq = [k for k, c in out.items() if c["fp32_3xbf16"]["equal_l2_error"] and c["fp32"]["equal_l2_error"]]
     if eq:
