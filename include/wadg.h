@@ -208,16 +208,29 @@ int wadg_set_formulation(wadg_mesh* mesh, int form);
 int wadg_set_conservation(wadg_mesh* mesh, int on);
 
 /* Compensated summation of the state in the LSRK steps (FP32 fields; not in
- * the paper): 1 = each stage adds b res to Q together with the rounding
- * error carried from the previous stages (Fast2Sum into a mesh-owned buffer
- * like Q, cleared at the start of every wadg_step / wadg_solve /
- * wadg_step_host call), so the FP32 state no longer loses 2^-24 of its
- * value per stage; 0 = plain FP32 updates (the default).  The stage's
- * right-hand side reads Q only.  Costs one read and one write of a
- * [4][K][S][Np] float array per stage.  WADG_EUNSUPPORTED for WADG_FP64
- * (wadg_set_operators with WADG_FP64 turns it off); mesh batches and the
- * adjoint entry points refuse compensated meshes (WADG_ESTATE). */
+ * the paper): each stage adds b res to Q together with the rounding error
+ * carried from the previous stages (Fast2Sum into a mesh-owned [4][K][S][Np]
+ * float buffer, the carry), so the FP32 state no longer loses 2^-24 of its
+ * value per stage.  on = 1: the carry is cleared at the start of every
+ * wadg_step / wadg_solve / wadg_step_host call (a call's result depends on
+ * its inputs only); on = 2: the carry is kept from one call to the next, so
+ * that a run split into several calls equals one call bit for bit (clear it
+ * by calling wadg_set_compensation again, or save and restore it with
+ * wadg_compensation_carry beside a checkpoint of Q and res, when the state
+ * is replaced between calls); 0 = plain FP32 updates (the default).  Every
+ * call with on != 0 clears the carry (synchronously).  The stage's
+ * right-hand side reads Q only.  Costs one read and one write of the carry
+ * per stage.  WADG_EUNSUPPORTED for WADG_FP64 (wadg_set_operators with
+ * WADG_FP64 turns it off); mesh batches and the adjoint entry points refuse
+ * compensated meshes (WADG_ESTATE); WADG_EINVAL for other values of on. */
 int wadg_set_compensation(wadg_mesh* mesh, int on);
+
+/* The compensation carry to (direction 0) or from (direction 1) lo, a host
+ * or device buffer of 4 K S Np floats (the layout of Q), for checkpoints of
+ * compensated runs (on = 2).  Enqueued on stream; returns after the copy has
+ * completed.  WADG_ESTATE when compensation is off; WADG_EINVAL for a null
+ * buffer or another direction. */
+int wadg_compensation_carry(wadg_mesh* mesh, void* lo, int direction, wadg_stream stream);
 
 /* Planar and curved elements in separate tensor-core kernels (Sec. 6: planar
  * elements admit a cheaper implementation; N <= 4): an element is affine when

@@ -50,6 +50,7 @@ from .api import (  # noqa: E402,F401
     wadg_set_formulation,
     wadg_set_conservation,
     wadg_set_compensation,
+    wadg_compensation_carry,
     wadg_set_planar_split,
     wadg_planar_info,
     FORMULATIONS,

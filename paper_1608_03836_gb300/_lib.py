@@ -29,6 +29,7 @@ SIGNATURES = {
     "wadg_set_formulation": (c_int, [c_void_p, c_int]),
     "wadg_set_conservation": (c_int, [c_void_p, c_int]),
     "wadg_set_compensation": (c_int, [c_void_p, c_int]),
+    "wadg_compensation_carry": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
     "wadg_set_planar_split": (c_int, [c_void_p, c_int]),
     "wadg_planar_info": (c_int, [c_void_p, c_void_p]),
     "wadg_step_host": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_double, ctypes.c_double, c_int, c_void_p]),

@@ -186,10 +186,22 @@ def wadg_set_conservation(mesh: MeshHandle, on: bool):
     _check(load().wadg_set_conservation(mesh.handle, 1 if on else 0), "wadg_set_conservation", mesh)
 
 
-def wadg_set_compensation(mesh: MeshHandle, on: bool):
-    """Compensated summation of the FP32 state in the LSRK steps (True) or
-    plain FP32 updates (False, the default); see include/wadg.h."""
-    _check(load().wadg_set_compensation(mesh.handle, 1 if on else 0), "wadg_set_compensation", mesh)
+def wadg_set_compensation(mesh: MeshHandle, on=True):
+    """Compensated summation of the FP32 state in the LSRK steps: True or 1
+    (the carry cleared at every call), 2 (the carry kept across calls), False
+    or 0 (plain FP32 updates, the default); see include/wadg.h."""
+    _check(load().wadg_set_compensation(mesh.handle, int(on)), "wadg_set_compensation", mesh)
+
+
+def wadg_compensation_carry(mesh: MeshHandle, lo, store: bool, stream=None):
+    """Copy the compensation carry into lo (store=True) or from lo into the
+    mesh (store=False); lo is a float32 tensor of the shape of Q, on the host
+    or the device."""
+    import torch
+    if lo.dtype != torch.float32 or lo.numel() != 4 * mesh.K * mesh.S * mesh.Np or not lo.is_contiguous():
+        raise ValueError("lo must be a contiguous float32 tensor of 4*K*S*Np values")
+    _check(load().wadg_compensation_carry(mesh.handle, ctypes.c_void_p(lo.data_ptr()), 0 if store else 1,
+                                          _stream(stream)), "wadg_compensation_carry", mesh)
 
 
 PLANAR_SPLIT = {False: 0, True: 1, "off": 0, "planned": 1, "all": 2}

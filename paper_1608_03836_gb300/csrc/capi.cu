@@ -858,6 +858,7 @@ int wadg_set_operators(wadg_mesh* m, int precision, int shots, double tau_p, dou
     dfree(m->d_Qlo);
   } else if (m->compensate && !m->d_Qlo) {
     WADG_CUDA(m, cudaMalloc(&m->d_Qlo, qbytes));
+    WADG_CUDA(m, cudaMemset(m->d_Qlo, 0, qbytes));
   }
   if (shots != m->S || precision != m->precision) {
     // sources and receivers depend on the shot count and precision
@@ -1108,9 +1109,12 @@ int step_t(wadg_mesh* m, void* Q, void* res, double t0, double dt, int nsteps, v
   T* other = (T*)m->d_Qtmp;
   const size_t bytes = (size_t)4 * m->K * m->S * m->ref.Np * sizeof(T);
   if (sizeof(T) == 4 && m->compensate && m->d_Qlo) {
-    // compensated summation of the state over this call's stages
-    cudaError_t e = cudaMemsetAsync(m->d_Qlo, 0, bytes, st);
-    if (e != cudaSuccess) return cuda_fail(m, e, "clearing the compensation");
+    // compensated summation of the state: mode 1 carries the rounding error
+    // over this call's stages, mode 2 also from the previous call's
+    if (m->compensate == 1) {
+      cudaError_t e = cudaMemsetAsync(m->d_Qlo, 0, bytes, st);
+      if (e != cudaSuccess) return cuda_fail(m, e, "clearing the compensation");
+    }
     p.qlo = (T*)m->d_Qlo;
   }
   for (int n = 0; n < nsteps; ++n) {
@@ -1233,14 +1237,28 @@ int wadg_set_conservation(wadg_mesh* m, int on) {
 int wadg_set_compensation(wadg_mesh* m, int on) {
   int st = check_ready(m);
   if (st != WADG_OK) return st;
-  if (on != 0 && on != 1) return fail(m, WADG_EINVAL, "compensation %d (0 off, 1 on)", on);
+  if (on < 0 || on > 2) return fail(m, WADG_EINVAL, "compensation %d (0 off, 1 per call, 2 across calls)", on);
   if (on && m->precision == WADG_FP64) return fail(m, WADG_EUNSUPPORTED, "compensation is for FP32 fields");
   DeviceGuard g(m->device);
   if (on && !m->d_Qlo) WADG_CUDA(m, cudaMalloc(&m->d_Qlo, m->qtmp_bytes));
+  if (on) WADG_CUDA(m, cudaMemset(m->d_Qlo, 0, m->qtmp_bytes));  // every call starts a zero carry
   if (!on) dfree(m->d_Qlo);
   if (on != m->compensate) ++m->generation;
   m->compensate = on;
   return WADG_OK;
+}
+
+int wadg_compensation_carry(wadg_mesh* m, void* lo, int direction, wadg_stream stream) {
+  int st = check_ready(m);
+  if (st != WADG_OK) return st;
+  if (!lo || (direction != 0 && direction != 1)) return fail(m, WADG_EINVAL, "carry buffer or direction");
+  if (!m->compensate || !m->d_Qlo) return fail(m, WADG_ESTATE, "compensation is off");
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = direction == 0 ? cudaMemcpyAsync(lo, m->d_Qlo, m->qtmp_bytes, cudaMemcpyDefault, s)
+                                 : cudaMemcpyAsync(m->d_Qlo, lo, m->qtmp_bytes, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? WADG_OK : cuda_fail(m, e, "copying the compensation carry");
 }
 
 int wadg_set_planar_split(wadg_mesh* m, int on) {

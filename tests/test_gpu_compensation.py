@@ -98,3 +98,75 @@ def test_compensation_refusals(W):
     W.wadg_set_compensation(m, False)
     W.wadg_step_record(m, Q, torch.zeros_like(Q), 0.0, 1e-3)
     W.wadg_device_status(m)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_3xbf16"])
+def test_carry_across_calls_resumes_bit_for_bit(W, precision):
+    """With the carry kept across calls (mode 2), six steps in one call equal
+    three steps, a checkpoint of (Q, res, carry) on the host, and three more
+    steps on a new mesh restored from it, bit for bit (dt a power of two, so
+    the resumed start time is the same double).  With the carry cleared per
+    call (mode 1) the split run differs from the single call."""
+    import torch
+    N, S = 3, 2
+    VXYZ, EToV, geom = make_mesh_inputs(2, N)
+    Q0 = random_Q(48, S, 20, seed=83)
+    dt = 2.0 ** -9
+
+    def mesh(mode):
+        m = library_mesh(VXYZ, EToV, geom, N, precision, shots=S)
+        W.wadg_set_compensation(m, mode)
+        return m
+
+    m = mesh(2)
+    Qa = to_torch(Q0, torch.float32)
+    Ra = torch.zeros_like(Qa)
+    W.wadg_step(m, Qa, Ra, 0.0, dt, 6)
+    # first half, checkpoint to the host
+    m1 = mesh(2)
+    Qb = to_torch(Q0, torch.float32)
+    Rb = torch.zeros_like(Qb)
+    W.wadg_step(m1, Qb, Rb, 0.0, dt, 3)
+    lo = torch.empty(Qb.shape, dtype=torch.float32).pin_memory()
+    W.wadg_compensation_carry(m1, lo, store=True)
+    assert float(lo.abs().max()) > 0.0
+    ck = (Qb.cpu(), Rb.cpu(), lo.clone())
+    W.wadg_device_status(m1)
+    # resume on a new mesh
+    m2 = mesh(2)
+    Qc, Rc = ck[0].cuda(), ck[1].cuda()
+    W.wadg_compensation_carry(m2, ck[2], store=False)
+    W.wadg_step(m2, Qc, Rc, 3 * dt, dt, 3)
+    torch.cuda.synchronize()
+    W.wadg_device_status(m2)
+    assert torch.equal(Qc, Qa) and torch.equal(Rc, Ra)
+    # the same split with the carry cleared per call
+    m3 = mesh(1)
+    Qd = to_torch(Q0, torch.float32)
+    Rd = torch.zeros_like(Qd)
+    W.wadg_step(m3, Qd, Rd, 0.0, dt, 3)
+    W.wadg_step(m3, Qd, Rd, 3 * dt, dt, 3)
+    torch.cuda.synchronize()
+    assert not torch.equal(Qd, Qa)
+    assert float((Qd - Qa).abs().max()) < 1e-5 * float(Qa.abs().max())
+    # a captured solve in mode 2 continues from the carry as the steps do
+    m4 = mesh(2)
+    Qe = to_torch(Q0, torch.float32)
+    Re = torch.zeros_like(Qe)
+    assert W.wadg_solve(m4, Qe, Re, 0.0, 3 * dt, dt) == 3
+    W.wadg_step(m4, Qe, Re, 3 * dt, dt, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(Qe, Qa)
+
+
+def test_carry_refusals(W):
+    import torch
+    VXYZ, EToV, geom = make_mesh_inputs(1, 3)
+    m = library_mesh(VXYZ, EToV, geom, 3, "fp32")
+    lo = torch.zeros((4, m.K, 1, m.Np), dtype=torch.float32)
+    with pytest.raises(W.WadgError) as e:
+        W.wadg_compensation_carry(m, lo, store=True)
+    assert e.value.status == -5
+    with pytest.raises(W.WadgError) as e:
+        W.wadg_set_compensation(m, 3)
+    assert e.value.status == -1
