@@ -233,7 +233,7 @@ int wadg_set_compensation(wadg_mesh* mesh, int on);
 int wadg_compensation_carry(wadg_mesh* mesh, void* lo, int direction, wadg_stream stream);
 
 /* Planar and curved elements in separate tensor-core kernels (Sec. 6: planar
- * elements admit a cheaper implementation; N <= 4): an element is affine when
+ * elements admit a cheaper implementation; N <= 5): an element is affine when
  * its geometry nodes are its vertices' affine lattice map (to 1e-13 of its
  * extent; every element when wadg_mesh_create got no nodes).  A tile of 128
  * columns whose elements are all affine may run a kernel that reads each
@@ -252,7 +252,7 @@ int wadg_set_planar_split(wadg_mesh* mesh, int on);
 
 /* info[0..3] = affine elements, tiles of affine elements, tiles, tiles the
  * planar kernel runs (the last three are 0 until wadg_set_operators selects
- * a tensor-core precision with N <= 4 and some tile is all affine). */
+ * a tensor-core precision with N <= 5 and some tile is all affine). */
 int wadg_planar_info(const wadg_mesh* mesh, int64_t info[4]);
 
 /* wadg_step on host fields: Q and res are HOST [4][K][S][Np] arrays in the

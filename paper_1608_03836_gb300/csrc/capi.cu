@@ -961,13 +961,16 @@ int mean_correction(wadg_mesh* m) {
 // How many of the all-affine tiles the planar kernel runs; the rest join the
 // curved launch (the curved kernel takes any tile).  Each launch's CTAs (one
 // per SM) walk its tiles in rounds, so a launch costs ceil(tiles / SMs)
-// rounds of its kernel; a planar tile takes about 0.86 of a curved one and a
-// second launch in the stage about 0.7 of a curved round (N = 4, 196,608
-// tets, 1,536 tiles: 0.499 ms per stage all planar, 0.578 all curved, 0.577
-// with 760 planar tiles after 776 curved ones, against 0.542 from the rounds
-// alone).  The cheapest split wins, ties going to the larger curved launch
-// (a single launch when nothing is saved).  Mode 2 runs every all-affine tile
-// on the planar kernel.
+// rounds of its kernel; a planar tile takes a fraction of a curved one and a
+// second launch in the stage adds a ramp, both measured in curved rounds:
+// N = 4 (196,608 tets, 1,536 tiles, 52 us rounds): planar 0.86 (0.499 ms per
+// stage all planar, 0.578 all curved), second launch 0.7 (0.577 ms with 760
+// planar tiles after 776 curved ones against 0.542 from the rounds alone);
+// N = 5 (82,944 tets, 648 tiles, 118 us rounds): planar 0.91 (0.534 vs
+// 0.589 ms), second launch 0.2 (0.568 ms with 567 planar tiles after 81
+// curved ones against 0.545).  N <= 3 takes the N = 4 values.  The cheapest
+// split wins, ties going to the larger curved launch (a single launch when
+// nothing is saved).  Mode 2 runs every all-affine tile on the planar kernel.
 void plan_planar_launch(wadg_mesh* m) {
   const int64_t np = m->n_planar_tiles, nc = m->n_curved_tiles, G = std::max(1, m->num_sms);
   m->n_planar_launch = 0;
@@ -976,7 +979,7 @@ void plan_planar_launch(wadg_mesh* m) {
     m->n_planar_launch = np;
     return;
   }
-  const double planar_cost = 0.86, second_launch = 0.7;
+  const double planar_cost = m->N == 5 ? 0.91 : 0.86, second_launch = m->N == 5 ? 0.2 : 0.7;
   auto rounds = [&](int64_t n) { return (double)((n + G - 1) / G); };
   double best = 1e300;
   for (int64_t mv = np; mv >= 0; --mv) {
@@ -999,7 +1002,7 @@ int planar_tiles(wadg_mesh* m, int shots) {
   dfree(m->d_gP);
   dfree(m->d_nP);
   m->n_planar_tiles = m->n_curved_tiles = m->n_planar_launch = 0;
-  if (m->N > 4 || m->n_affine == 0) return WADG_OK;
+  if (m->N > 5 || m->n_affine == 0) return WADG_OK;
   const int64_t ncols = m->K * shots, ntiles = (ncols + 127) / 128;
   std::vector<int32_t> planar, curved;
   for (int64_t t = 0; t < ntiles; ++t) {
@@ -1053,7 +1056,7 @@ cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p,
     // of a tile starts 16-byte aligned in every field array the stage touches
     auto a16 = [](const void* q) { return ((uintptr_t)q & 15) == 0; };
     P.bulk_q = (p.ncols * m->ref.Np) % 4 == 0 && a16(p.Qin) && a16(p.out) && a16(p.res) && a16(p.Qout);
-    if (m->n_planar_launch > 0 && m->N <= 4 && p.ncols == m->K * m->S) {
+    if (m->n_planar_launch > 0 && m->N <= 5 && p.ncols == m->K * m->S) {
       // the planar kernel's tiles, then the curved kernel's (disjoint
       // columns; both launches read Q_in only)
       const int64_t total = m->n_planar_tiles + m->n_curved_tiles;
@@ -1061,7 +1064,8 @@ cudaError_t stage_launch<float>(const wadg_mesh* m, const StageParams<float>& p,
       P.nP = m->d_nP;
       P.tiles = m->d_tlist;
       P.ntiles_list = m->n_planar_launch;
-      cudaError_t e = launch_stage_tc_planar(m->N, P, mode, m->tc_fmt, m->num_sms, st);
+      cudaError_t e = m->N == 5 ? launch_stage_tc5_planar(P, mode, m->tc_fmt, m->num_sms, st)
+                                : launch_stage_tc_planar(m->N, P, mode, m->tc_fmt, m->num_sms, st);
       if (e != cudaSuccess || m->n_planar_launch == total) return e;
       P.tiles = m->d_tlist + m->n_planar_launch;
       P.ntiles_list = total - m->n_planar_launch;

@@ -166,11 +166,13 @@ struct TcStageParams {
   const float* nP = nullptr;
 };
 cudaError_t launch_stage_tc(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
-// The same over the tiles of P.tiles whose elements are all affine (N <= 4).
+// The same over the tiles of P.tiles whose elements are all affine (N <= 4;
+// N = 5: launch_stage_tc5_planar).
 cudaError_t launch_stage_tc_planar(int N, const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
 bool pack_tc_ops(int N, const RefOps& o, int fmt, std::vector<uint8_t>& out);
-// N = 5 (stage_tc5.cu), the collapsed 216-point volume rule.
+// N = 5 (stage_tc5_kernel.cuh), on the 216-point or the 96-point volume rule.
 cudaError_t launch_stage_tc5(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
+cudaError_t launch_stage_tc5_planar(const TcStageParams& P, int mode, int fmt, int grid, cudaStream_t stream);
 bool pack_tc5_ops(const RefOps& o, int fmt, std::vector<uint8_t>& out);
 cudaError_t launch_bounded_wait_selftest(int* err, uint32_t max_iters, cudaStream_t stream);
 
@@ -206,7 +208,7 @@ struct wadg_mesh {
   std::vector<uint8_t> affine;  // [K] 1: the element's geometry nodes are its vertices' affine map
   int64_t n_affine = 0;
   int planar_split = 1;          // 0 off, 1 planned (the default), 2 every all-affine tile (wadg_set_planar_split)
-  int32_t* d_tlist = nullptr;    // the planar tiles, then the others (tensor-core stage, N <= 4)
+  int32_t* d_tlist = nullptr;    // the planar tiles, then the others (tensor-core stage, N <= 5)
   int64_t n_planar_tiles = 0, n_curved_tiles = 0;
   float* d_gP = nullptr;         // compact geometry of the affine elements (see TcStageParams)
   float* d_nP = nullptr;

@@ -63,11 +63,16 @@ def test_planar_tile_counts(W):
 
 
 @pytest.mark.parametrize("precision", ["fp32_3xbf16", "fp32_tf32"])
-@pytest.mark.parametrize("N,n,S", [(1, 4, 2), (2, 4, 1), (3, 4, 3), (4, 4, 1)])
-def test_split_rhs_matches_oracle_and_single_launch(W, precision, N, n, S):
+@pytest.mark.parametrize("N,n,S,fewer", [(1, 4, 2, False), (2, 4, 1, False), (3, 4, 3, False), (4, 4, 1, False),
+                                         (5, 4, 1, False), (5, 4, 2, True)])
+def test_split_rhs_matches_oracle_and_single_launch(W, precision, N, n, S, fewer):
+    """fewer: the fewer-point volume rule (96 points at N = 5) instead of the
+    collapsed one."""
+    from synthetic import fewer_point_rule
+    rule = fewer_point_rule(N) if fewer else None
     VXYZ, EToV, geom = _half_planar(n, N)
-    om = oracle_case(VXYZ, EToV, geom, N)
-    m = library_mesh(VXYZ, EToV, geom, N, precision, shots=S, c2="heterogeneous")
+    om = oracle_case(VXYZ, EToV, geom, N, rule=rule)
+    m = library_mesh(VXYZ, EToV, geom, N, precision, shots=S, c2="heterogeneous", rule=rule)
     W.wadg_set_planar_split(m, "all")
     info = W.wadg_planar_info(m)
     assert 0 < info["planar_launch_tiles"] == info["planar_tiles"] < info["tiles"], info
