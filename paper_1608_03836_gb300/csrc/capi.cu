@@ -968,7 +968,11 @@ int mean_correction(wadg_mesh* m) {
 // planar tiles after 776 curved ones against 0.542 from the rounds alone);
 // N = 5 (82,944 tets, 648 tiles, 118 us rounds): planar 0.91 (0.534 vs
 // 0.589 ms), second launch 0.2 (0.568 ms with 567 planar tiles after 81
-// curved ones against 0.545).  N <= 3 takes the N = 4 values.  The cheapest
+// curved ones against 0.545); N = 2, 3 (196,608 and 82,944 tets, 29 and
+// 44 us rounds): planar 0.96 (0.307 vs 0.319 and 0.212 vs 0.222 ms), second
+// launch 0.35 (0.318 ms with 1,232 planar tiles after 304 curved ones at
+// N = 2; 0.229 ms with 567 after 81 at N = 3).  N = 1 takes the N = 2
+// values.  The cheapest
 // split wins, ties going to the larger curved launch (a single launch when
 // nothing is saved).  Mode 2 runs every all-affine tile on the planar kernel.
 void plan_planar_launch(wadg_mesh* m) {
@@ -979,7 +983,8 @@ void plan_planar_launch(wadg_mesh* m) {
     m->n_planar_launch = np;
     return;
   }
-  const double planar_cost = m->N == 5 ? 0.91 : 0.86, second_launch = m->N == 5 ? 0.2 : 0.7;
+  const double planar_cost = m->N == 5 ? 0.91 : m->N == 4 ? 0.86 : 0.96;
+  const double second_launch = m->N == 5 ? 0.2 : m->N == 4 ? 0.7 : 0.35;
   auto rounds = [&](int64_t n) { return (double)((n + G - 1) / G); };
   double best = 1e300;
   for (int64_t mv = np; mv >= 0; --mv) {
